@@ -1,0 +1,216 @@
+"""Plain CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package.  The product library never does, and this
+package never imports the product.  The arithmetic lives in ``oracle.c``
+(plain C, OpenMP over start vertices); this module marshals arguments and
+adds the few closed forms that are easier to read in Python:
+
+* ``count``            distinct matches = valid injective maps / |Aut|
+                       (Section 2.1 definitions; Section 3.1.1 anti-edges;
+                       Section 3.1.2 anti-vertices).
+* ``motif4_induced``   the six induced 4-vertex motifs from non-induced
+                       counts through the spanning-subgraph linear system.
+* ``fsm_mni``          labeled frequent subgraphs up to three edges with MNI
+                       support (Section 2.1 FSM / MNI; Section 3.2.1 label
+                       discovery), by per-vertex existence of a match.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from math import comb
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+MAXK = 8
+
+OR_ERRORS = {1: "invalid argument", 2: "out of memory", 3: "uint64 overflow"}
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-Wall", "-Wextra", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("off", ctypes.c_void_p),
+                ("adj", ctypes.c_void_p), ("label", ctypes.c_void_p)]
+
+
+class _Pattern(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("rel", ctypes.c_uint8 * (MAXK * MAXK)),
+                ("label", ctypes.c_int32 * MAXK), ("anti_vertex", ctypes.c_uint8 * MAXK),
+                ("vertex_induced", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.or_pattern_aut.argtypes = [ctypes.POINTER(_Pattern), u64p]
+        L.or_count_maps.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), ctypes.c_int, u64p]
+        L.or_mni_bruteforce.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), u64p]
+        L.or_triangles.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int]
+        L.or_triangles.restype = ctypes.c_uint64
+        L.or_triangles_per_vertex.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, ctypes.c_void_p]
+        L.or_kcliques.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_void_p, ctypes.c_int64, u64p]
+        L.or_motif4_noninduced.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, u64p]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise RuntimeError(f"oracle error {rc}: {OR_ERRORS.get(rc, '?')}")
+
+
+class _GraphRef:
+    """Keeps the numpy arrays alive while C holds raw pointers to them."""
+
+    def __init__(self, g):
+        self.off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+        self.adj = np.ascontiguousarray(g.adj, dtype=np.int32)
+        self.lab = None if g.labels is None else np.ascontiguousarray(g.labels, dtype=np.int32)
+        self.s = _Graph(g.n, self.off.ctypes.data, self.adj.ctypes.data if self.adj.size else 0,
+                        None if self.lab is None else self.lab.ctypes.data)
+
+
+def _pattern_struct(p: dict) -> _Pattern:
+    k = p["k"]
+    if not 1 <= k <= MAXK:
+        raise ValueError("pattern size out of range")
+    s = _Pattern()
+    s.k = k
+    for (u, w) in p["edges"]:
+        s.rel[u * MAXK + w] = 1
+        s.rel[w * MAXK + u] = 1
+    for (u, w) in p.get("anti_edges", ()):
+        s.rel[u * MAXK + w] = 2
+        s.rel[w * MAXK + u] = 2
+    labels = p.get("labels")
+    for u in range(MAXK):
+        s.label[u] = -1 if labels is None or u >= k else int(labels[u])
+    av = p.get("anti_vertex")
+    for u in range(MAXK):
+        s.anti_vertex[u] = 0 if av is None or u >= k else int(av[u])
+    s.vertex_induced = 1 if p.get("vertex_induced") else 0
+    return s
+
+
+def automorphisms(p: dict) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().or_pattern_aut(ctypes.byref(_pattern_struct(p)), ctypes.byref(out)))
+    return int(out.value)
+
+
+def count_maps(g, p: dict, threads: int = 0) -> int:
+    """Number of valid injective maps (no symmetry breaking)."""
+    gr = _GraphRef(g)
+    out = ctypes.c_uint64()
+    _check(lib().or_count_maps(ctypes.byref(gr.s), ctypes.byref(_pattern_struct(p)),
+                               threads, ctypes.byref(out)))
+    return int(out.value)
+
+
+def count(g, p: dict, threads: int = 0) -> int:
+    """Distinct matches of p in g: valid maps / |Aut(p)| (exact division)."""
+    maps = count_maps(g, p, threads)
+    aut = automorphisms(p)
+    if maps % aut:
+        raise AssertionError(f"maps {maps} not divisible by |Aut| {aut}")
+    return maps // aut
+
+
+def mni_domains_bruteforce(g, p: dict) -> list[int]:
+    gr = _GraphRef(g)
+    out = (ctypes.c_uint64 * MAXK)()
+    _check(lib().or_mni_bruteforce(ctypes.byref(gr.s), ctypes.byref(_pattern_struct(p)), out))
+    return [int(out[i]) for i in range(p["k"])]
+
+
+def triangles(g, threads: int = 0) -> int:
+    gr = _GraphRef(g)
+    return int(lib().or_triangles(ctypes.byref(gr.s), threads))
+
+
+def triangles_per_vertex(g, threads: int = 0) -> np.ndarray:
+    gr = _GraphRef(g)
+    t = np.zeros(max(g.n, 1), dtype=np.uint64)
+    _check(lib().or_triangles_per_vertex(ctypes.byref(gr.s), threads, t.ctypes.data))
+    return t[:g.n]
+
+
+def kcliques(g, k: int, threads: int = 0, sources=None) -> int:
+    gr = _GraphRef(g)
+    out = ctypes.c_uint64()
+    if sources is None:
+        _check(lib().or_kcliques(ctypes.byref(gr.s), k, threads, None, 0, ctypes.byref(out)))
+    else:
+        src = np.ascontiguousarray(sources, dtype=np.int32)
+        _check(lib().or_kcliques(ctypes.byref(gr.s), k, threads, src.ctypes.data,
+                                 src.shape[0], ctypes.byref(out)))
+    return int(out.value)
+
+
+MOTIF4_ORDER = ("star", "path", "tailed_triangle", "cycle", "diamond", "clique")
+
+
+def motif4_noninduced(g, threads: int = 0) -> dict:
+    gr = _GraphRef(g)
+    out = (ctypes.c_uint64 * 6)()
+    _check(lib().or_motif4_noninduced(ctypes.byref(gr.s), threads, out))
+    return {name: int(out[i]) for i, name in enumerate(MOTIF4_ORDER)}
+
+
+def motif4_induced(g, threads: int = 0) -> dict:
+    """Induced counts I from non-induced counts S of the connected 4-vertex
+    graphs.  S(H) = sum over induced shapes H' of (number of spanning copies
+    of H inside H') * I(H'):
+
+        S(K4)      = I(K4)
+        S(diamond) = I(diamond) + 6 I(K4)
+        S(C4)      = I(C4) + I(diamond) + 3 I(K4)
+        S(tailed)  = I(tailed) + 4 I(diamond) + 12 I(K4)
+        S(star)    = I(star) + I(tailed) + 2 I(diamond) + 4 I(K4)
+        S(path)    = I(path) + 4 I(C4) + 2 I(tailed) + 6 I(diamond) + 12 I(K4)
+    """
+    S = motif4_noninduced(g, threads)
+    I = {}
+    I["clique"] = S["clique"]
+    I["diamond"] = S["diamond"] - 6 * I["clique"]
+    I["cycle"] = S["cycle"] - I["diamond"] - 3 * I["clique"]
+    I["tailed_triangle"] = S["tailed_triangle"] - 4 * I["diamond"] - 12 * I["clique"]
+    I["star"] = S["star"] - I["tailed_triangle"] - 2 * I["diamond"] - 4 * I["clique"]
+    I["path"] = (S["path"] - 4 * I["cycle"] - 2 * I["tailed_triangle"]
+                 - 6 * I["diamond"] - 12 * I["clique"])
+    for k, v in I.items():
+        if v < 0:
+            raise AssertionError(f"negative induced count for {k}")
+    return I
+
+
+def wedges_induced(g, threads: int = 0) -> int:
+    """Induced wedges (open triplets) = sum_v C(d_v, 2) - 3 T."""
+    d = np.diff(g.offsets).astype(object)
+    return int(sum(comb(int(x), 2) for x in d)) - 3 * triangles(g, threads)
+
+
+def stars(g, leaves: int) -> int:
+    """Edge-induced stars with the given number of leaves = sum_v C(d_v, leaves)."""
+    d = np.diff(g.offsets)
+    return int(sum(comb(int(x), leaves) for x in d))
