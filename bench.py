@@ -1,0 +1,348 @@
+"""Benchmark: exact k-clique counting (4- and 5-cliques) on the Chung-Lu
+power-law graph (1M vertices, 10M edges, exponent 2.1, max weight 20K).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = counting every 4-clique and every 5-clique of the resident graph
+(one launch of the persistent clique kernel computes both).  Prints one JSON
+line on rank 0.  ``--impl reference`` times the plain CPU oracle (textbook
+oriented clique lister) on a bounded sample of start vertices instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthgraph as sg  # noqa: E402
+
+WORKLOAD = "kclique_chunglu_n1M_m10M_g2.1"
+METRIC = "exact pattern matches/sec"
+UNIT = "matches/s"
+CLIQUE_SIZES = (4, 5)
+CPU_SAMPLE_SOURCES = 100_000
+
+
+def workload_config(g):
+    return {"workload": WORKLOAD,
+            "graph": {"generator": "chung_lu", "n": g.n, "m": g.m, "gamma": 2.1,
+                      "max_weight": 20000, "max_degree": int(g.meta["max_degree"]),
+                      "seed": int(g.meta["seed"])},
+            "patterns": [f"{k}-clique" for k in CLIQUE_SIZES]}
+
+
+# --------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers ---
+
+def algorithmic_bytes(g, rank: np.ndarray, kmin: int) -> int:
+    """Bytes of adjacency operands the clique plan's level-1 set operations
+    read in one launch: for every start vertex v with at least kmin-1
+    higher-ranked neighbours, its out-list N+(v) plus the out-list of every
+    u in N+(v) except the first (row 0 of the sub-graph has no bits), plus
+    the 16-byte vertex record of every start vertex."""
+    deg = np.diff(g.offsets)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dst = g.adj.astype(np.int64)
+    out = rank[dst] < rank[src]
+    dplus = np.bincount(src[out], minlength=g.n).astype(np.int64)
+    s, d = src[out], dst[out]
+    active = dplus[s] >= kmin - 1
+    s, d = s[active], d[active]
+    total = int(dplus[dplus >= kmin - 1].sum()) + int(dplus[d].sum())
+    # remove the first out-neighbour (smallest rank) of every active start
+    if s.size:
+        order = np.lexsort((rank[d], s))
+        s, d = s[order], d[order]
+        first = np.ones(s.size, dtype=bool)
+        first[1:] = s[1:] != s[:-1]
+        total -= int(dplus[d[first]].sum())
+    return 4 * total + 16 * g.n
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, x: float, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- CPU arm ---
+
+def cpu_oracle_rate(g, steps: int, seed: int = 7):
+    """Oracle lister on `steps` seeded samples of start vertices."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    total, secs = 0, 0.0
+    for _ in range(steps):
+        src = np.sort(rng.choice(g.n, CPU_SAMPLE_SOURCES, replace=False)).astype(np.int32)
+        t = time.perf_counter()
+        for k in CLIQUE_SIZES:
+            total += oracle.kcliques(g, k, sources=src)
+        secs += time.perf_counter() - t
+    return total / secs, total, secs
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    g = sg.workload_graph(2)
+    cores = os.cpu_count()
+    cpu_oracle_rate(g, max(1, min(args.warmup, 1)))  # warm-up (page-in, build)
+    rate, total, secs = cpu_oracle_rate(g, args.steps, seed=11)
+    sample = (f"{CPU_SAMPLE_SOURCES} seeded random start vertices per step (of {g.n}); "
+              f"4- and 5-cliques whose lowest (degree, id) vertex is sampled")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": workload_config(g),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm ---
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2004_02369_b300 as pg
+
+    g = sg.workload_graph(2)
+    stream = torch.cuda.current_stream(dev)
+    G = pg.Graph.from_synth(g, stream=stream)
+    plans = [pg.Plan(k, sg.clique_edges(k), name=f"{k}-clique") for k in CLIQUE_SIZES]
+    counts = torch.zeros(2 * len(plans), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def step():
+        pg.count_async(G, plans, counts, kernel=args.kernel, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    expect = pg.decode_counts(counts)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step()
+        e.record(stream)
+        times.append((s, e))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    ms = [s.elapsed_time(e) for s, e in times]
+    got = pg.decode_counts(counts)
+    if got != expect:
+        raise SystemExit(f"counts changed between steps: {expect} -> {got}")
+    matches = sum(got)
+    ms_step = float(np.mean(ms))
+    ms_step_max = max_over_ranks(world, ms_step, dev)
+    value = sum_over_ranks(world, matches, dev) / (ms_step_max / 1e3)
+
+    # ---- end to end: host CSR in pinned memory -> load -> count -> host ----
+    off_h = torch.from_numpy(g.offsets).pin_memory()
+    adj_h = torch.from_numpy(g.adj).pin_memory()
+    e2e_ms = []
+    for it in range(1 + max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        off_d = off_h.to(dev, non_blocking=True)
+        adj_d = adj_h.to(dev, non_blocking=True)
+        G2 = pg.Graph(off_d, adj_d, stream=stream)
+        pg.count_async(G2, plans, counts, kernel=args.kernel, stream=stream)
+        host = counts.cpu()
+        dt = (time.perf_counter() - t) * 1e3
+        G2.close()
+        del off_d, adj_d
+        if pg.decode_counts(host) != expect:
+            raise SystemExit("end-to-end counts differ")
+        if it > 0:
+            e2e_ms.append(dt)
+    e2e = {"value": matches / (np.mean(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(g.offsets.nbytes + g.adj.nbytes),
+           "d2h_bytes_per_step": int(counts.numel() * 8),
+           "ms_per_step": float(np.mean(e2e_ms)),
+           "includes": "pinned H2D of the CSR, validation + degree relabel on device, count, D2H"}
+
+    # ---- one-pattern-per-launch plain interpreter, for comparison ----------
+    plain = None
+    if args.compare_plain and rank == 0:
+        pc = torch.zeros(2, dtype=torch.int64, device=dev)
+        per = {}
+        for p in plans:
+            pg.count_async(G, [p], pc, kernel=pg.KERNEL_CLIQUE_PLAIN, stream=stream)  # warm
+            torch.cuda.synchronize()
+            flush.zero_()
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            pg.count_async(G, [p], pc, kernel=pg.KERNEL_CLIQUE_PLAIN, stream=stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            assert pg.decode_counts(pc)[0] == expect[plans.index(p)]
+            per[p.name] = s.elapsed_time(e)
+        tot = sum(per.values())
+        plain = {"kernel": "plan interpreter, one warp per start vertex, one launch per pattern",
+                 "ms_per_step": tot, "value": matches / (tot / 1e3), "per_pattern_ms": per,
+                 "speedup_of_value": (matches / (ms_step / 1e3)) / (matches / (tot / 1e3))}
+
+    if rank != 0:
+        return 0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+    alg = algorithmic_bytes(g, G.rank(), min(CLIQUE_SIZES))
+    achieved = alg / (ms_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_count_clique", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "algorithmic_bytes_per_launch": alg, "traffic": args.traffic}
+
+    cpu_rate, _, cpu_secs = cpu_oracle_rate(g, 1)
+    cfg = workload_config(g)
+    cfg.update({"kernel": {0: "auto (persistent bitmap clique kernel)", 3: "clique"}.get(args.kernel, str(args.kernel)),
+                "l2": "256 MiB buffer written between timed steps (not timed)",
+                "counts": {p.name: c for p, c in zip(plans, got)}})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": cfg, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roofline, "clocks": clk,
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{CPU_SAMPLE_SOURCES} seeded random start vertices, 4- and 5-cliques, "
+                                       f"{cpu_secs:.1f} s"},
+            "plain_one_pattern_per_launch": plain,
+            "wall_s_timed": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kernel", type=int, default=0, help="PG_KERNEL_* (0 = auto)")
+    ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch from an ncu capture of this kernel")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * pg.h - C-ABI of the pattern-aware subgraph matching library (libpg.so).
+ *
+ * The library implements the matching engine of Peregrine (Jamshidi, Mahadasa,
+ * Vora, "Peregrine: A Pattern-Aware Graph Mining System", EuroSys 2020) on one
+ * CUDA device: a host plan compiler turns a pattern into an exploration plan
+ * (Section 4.1, "Computing exploration plan" figure) and CUDA kernels extend
+ * every start vertex of a device-resident graph along that plan (Section 5.1,
+ * "Pattern-Aware Processing Model" figure), counting matches exactly
+ * (128-bit counters returned as two uint64 words).
+ *
+ * Conventions for every entry point:
+ *  - Return value: PG_OK (0) on success, otherwise one of the PG_E* codes.
+ *    pg_last_error() then gives a human-readable message for the calling
+ *    host thread.  No entry point aborts the process.
+ *  - Pointers documented as "host" must be readable by the CPU; "device"
+ *    pointers must be CUDA device (or managed) memory of the current device.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Functions documented as asynchronous only enqueue work on it.
+ *  - Objects returned through `**out` are owned by the caller and released
+ *    with the matching pg_free_* function.
+ *  - Vertex ids are int32 (n < 2^31); adjacency offsets are int64.
+ *  - The library allocates its own device memory with cudaMalloc for graphs,
+ *    plans and scratch, and frees it in the pg_free_* calls.
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define PG_OK 0
+#define PG_EINVAL 1    /* malformed argument: bad CSR, bad pattern, size limit */
+#define PG_ENOMEM 2    /* host or device allocation failed */
+#define PG_ETRUNC 3    /* output buffer too small (match listing); totals still valid */
+#define PG_ETIMEOUT 4  /* a kernel's work budget ran out; partial results discarded */
+#define PG_EDEVICE 5   /* CUDA runtime error (launch failure, no device, ...) */
+#define PG_EUNSUPPORTED 6 /* valid request that this build does not implement */
+
+#define PG_MAX_PATTERN 8 /* pattern vertices, regular plus anti-vertices */
+
+typedef struct pg_graph pg_graph; /* device-resident data graph (opaque) */
+typedef struct pg_plan pg_plan;   /* compiled exploration plan (opaque, host) */
+
+/*
+ * Pattern description (Section 3.1, "Pattern Interface" figure; anti-edges
+ * Section 3.1.1; anti-vertices Section 3.1.2; vertex-induced matching
+ * Section 3.1.3).  Pattern vertices are 0..k-1.
+ *   edges        n_edges pairs (u, v), u != v.
+ *   anti_edges   n_anti pairs (u, v): m(u) and m(v) must not be adjacent.
+ *   labels       k labels, -1 = any label; NULL = unlabeled pattern.
+ *   anti_vertex  k flags (1 = anti-vertex: never matched, only its anti-edges
+ *                constrain the match); NULL = none.
+ *   vertex_induced  1: every non-adjacent pair of regular vertices becomes
+ *                an anti-edge (the Theorem of Section 3.1.3).
+ * All arrays are host memory, read during pg_compile_pattern only.
+ */
+typedef struct {
+    int32_t k;
+    int32_t n_edges;
+    const int32_t *edges;
+    int32_t n_anti;
+    const int32_t *anti_edges;
+    const int32_t *labels;
+    const uint8_t *anti_vertex;
+    int32_t vertex_induced;
+} pg_pattern_desc;
+
+/* Graph facts after loading (all counts of the undirected simple graph). */
+typedef struct {
+    int64_t n;           /* vertices */
+    int64_t m;           /* undirected edges */
+    int64_t max_degree;
+    int64_t max_out_degree; /* neighbours of higher degree rank (Section 5.2 order) */
+    int64_t device_bytes;   /* device memory held by the graph */
+    int32_t labeled;
+    int32_t n_labels;       /* 1 + largest label, 0 if unlabeled */
+} pg_graph_info;
+
+/* Plan facts for inspection and tests. */
+typedef struct {
+    int32_t k;               /* pattern vertices (regular + anti) */
+    int32_t n_regular;
+    uint64_t automorphisms;  /* |Aut| restricted to regular vertices */
+    int32_t n_po;            /* symmetry-breaking pairs, po[i] = (a, b) means m(a) < m(b) */
+    int32_t po[2 * 28];
+    uint32_t core_mask;      /* bit u set: pattern vertex u is in the core p_C */
+    int32_t n_orders;        /* matching orders (valid core vertex sequences) */
+    int32_t n_levels;        /* levels per order: core + enumerated non-core + counted */
+    int32_t counted_group;   /* size of the non-core group counted by C(|S|, g) */
+    int32_t kernel;          /* PG_KERNEL_* the automatic dispatch would choose */
+    double compile_ms;       /* host time spent in pg_compile_pattern */
+} pg_plan_info;
+
+/* Kernel families for pg_count_ex. */
+#define PG_KERNEL_AUTO 0
+#define PG_KERNEL_GENERIC 1       /* plan interpreter, any pattern */
+#define PG_KERNEL_CLIQUE_PLAIN 2  /* plan interpreter, one warp per task, one launch per pattern */
+#define PG_KERNEL_CLIQUE 3        /* k-clique, persistent, bitmap sub-graph */
+#define PG_KERNEL_MOTIF4_FUSED 4  /* the six induced 4-vertex motifs in one launch */
+
+/*
+ * pg_load_graph - make a data graph resident on the current device.
+ * Section 5.5 (adjacency lists) and Section 5.2 (degree ordering).
+ *   offsets  int64[n+1], adj int32[nnz]: an undirected simple graph in CSR
+ *            form, every list sorted strictly ascending, no self loops, every
+ *            edge present in both directions (nnz = 2m).
+ *   labels   int32[n] vertex labels >= 0, or NULL.
+ *   inputs_on_device  0: offsets/adj/labels are host memory (copied in);
+ *            1: they are device memory (read, not kept).
+ *   stream   stream for the copies and the relabelling kernels; the call
+ *            synchronises it before returning.
+ * The library relabels vertices by (degree descending, id ascending), so that
+ * lower ids mean higher degree, rewrites and re-sorts every list in the new
+ * ids and pads each list to 16 bytes.  Results never expose the new ids
+ * except through pg_graph_rank.
+ * Errors: PG_EINVAL (n < 0, nnz mismatch, unsorted list, self loop,
+ * asymmetric edge, vertex id out of range, negative label), PG_ENOMEM,
+ * PG_EDEVICE.
+ */
+int pg_load_graph(const int64_t *offsets, int64_t n, const int32_t *adj, int64_t nnz,
+                  const int32_t *labels, int32_t inputs_on_device, void *stream,
+                  pg_graph **out);
+
+/* pg_graph_get_info - facts about a loaded graph (host struct out). */
+int pg_graph_get_info(const pg_graph *g, pg_graph_info *out);
+
+/* pg_graph_rank - copy the relabelling to host: rank_out[v] = new id of
+ * original vertex v (int32[n], host).  Synchronous. */
+int pg_graph_rank(const pg_graph *g, int32_t *rank_out);
+
+/* pg_free_graph - release the graph's device memory (NULL is a no-op). */
+void pg_free_graph(pg_graph *g);
+
+/*
+ * pg_compile_pattern - build the exploration plan of a pattern (Section 4.1
+ * "Computing exploration plan" figure; anti-edges Section 4.2; anti-vertices
+ * Section 4.3): automorphisms, symmetry-breaking partial order, minimum
+ * connected vertex cover as the core, matching orders, and the per-level set
+ * operations of the core and of the non-core completion.  Host only; touches
+ * no graph.
+ * Errors: PG_EINVAL (k outside 1..8, self loop, pair both edge and anti-edge,
+ * regular vertices not connected by edges, anti-vertex with a true edge or
+ * with no anti-edge), PG_EUNSUPPORTED (anti-vertices: not in this build),
+ * PG_ENOMEM.
+ */
+int pg_compile_pattern(const pg_pattern_desc *desc, pg_plan **out);
+
+/* pg_plan_get_info - inspect a plan (host struct out). */
+int pg_plan_get_info(const pg_plan *p, pg_plan_info *out);
+
+/* pg_free_plan - release a plan and its device copies (NULL is a no-op). */
+void pg_free_plan(pg_plan *p);
+
+/*
+ * pg_count - number of distinct matches of each plan's pattern in the graph
+ * (Section 3.2: count() is match() with an incrementing callback).
+ *   plans       n_plans compiled plans (host array of handles), n_plans <= 64.
+ *   counts_out  uint64[2 * n_plans], host: count i is the 128-bit integer
+ *               counts_out[2i] + 2^64 * counts_out[2i+1] (exact; star counts
+ *               on hub-heavy graphs exceed 2^64).
+ * Synchronous: returns after the counts are on the host.  Kernel choice is
+ * automatic (PG_KERNEL_AUTO).  Errors: PG_EINVAL, PG_ENOMEM, PG_EDEVICE,
+ * PG_ETIMEOUT.
+ */
+int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_out,
+             void *stream);
+
+/*
+ * pg_count_ex - asynchronous counting with an explicit kernel family.
+ *   counts_dev  uint64[2 * n_plans], device, same (low, high) layout as
+ *               pg_count; the call zeroes it on `stream` and the kernels add
+ *               into it.
+ *   kernel      PG_KERNEL_*; PG_EINVAL if the family cannot run these plans
+ *               (e.g. PG_KERNEL_CLIQUE for a non-clique).
+ * Only enqueues work (no host synchronisation, no allocation once the
+ * graph's scratch has been sized by a first call with the same plans), so a
+ * sequence of calls can be captured in a CUDA graph after one warm-up call.
+ */
+int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev,
+                int32_t kernel, void *stream);
+
+/* pg_last_error - message of the last failed call on this host thread. */
+const char *pg_last_error(void);
+
+/* pg_version - library version (major * 10000 + minor * 100 + patch). */
+int pg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H */

@@ -1,0 +1,237 @@
+"""Python binding of libpg (pattern-aware subgraph matching on one CUDA device).
+
+Argument marshalling only: every step of matching runs in the library's CUDA
+kernels.  The shared library must have been built in-tree
+(``python -m paper_2004_02369_b300.build``); importing this package without it
+raises ImportError instead of falling back to anything else.
+
+PyTorch supplies device memory and streams: graph inputs may be torch CUDA
+tensors (read in place), ``count_async`` writes into a caller-owned torch
+CUDA tensor on the caller's stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpg.so")
+
+PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETRUNC, PG_ETIMEOUT, PG_EDEVICE, PG_EUNSUPPORTED = range(7)
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_MOTIF4_FUSED = range(5)
+MAX_PATTERN = 8
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2004_02369_b300.build`")
+
+
+class PgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libpg error {code}: {msg}")
+        self.code = code
+
+
+class _PatternDesc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.c_void_p),
+                ("n_anti", ctypes.c_int32), ("anti_edges", ctypes.c_void_p),
+                ("labels", ctypes.c_void_p), ("anti_vertex", ctypes.c_void_p),
+                ("vertex_induced", ctypes.c_int32)]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("max_degree", ctypes.c_int64),
+                ("max_out_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("labeled", ctypes.c_int32), ("n_labels", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("n_regular", ctypes.c_int32),
+                ("automorphisms", ctypes.c_uint64), ("n_po", ctypes.c_int32),
+                ("po", ctypes.c_int32 * 56), ("core_mask", ctypes.c_uint32),
+                ("n_orders", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("counted_group", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("compile_ms", ctypes.c_double)]
+
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp, _i32, _i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+_lib.pg_load_graph.argtypes = [_vp, _i64, _vp, _i64, _vp, _i32, _vp, ctypes.POINTER(_vp)]
+_lib.pg_graph_get_info.argtypes = [_vp, ctypes.POINTER(GraphInfo)]
+_lib.pg_graph_rank.argtypes = [_vp, _vp]
+_lib.pg_free_graph.argtypes = [_vp]
+_lib.pg_free_graph.restype = None
+_lib.pg_compile_pattern.argtypes = [ctypes.POINTER(_PatternDesc), ctypes.POINTER(_vp)]
+_lib.pg_plan_get_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
+_lib.pg_free_plan.argtypes = [_vp]
+_lib.pg_free_plan.restype = None
+_lib.pg_count.argtypes = [_vp, _vp, _i32, _vp, _vp]
+_lib.pg_count_ex.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp]
+_lib.pg_last_error.restype = ctypes.c_char_p
+
+
+def lib():
+    return _lib
+
+
+def _check(rc: int):
+    if rc != PG_OK:
+        raise PgError(rc, _lib.pg_last_error().decode())
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Graph:
+    """A data graph resident on the current CUDA device.
+
+    ``offsets`` int64[n+1] and ``adj`` int32[2m]: undirected simple CSR with
+    sorted lists (numpy arrays, or torch CUDA tensors read in place);
+    ``labels`` optional int32[n].
+    """
+
+    def __init__(self, offsets, adj, labels=None, stream=None):
+        on_dev = _is_torch_cuda(offsets)
+        if on_dev:
+            import torch
+            offsets = offsets.to(torch.int64).contiguous()
+            adj = adj.to(torch.int32).contiguous()
+            labels = None if labels is None else labels.to(torch.int32).contiguous()
+            p_off, p_adj = offsets.data_ptr(), adj.data_ptr()
+            p_lab = None if labels is None else labels.data_ptr()
+            n, nnz = offsets.numel() - 1, adj.numel()
+        else:
+            offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+            adj = np.ascontiguousarray(adj, dtype=np.int32)
+            labels = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+            p_off = offsets.ctypes.data
+            p_adj = adj.ctypes.data if adj.size else None
+            p_lab = None if labels is None else labels.ctypes.data
+            n, nnz = offsets.shape[0] - 1, adj.shape[0]
+        h = _vp()
+        _check(_lib.pg_load_graph(p_off, n, p_adj, nnz, p_lab, 1 if on_dev else 0,
+                                  _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_synth(cls, g, stream=None):
+        return cls(g.offsets, g.adj, g.labels, stream=stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> GraphInfo:
+        out = GraphInfo()
+        _check(_lib.pg_graph_get_info(self._h, ctypes.byref(out)))
+        return out
+
+    def rank(self) -> np.ndarray:
+        n = self.info().n
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        _check(_lib.pg_graph_rank(self._h, out.ctypes.data))
+        return out[:n]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pg_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Plan:
+    """Compiled exploration plan of one pattern (host object)."""
+
+    def __init__(self, k, edges, anti_edges=(), labels=None, anti_vertex=None,
+                 vertex_induced=False, name=None):
+        self.name = name
+        self.pattern = dict(k=int(k), edges=[tuple(e) for e in edges],
+                            anti_edges=[tuple(e) for e in anti_edges],
+                            labels=None if labels is None else list(labels),
+                            anti_vertex=None if anti_vertex is None else list(anti_vertex),
+                            vertex_induced=bool(vertex_induced))
+        e = np.ascontiguousarray(np.asarray(list(edges), dtype=np.int32).reshape(-1))
+        a = np.ascontiguousarray(np.asarray(list(anti_edges), dtype=np.int32).reshape(-1))
+        lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32)
+        av = None if anti_vertex is None else np.ascontiguousarray(anti_vertex, dtype=np.uint8)
+        d = _PatternDesc(int(k), e.size // 2, e.ctypes.data if e.size else None,
+                         a.size // 2, a.ctypes.data if a.size else None,
+                         None if lab is None else lab.ctypes.data,
+                         None if av is None else av.ctypes.data, 1 if vertex_induced else 0)
+        h = _vp()
+        _check(_lib.pg_compile_pattern(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_dict(cls, p: dict):
+        return cls(p["k"], p["edges"], p.get("anti_edges", ()), p.get("labels"),
+                   p.get("anti_vertex"), p.get("vertex_induced", False), p.get("name"))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> PlanInfo:
+        out = PlanInfo()
+        _check(_lib.pg_plan_get_info(self._h, ctypes.byref(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pg_free_plan(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def _plan_array(plans):
+    arr = (_vp * len(plans))(*[p.handle.value for p in plans])
+    return arr
+
+
+def _u128(lo: int, hi: int) -> int:
+    return (int(hi) << 64) | int(lo)
+
+
+def count(graph: Graph, plans, stream=None) -> list[int]:
+    """Exact match counts of each plan's pattern (synchronous)."""
+    plans = list(plans)
+    out = np.zeros(2 * max(len(plans), 1), dtype=np.uint64)
+    _check(_lib.pg_count(graph.handle, _plan_array(plans), len(plans), out.ctypes.data,
+                         _stream_ptr(stream)))
+    return [_u128(out[2 * i], out[2 * i + 1]) for i in range(len(plans))]
+
+
+def count_async(graph: Graph, plans, out, kernel: int = KERNEL_AUTO, stream=None):
+    """Enqueue counting into ``out`` (torch CUDA int64 tensor with 2*len(plans)
+    elements, (low, high) words per count) on ``stream``; no host sync."""
+    plans = list(plans)
+    if out.numel() < 2 * len(plans) or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor with 2*len(plans) 64-bit elements")
+    _check(_lib.pg_count_ex(graph.handle, _plan_array(plans), len(plans), out.data_ptr(),
+                            kernel, _stream_ptr(stream)))
+
+
+def decode_counts(words) -> list[int]:
+    """(low, high) 64-bit words (numpy or torch int64) -> Python ints."""
+    w = np.asarray(words.cpu() if hasattr(words, "cpu") else words).view(np.uint64)
+    return [_u128(w[2 * i], w[2 * i + 1]) for i in range(w.shape[0] // 2)]

@@ -1,0 +1,274 @@
+// C-ABI entry points (include/pg.h): argument checking, ownership, kernel
+// dispatch.  No compute happens here; every step of the path runs in the
+// library's kernels.
+#include <cstring>
+#include <string>
+
+#include "pg_internal.h"
+
+namespace {
+thread_local std::string g_last_error;
+
+struct DevTmp {
+    void *p = nullptr;
+    ~DevTmp() { if (p) cudaFree(p); }
+};
+}  // namespace
+
+int pg_set_error(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int pg_cuda_error(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PG_ENOMEM : PG_EDEVICE;
+}
+
+extern "C" const char *pg_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int pg_version(void) { return 100; }
+
+// ---------------------------------------------------------------- graph ----
+
+extern "C" int pg_load_graph(const int64_t *offsets, int64_t n, const int32_t *adj, int64_t nnz,
+                             const int32_t *labels, int32_t inputs_on_device, void *stream, pg_graph **out) {
+    if (!out) return pg_set_error(PG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || nnz < 0 || !offsets || (nnz > 0 && !adj))
+        return pg_set_error(PG_EINVAL, "bad graph arguments");
+    if (n >= 0x7fffffff) return pg_set_error(PG_EINVAL, "more than 2^31-1 vertices");
+    cudaStream_t s = (cudaStream_t)stream;
+    pg_graph *g = new (std::nothrow) pg_graph();
+    if (!g) return pg_set_error(PG_ENOMEM, "host allocation failed");
+    g->n = n;
+    g->m = nnz / 2;
+    g->labeled = labels ? 1 : 0;
+    int rc = PG_OK;
+    do {
+        cudaError_t e = cudaGetDevice(&g->device);
+        if (e != cudaSuccess) { rc = pg_cuda_error(e, "cudaGetDevice"); break; }
+        e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+        if (e != cudaSuccess) { rc = pg_cuda_error(e, "cudaDeviceGetAttribute"); break; }
+        DevTmp toff, tadj, tlab;
+        const int64_t *d_off = offsets;
+        const int32_t *d_adj = adj;
+        const int32_t *d_lab = labels;
+        if (!inputs_on_device) {
+            if (offsets[0] != 0 || offsets[n] != nnz) { rc = pg_set_error(PG_EINVAL, "offsets[0] must be 0 and offsets[n] == nnz"); break; }
+            if ((e = cudaMalloc(&toff.p, (n + 1) * sizeof(int64_t))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+            if ((e = cudaMalloc(&tadj.p, (nnz > 0 ? nnz : 1) * sizeof(int32_t))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+            if ((e = cudaMemcpyAsync(toff.p, offsets, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMemcpyAsync"); break; }
+            if (nnz > 0 && (e = cudaMemcpyAsync(tadj.p, adj, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMemcpyAsync"); break; }
+            if (labels) {
+                if ((e = cudaMalloc(&tlab.p, (n > 0 ? n : 1) * sizeof(int32_t))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+                if (n > 0 && (e = cudaMemcpyAsync(tlab.p, labels, n * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMemcpyAsync"); break; }
+            }
+            d_off = (const int64_t *)toff.p;
+            d_adj = (const int32_t *)tadj.p;
+            d_lab = labels ? (const int32_t *)tlab.p : nullptr;
+        }
+        rc = pg_graph_build(g, d_off, d_adj, nnz, d_lab, s);
+        if (rc) break;
+        if ((e = cudaMalloc(&g->queues, PG_MAX_QUEUES * sizeof(unsigned long long))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+        if ((e = cudaMalloc(&g->tmp_counts, 2 * PG_MAX_QUEUES * sizeof(unsigned long long))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaStreamSynchronize"); break; }
+    } while (0);
+    if (rc) {
+        pg_free_graph(g);
+        return rc;
+    }
+    g->d.vinfo = g->vinfo;
+    g->d.adj = g->adj;
+    g->d.n = (int)g->n;
+    g->d.max_deg = (int)g->max_deg;
+    g->d.max_out = (int)g->max_out;
+    g->d.labeled = g->labeled;
+    *out = g;
+    return PG_OK;
+}
+
+extern "C" int pg_graph_get_info(const pg_graph *g, pg_graph_info *out) {
+    if (!g || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    out->n = g->n;
+    out->m = g->m;
+    out->max_degree = g->max_deg;
+    out->max_out_degree = g->max_out;
+    out->device_bytes = g->bytes_device + (int64_t)g->scratch_bytes;
+    out->labeled = g->labeled;
+    out->n_labels = g->n_labels;
+    return PG_OK;
+}
+
+extern "C" int pg_graph_rank(const pg_graph *g, int32_t *rank_out) {
+    if (!g || (!rank_out && g->n > 0)) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (g->n > 0) PG_CUDA(cudaMemcpy(rank_out, g->rank, g->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return PG_OK;
+}
+
+extern "C" void pg_free_graph(pg_graph *g) {
+    if (!g) return;
+    if (g->vinfo) cudaFree(g->vinfo);
+    if (g->adj) cudaFree(g->adj);
+    if (g->rank) cudaFree(g->rank);
+    if (g->scratch) cudaFree(g->scratch);
+    if (g->queues) cudaFree(g->queues);
+    if (g->tmp_counts) cudaFree(g->tmp_counts);
+    delete g;
+}
+
+int pg_ensure_scratch(pg_graph *g, size_t bytes, cudaStream_t s) {
+    if (bytes <= g->scratch_bytes) return PG_OK;
+    if (g->scratch) {
+        // earlier launches on any stream may still read the old arena
+        PG_CUDA(cudaDeviceSynchronize());
+        cudaFree(g->scratch);
+        g->scratch = nullptr;
+        g->scratch_bytes = 0;
+    }
+    (void)s;
+    PG_CUDA(cudaMalloc(&g->scratch, bytes));
+    g->scratch_bytes = bytes;
+    return PG_OK;
+}
+
+// ---------------------------------------------------------------- plans ----
+
+extern "C" int pg_compile_pattern(const pg_pattern_desc *d, pg_plan **out) {
+    if (!d || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (d->k < 1 || d->k > PG_MAX_PATTERN) return pg_set_error(PG_EINVAL, "pattern size must be 1..8");
+    PgPattern p;
+    p.k = d->k;
+    auto add = [&](const int32_t *pairs, int32_t np, uint8_t val) -> int {
+        if (np < 0 || (np > 0 && !pairs)) return pg_set_error(PG_EINVAL, "bad edge array");
+        for (int i = 0; i < np; ++i) {
+            int u = pairs[2 * i], w = pairs[2 * i + 1];
+            if (u < 0 || w < 0 || u >= d->k || w >= d->k) return pg_set_error(PG_EINVAL, "pattern vertex out of range");
+            if (u == w) return pg_set_error(PG_EINVAL, "self loop in pattern");
+            if (p.rel[u][w] && p.rel[u][w] != val) return pg_set_error(PG_EINVAL, "pair is both edge and anti-edge");
+            p.rel[u][w] = p.rel[w][u] = val;
+        }
+        return PG_OK;
+    };
+    int rc = add(d->edges, d->n_edges, 1);
+    if (rc) return rc;
+    rc = add(d->anti_edges, d->n_anti, 2);
+    if (rc) return rc;
+    for (int u = 0; u < d->k; ++u) {
+        p.label[u] = d->labels ? d->labels[u] : -1;
+        p.anti_vertex[u] = d->anti_vertex ? (d->anti_vertex[u] ? 1 : 0) : 0;
+    }
+    pg_plan *pl = new (std::nothrow) pg_plan();
+    if (!pl) return pg_set_error(PG_ENOMEM, "host allocation failed");
+    std::string err;
+    rc = pg_plan_compile(p, d->vertex_induced != 0, pl->h, err);
+    if (rc) {
+        delete pl;
+        return pg_set_error(rc, err);
+    }
+    pl->kernel_auto = (pl->h.is_clique && pl->h.pat.k >= 3) ? PG_KERNEL_CLIQUE : PG_KERNEL_GENERIC;
+    *out = pl;
+    return PG_OK;
+}
+
+extern "C" int pg_plan_get_info(const pg_plan *pl, pg_plan_info *out) {
+    if (!pl || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    const PgPlanHost &h = pl->h;
+    out->k = h.pat.k;
+    out->n_regular = h.n_regular;
+    out->automorphisms = h.aut;
+    out->n_po = (int32_t)h.po.size();
+    for (int i = 0; i < out->n_po && i < 28; ++i) {
+        out->po[2 * i] = h.po[i].first;
+        out->po[2 * i + 1] = h.po[i].second;
+    }
+    out->core_mask = h.core_mask;
+    out->n_orders = (int32_t)h.orders.size();
+    out->n_levels = h.orders.empty() ? 0 : h.orders[0].n_levels;
+    out->counted_group = h.counted_group;
+    out->kernel = pl->kernel_auto;
+    out->compile_ms = h.compile_ms;
+    return PG_OK;
+}
+
+extern "C" void pg_free_plan(pg_plan *pl) {
+    if (!pl) return;
+    if (pl->d_orders) cudaFree(pl->d_orders);
+    delete pl;
+}
+
+int pg_plan_upload(pg_plan *pl) {
+    if (pl->d_orders || pl->h.orders.empty()) return PG_OK;
+    const size_t bytes = pl->h.orders.size() * sizeof(PgOrder);
+    PG_CUDA(cudaMalloc(&pl->d_orders, bytes));
+    PG_CUDA(cudaMemcpy(pl->d_orders, pl->h.orders.data(), bytes, cudaMemcpyHostToDevice));
+    return PG_OK;
+}
+
+// ---------------------------------------------------------------- count ----
+
+extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev,
+                           int32_t kernel, void *stream) {
+    if (!g || (n_plans > 0 && (!plans || !counts_dev)) || n_plans < 0)
+        return pg_set_error(PG_EINVAL, "NULL argument");
+    if (n_plans > PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "at most 64 plans per call");
+    if (n_plans == 0) return PG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    bool all_clique = true;
+    int kmin = PG_MAX_PATTERN + 1, kmax = 0;
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return pg_set_error(PG_EINVAL, "NULL plan");
+        const PgPlanHost &h = plans[i]->h;
+        if (h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+        all_clique &= h.is_clique && h.pat.k >= 3;
+        kmin = std::min(kmin, h.pat.k);
+        kmax = std::max(kmax, h.pat.k);
+    }
+    if (kernel == PG_KERNEL_AUTO) kernel = all_clique ? PG_KERNEL_CLIQUE : PG_KERNEL_GENERIC;
+    if (kernel == PG_KERNEL_CLIQUE && !all_clique)
+        return pg_set_error(PG_EINVAL, "PG_KERNEL_CLIQUE needs unlabeled k-clique patterns, k >= 3");
+    if (kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN && kernel != PG_KERNEL_CLIQUE)
+        return pg_set_error(PG_EUNSUPPORTED, "kernel family not built");
+    size_t need = 0;
+    for (int i = 0; i < n_plans; ++i) {
+        int rc = pg_plan_upload(plans[i]);
+        if (rc) return rc;
+        if (kernel == PG_KERNEL_GENERIC) need = std::max(need, pg_generic_scratch_bytes(g, plans[i], true));
+        if (kernel == PG_KERNEL_CLIQUE_PLAIN) need = std::max(need, pg_generic_scratch_bytes(g, plans[i], false));
+    }
+    if (kernel == PG_KERNEL_CLIQUE) need = pg_clique_scratch_bytes(g);
+    int rc = pg_ensure_scratch(g, need, s);
+    if (rc) return rc;
+    PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * n_plans, s));
+    if (kernel == PG_KERNEL_CLIQUE) {
+        // one launch counts every size kmin..kmax; copy each plan's size out
+        PG_CUDA(cudaMemsetAsync(g->tmp_counts, 0, 2 * sizeof(uint64_t) * (kmax - kmin + 1), s));
+        rc = pg_launch_clique(g, kmin, kmax, g->tmp_counts, 0, s);
+        if (rc) return rc;
+        for (int i = 0; i < n_plans; ++i)
+            PG_CUDA(cudaMemcpyAsync(counts_dev + 2 * i, g->tmp_counts + 2 * (plans[i]->h.pat.k - kmin),
+                                    2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        return PG_OK;
+    }
+    for (int i = 0; i < n_plans; ++i) {
+        rc = pg_launch_generic(g, plans[i], (unsigned long long *)counts_dev + 2 * i, i,
+                               kernel == PG_KERNEL_GENERIC, s);
+        if (rc) return rc;
+    }
+    return PG_OK;
+}
+
+extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_out, void *stream) {
+    if (n_plans > 0 && !counts_out) return pg_set_error(PG_EINVAL, "NULL counts_out");
+    if (n_plans == 0) return PG_OK;
+    DevTmp c;
+    PG_CUDA(cudaMalloc(&c.p, 2 * sizeof(uint64_t) * n_plans));
+    int rc = pg_count_ex(g, plans, n_plans, (uint64_t *)c.p, PG_KERNEL_AUTO, stream);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    PG_CUDA(cudaMemcpyAsync(counts_out, c.p, 2 * sizeof(uint64_t) * n_plans, cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    return PG_OK;
+}

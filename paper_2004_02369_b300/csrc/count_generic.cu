@@ -1,0 +1,293 @@
+// K1: plan-interpreter counting kernel (any pattern the compiler accepts).
+//
+// Section 5.1 "Pattern-Aware Processing Model" figure: every task is one
+// (start vertex, matching order) pair; the start vertex binds the highest
+// core position and the remaining core vertices are bound level by level
+// (matchFrom), candidates being intersections / differences of sorted
+// adjacency lists cut to the id range that the partial order allows (the
+// "PO" stage, found by binary search on the sorted lists).  Non-core vertices
+// other than the counted group are bound the same way; the counted group is
+// never enumerated: its candidate set's cardinality |S| gives C(|S|, g)
+// matches (Section 5.1, completing a core match by set operations).
+//
+// GPU mapping: one warp per task, tasks handed out through a device atomic
+// counter in start-vertex rank order, i.e. highest degree first (Section
+// 5.2, Section 5.5).  A warp binds levels depth first with an explicit stack;
+// each level's candidate set is built cooperatively (lanes take driver
+// elements, check membership in the other lists by binary search, compact
+// with __ballot_sync/__popc) into a per-warp scratch buffer.  The last level
+// is counted, by inclusion-exclusion over its difference lists when that
+// touches fewer elements than filtering the driver list.
+#include "device_sets.cuh"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kBlock = kWarpsPerBlock * 32;
+
+struct GenericArgs {
+    DevGraph g;
+    const PgOrder *orders;
+    int n_orders;
+    int *scratch;
+    long long warp_stride;      // ints per warp
+    long long lvl_off[PGP_MAXK]; // offset of level l's buffer inside a warp's region
+    unsigned long long *queue;  // dynamic task counter (persistent mode)
+    unsigned long long n_tasks;
+    int persistent;             // 0: one task per warp, no queue
+    unsigned long long *counts; // (low, high)
+};
+
+struct LevelRange {
+    int lo, hi; // open interval (lo, hi); lo = -1 / hi = INT_MAX when unbounded
+};
+
+__device__ __forceinline__ LevelRange level_range(const PgLevel &L, const int *m) {
+    LevelRange r{-1, 0x7fffffff};
+    for (int i = 0; i < L.n_lo; ++i) r.lo = max(r.lo, m[L.lo_src[i]]);
+    for (int i = 0; i < L.n_hi; ++i) r.hi = min(r.hi, m[L.hi_src[i]]);
+    return r;
+}
+
+// x passes label and exclusion tests of level L
+__device__ __forceinline__ bool pass_label_excl(const DevGraph &g, const PgLevel &L, const int *m, int x) {
+    bool ok = true;
+    for (int i = 0; i < L.n_excl; ++i) ok &= (x != m[L.excl_src[i]]);
+    if (ok && L.label >= 0) ok = (__ldg(&g.vinfo[x].w) == L.label);
+    return ok;
+}
+
+// Materialise the candidate set of (non-last) level L into buf; returns size.
+__device__ int fill_level(const DevGraph &g, const PgLevel &L, const int *m, int *buf, int lane) {
+    const LevelRange r = level_range(L, m);
+    if (r.lo + 1 >= r.hi) return 0;
+    Slice s[PGP_MAXK];
+    int drv = 0;
+    for (int i = 0; i < L.n_int; ++i) {
+        const int4 vi = __ldg(&g.vinfo[m[L.int_src[i]]]);
+        s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi);
+        if (s[i].len < s[drv].len) drv = i;
+    }
+    const Slice d = s[drv];
+    int n_out = 0;
+    for (int base = 0; base < d.len; base += 32) {
+        const int idx = base + lane;
+        bool ok = idx < d.len;
+        int x = 0;
+        if (ok) {
+            x = __ldg(d.p + idx);
+            for (int i = 0; i < L.n_int && ok; ++i)
+                if (i != drv) ok = contains_g(s[i].p, s[i].len, x);
+            for (int i = 0; i < L.n_diff && ok; ++i) {
+                const int4 vi = __ldg(&g.vinfo[m[L.diff_src[i]]]);
+                ok = !contains_g(adj_of(g, vi), vi.y, x);
+            }
+            if (ok) ok = pass_label_excl(g, L, m, x);
+        }
+        const unsigned bal = __ballot_sync(PG_FULL, ok);
+        if (ok) buf[n_out + __popc(bal & ((1u << lane) - 1))] = x;
+        n_out += __popc(bal);
+    }
+    __syncwarp();
+    return n_out;
+}
+
+// |S| of the last level (before C(|S|, g)).
+__device__ unsigned long long count_last(const DevGraph &g, const PgLevel &L, const int *m, int lane) {
+    const LevelRange r = level_range(L, m);
+    if (r.lo + 1 >= r.hi) return 0;
+    Slice s[2 * PGP_MAXK];
+    const int ni = L.n_int, nd = L.n_diff;
+    int drv = 0;
+    for (int i = 0; i < ni; ++i) {
+        const int4 vi = __ldg(&g.vinfo[m[L.int_src[i]]]);
+        s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi);
+        if (s[i].len < s[drv].len) drv = i;
+    }
+    for (int j = 0; j < nd; ++j) {
+        const int4 vi = __ldg(&g.vinfo[m[L.diff_src[j]]]);
+        s[ni + j] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi);
+    }
+    const bool labeled = L.label >= 0;
+    // cost of filtering the driver directly vs inclusion-exclusion
+    long long direct = (long long)s[drv].len * (ni - 1 + nd + (labeled ? 1 : 0));
+    long long ie = 0;
+    for (unsigned T = 1; T < (1u << nd); ++T) {
+        int mn = s[drv].len, terms = ni - 1 + (labeled ? 1 : 0);
+        for (int j = 0; j < nd; ++j)
+            if (T >> j & 1) { mn = min(mn, s[ni + j].len); ++terms; }
+        ie += (long long)mn * terms;
+    }
+    if (labeled || ni > 1) ie += (long long)s[drv].len * (ni - 1 + (labeled ? 1 : 0));
+    long long total = 0;
+    if (nd == 0 || direct <= ie) {
+        const Slice d = s[drv];
+        unsigned long long c = 0;
+        for (int base = 0; base < d.len; base += 32) {
+            const int idx = base + lane;
+            bool ok = idx < d.len;
+            if (ok) {
+                const int x = __ldg(d.p + idx);
+                for (int i = 0; i < ni && ok; ++i)
+                    if (i != drv) ok = contains_g(s[i].p, s[i].len, x);
+                for (int j = 0; j < nd && ok; ++j) ok = !contains_g(s[ni + j].p, s[ni + j].len, x);
+                if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
+            }
+            c += __popc(__ballot_sync(PG_FULL, ok));
+        }
+        total = (long long)c;
+    } else {
+        // |A \ (B1 u ... u Bd)| = sum over T subset of diffs of (-1)^|T| |A n B_T|
+        for (unsigned T = 0; T < (1u << nd); ++T) {
+            int dd = drv;
+            for (int j = 0; j < nd; ++j)
+                if ((T >> j & 1) && s[ni + j].len < s[dd].len) dd = ni + j;
+            const Slice d = s[dd];
+            long long term;
+            if (ni == 1 && T == 0 && !labeled) {
+                term = d.len;
+            } else {
+                unsigned long long c = 0;
+                for (int base = 0; base < d.len; base += 32) {
+                    const int idx = base + lane;
+                    bool ok = idx < d.len;
+                    if (ok) {
+                        const int x = __ldg(d.p + idx);
+                        for (int i = 0; i < ni && ok; ++i)
+                            if (i != dd) ok = contains_g(s[i].p, s[i].len, x);
+                        for (int j = 0; j < nd && ok; ++j)
+                            if ((T >> j & 1) && ni + j != dd) ok = contains_g(s[ni + j].p, s[ni + j].len, x);
+                        if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
+                    }
+                    c += __popc(__ballot_sync(PG_FULL, ok));
+                }
+                term = (long long)c;
+            }
+            total += (__popc(T) & 1) ? -term : term;
+        }
+    }
+    // injectivity: remove earlier images that fall inside S
+    // (earlier images are pairwise distinct, so each is removed at most once)
+    bool in = false;
+    if (lane < L.n_excl) {
+        const int x = m[L.excl_src[lane]];
+        in = x > r.lo && x < r.hi;
+        for (int i = 0; i < ni && in; ++i) in = contains_g(s[i].p, s[i].len, x);
+        for (int j = 0; j < nd && in; ++j) in = !contains_g(s[ni + j].p, s[ni + j].len, x);
+        if (in && labeled) in = (__ldg(&g.vinfo[x].w) == L.label);
+    }
+    total -= (long long)__popc(__ballot_sync(PG_FULL, in));
+    return (unsigned long long)total;
+}
+
+__device__ unsigned __int128 run_task(const GenericArgs &a, int v, const PgOrder &ord, int *wbuf, int lane) {
+    const DevGraph &g = a.g;
+    const int L = ord.n_levels;
+    const int4 v0 = __ldg(&g.vinfo[v]);
+    if (ord.lv[0].label >= 0 && v0.w != ord.lv[0].label) return 0;
+    if (L == 1) return 1;
+    int m[PGP_MAXK];
+    int sz[PGP_MAXK], idx[PGP_MAXK];
+    m[0] = v;
+    unsigned __int128 total = 0;
+    int l = 1;
+    for (;;) {
+        if (l == L - 1) {
+            const unsigned long long c = count_last(g, ord.lv[l], m, lane);
+            total += choose_u128(c, ord.lv[l].group);
+        } else {
+            sz[l] = fill_level(g, ord.lv[l], m, wbuf + a.lvl_off[l], lane);
+            idx[l] = 0;
+        }
+        // advance to the next unexplored candidate
+        while (l >= 1 && (l == L - 1 || idx[l] >= sz[l])) --l;
+        if (l < 1) break;
+        m[l] = wbuf[a.lvl_off[l] + idx[l]];
+        ++idx[l];
+        ++l;
+    }
+    return total;
+}
+
+__global__ void __launch_bounds__(kBlock) k_count_generic(GenericArgs a) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    int *wbuf = a.scratch + gw * a.warp_stride;
+    unsigned __int128 acc = 0;
+    for (;;) {
+        unsigned long long t = (unsigned long long)gw;
+        if (a.persistent) {
+            if (lane == 0) t = atomicAdd(a.queue, 1ull);
+            t = __shfl_sync(PG_FULL, t, 0);
+        }
+        if (t >= a.n_tasks) break;
+        const int v = (int)(t / (unsigned long long)a.n_orders);
+        const int o = (int)(t % (unsigned long long)a.n_orders);
+        acc += run_task(a, v, a.orders[o], wbuf, lane);
+        if (!a.persistent) break;
+    }
+    if (lane == 0 && acc) atomic_add_u128(a.counts, acc);
+}
+
+int generic_grid(const pg_graph *g) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_generic, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * g->num_sms;
+}
+
+// Per-warp buffer layout: level l (1 <= l < n_levels - 1) gets max out-degree
+// ints when its candidates lie in the start's out-neighbourhood, else max
+// degree ints (each rounded to 32).
+long long level_layout(const pg_graph *g, const pg_plan *p, long long *off) {
+    const long long cap_out = (g->max_out + 31) & ~31ll, cap_all = (g->max_deg + 31) & ~31ll;
+    long long total = 0;
+    for (int l = 0; l < PGP_MAXK; ++l) {
+        off[l] = total;
+        bool any = false, all_out = true;
+        for (auto &o : p->h.orders)
+            if (l >= 1 && l < o.n_levels - 1) {
+                any = true;
+                all_out &= o.lv[l].out_bounded != 0;
+            }
+        if (any) total += all_out ? cap_out : cap_all;
+    }
+    return total;
+}
+
+unsigned long long n_tasks_of(const pg_graph *g, const pg_plan *p) {
+    return (unsigned long long)g->n * (unsigned long long)p->h.orders.size();
+}
+
+int grid_of(const pg_graph *g, const pg_plan *p, bool persistent) {
+    if (persistent) return generic_grid(g);
+    const unsigned long long w = n_tasks_of(g, p);
+    return (int)((w + kWarpsPerBlock - 1) / kWarpsPerBlock);
+}
+
+}  // namespace
+
+size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persistent) {
+    long long off[PGP_MAXK];
+    const long long per_warp = level_layout(g, p, off);
+    return (size_t)grid_of(g, p, persistent) * kWarpsPerBlock * (size_t)per_warp * sizeof(int);
+}
+
+int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev, int queue_slot,
+                      bool persistent, cudaStream_t s) {
+    if (g->n == 0 || p->h.orders.empty()) return PG_OK;
+    GenericArgs a;
+    a.g = g->d;
+    a.orders = p->d_orders;
+    a.n_orders = (int)p->h.orders.size();
+    a.warp_stride = level_layout(g, p, a.lvl_off);
+    a.scratch = (int *)g->scratch;
+    a.queue = g->queues + queue_slot;
+    a.n_tasks = n_tasks_of(g, p);
+    a.persistent = persistent ? 1 : 0;
+    a.counts = counts_dev;
+    if (persistent) PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+    k_count_generic<<<grid_of(g, p, persistent), kBlock, 0, s>>>(a);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}

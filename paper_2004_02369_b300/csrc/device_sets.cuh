@@ -1,0 +1,76 @@
+// Device helpers for sorted-set work on degree-ranked adjacency lists.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pg_internal.h"
+
+#define PG_FULL 0xffffffffu
+
+struct Slice {
+    const int *p;
+    int len;
+};
+
+__device__ __forceinline__ const int *adj_of(const DevGraph &g, int4 vi) {
+    return g.adj + ((size_t)(unsigned)vi.x << 2);
+}
+
+// first index i in a[0, len) with a[i] >= x
+__device__ __forceinline__ int lower_bound_g(const int *__restrict__ a, int len, int x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool contains_g(const int *__restrict__ a, int len, int x) {
+    // branch-reduced search: halve while len > 1
+    const int *base = a;
+    int n = len;
+    if (n <= 0) return false;
+    while (n > 1) {
+        const int half = n >> 1;
+        base = (__ldg(base + half - 1) < x) ? base + half : base;
+        n -= half;
+    }
+    return __ldg(base) == x;
+}
+
+// Restrict a sorted list to values in the open interval (lo, hi).
+__device__ __forceinline__ Slice bound_slice(const int *p, int len, int lo, int hi) {
+    const int b = lo < 0 ? 0 : lower_bound_g(p, len, lo + 1);
+    const int e = hi == 0x7fffffff ? len : lower_bound_g(p, len, hi);
+    Slice s;
+    s.p = p + b;
+    s.len = e > b ? e - b : 0;
+    return s;
+}
+
+// 128-bit exact accumulation into two 64-bit words (low, high).
+__device__ __forceinline__ void atomic_add_u128(unsigned long long *c, unsigned __int128 x) {
+    const unsigned long long lo = (unsigned long long)x;
+    unsigned long long hi = (unsigned long long)(x >> 64);
+    if (lo) {
+        const unsigned long long old = atomicAdd(c, lo);
+        if (old + lo < old) hi += 1;
+    }
+    if (hi) atomicAdd(c + 1, hi);
+}
+
+// C(s, g) exactly, g <= 8, in 128 bits.
+__device__ __forceinline__ unsigned __int128 choose_u128(unsigned long long s, int g) {
+    if (g == 1) return s;
+    if ((long long)s < g) return 0;
+    unsigned __int128 r = 1;
+    for (int i = 0; i < g; ++i) r = r * (unsigned __int128)(s - i) / (unsigned __int128)(i + 1);
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(PG_FULL, x, o);
+    return x;
+}

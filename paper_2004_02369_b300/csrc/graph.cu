@@ -1,0 +1,231 @@
+// Graph residency: validation, degree ranking and CSR rewrite on the device.
+//
+// Section 5.5: the data graph is kept as sorted adjacency lists.
+// Section 5.2: vertices are ordered by degree so that, matched high-to-low,
+// a high-degree start vertex only extends to its few higher-ranked
+// neighbours.  Rank = position in (degree descending, original id
+// ascending); a smaller rank means a higher degree.
+//
+// Sorting uses CUB (header library shipped with the CUDA toolkit) radix sort
+// and scan: this runs once per graph load, outside the matching path.
+#include <cub/cub.cuh>
+
+#include "pg_internal.h"
+
+namespace {
+
+constexpr int kBlock = 256;
+
+// Per-vertex validation: ids in range, no loop, strictly ascending, and the
+// reverse edge present.  err bit 1: range, 2: loop, 4: order, 8: asymmetric,
+// 16: negative label.
+__global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t *labels, int64_t n,
+                           unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const int64_t b = off[u], e = off[u + 1];
+        unsigned bad = 0;
+        if (lane == 0 && labels && labels[u] < 0) bad |= 16;
+        for (int64_t i = b + lane; i < e; i += 32) {
+            const int32_t x = adj[i];
+            if (x < 0 || x >= n) { bad |= 1; continue; }
+            if (x == u) bad |= 2;
+            if (i > b && adj[i - 1] >= x) bad |= 4;
+            // reverse edge u in adj(x)
+            int64_t lo = off[x], hi = off[x + 1];
+            while (lo < hi) {
+                int64_t mid = (lo + hi) >> 1;
+                if (adj[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= off[x + 1] || adj[lo] != u) bad |= 8;
+        }
+        if (bad) atomicOr(err, bad);
+    }
+}
+
+__global__ void k_check_offsets(const int64_t *off, int64_t n, int64_t nnz, unsigned *err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(err, 32u);
+    if (i < n && off[i + 1] < off[i]) atomicOr(err, 32u);
+}
+
+__global__ void k_degree_keys(const int64_t *off, int64_t n, unsigned long long *keys) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const unsigned long long deg = (unsigned long long)(off[v + 1] - off[v]);
+    keys[v] = ((0xffffffffull - deg) << 32) | (unsigned long long)v;
+}
+
+// rank[orig] = r ; pdeg[r] = padded degree ; udeg[r] = degree
+__global__ void k_rank(const unsigned long long *sorted, const int64_t *off, int64_t n, int *rank,
+                       int64_t *pdeg, int64_t *udeg) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int v = (int)(sorted[r] & 0xffffffffull);
+    rank[v] = (int)r;
+    const int64_t d = off[v + 1] - off[v];
+    udeg[r] = d;
+    pdeg[r] = (d + 3) & ~3ll;
+}
+
+__global__ void k_edge_keys(const int64_t *off, const int32_t *adj, int64_t n, const int *rank,
+                            unsigned long long *keys) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        const unsigned long long ru = (unsigned long long)rank[u] << 32;
+        for (int64_t i = off[u] + lane; i < off[u + 1]; i += 32)
+            keys[i] = ru | (unsigned long long)(unsigned)rank[adj[i]];
+    }
+}
+
+// Sorted (rank_u, rank_w) keys -> padded lists.  ustart[r] = first key of r.
+__global__ void k_scatter(const unsigned long long *keys, int64_t nnz, const int64_t *ustart,
+                          const int64_t *pstart, int *adj_out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nnz) return;
+    const unsigned long long k = keys[i];
+    const int r = (int)(k >> 32);
+    adj_out[pstart[r] + (i - ustart[r])] = (int)(k & 0xffffffffull);
+}
+
+__global__ void k_finish(int *adj, const int64_t *pstart, const int64_t *udeg, const int64_t *pdeg,
+                         const unsigned long long *sorted, const int32_t *labels, int64_t n,
+                         int4 *vinfo, int *maxes) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t s = pstart[r], d = udeg[r];
+    for (int64_t j = d; j < pdeg[r]; ++j) adj[s + j] = PG_PAD;
+    // out-degree: neighbours with rank < r
+    int lo = 0, hi = (int)d;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (adj[s + mid] < r) lo = mid + 1; else hi = mid;
+    }
+    const int orig = (int)(sorted[r] & 0xffffffffull);
+    const int lab = labels ? labels[orig] : 0;
+    vinfo[r] = make_int4((int)(unsigned)(s >> 2), (int)d, lo, lab);
+    atomicMax(maxes + 0, (int)d);
+    atomicMax(maxes + 1, lo);
+    atomicMax(maxes + 2, lab);
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 0x7fffffff) g = 0x7fffffff;
+    return (unsigned)g;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+}  // namespace
+
+int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int64_t nnz,
+                   const int32_t *d_labels, cudaStream_t s) {
+    const int64_t n = g->n;
+    DevBuf err_b, vkeys, vkeys2, tmp, udeg, pdeg, ustart, pstart, ekeys, ekeys2, maxes_b;
+    PG_CUDA(cudaMalloc(&err_b.p, sizeof(unsigned)));
+    unsigned *err = (unsigned *)err_b.p;
+    PG_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    k_check_offsets<<<grid_for(n + 1, kBlock), kBlock, 0, s>>>(d_off, n, nnz, err);
+    unsigned herr = 0;
+    PG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    if (herr) return pg_set_error(PG_EINVAL, "offsets must start at 0, end at nnz and be non-decreasing");
+    if (n > 0) {
+        k_validate<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, d_labels, n, err);
+        PG_CUDA(cudaGetLastError());
+        PG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+    }
+    if (herr & 1) return pg_set_error(PG_EINVAL, "adjacency entry out of range");
+    if (herr & 2) return pg_set_error(PG_EINVAL, "self loop in data graph");
+    if (herr & 4) return pg_set_error(PG_EINVAL, "adjacency list not strictly ascending (unsorted or duplicate)");
+    if (herr & 8) return pg_set_error(PG_EINVAL, "asymmetric edge: graph must be undirected");
+    if (herr & 16) return pg_set_error(PG_EINVAL, "negative vertex label");
+
+    const int64_t nn = n > 0 ? n : 1;
+    PG_CUDA(cudaMalloc(&vkeys.p, nn * sizeof(unsigned long long)));
+    PG_CUDA(cudaMalloc(&vkeys2.p, nn * sizeof(unsigned long long)));
+    PG_CUDA(cudaMalloc(&udeg.p, nn * sizeof(int64_t)));
+    PG_CUDA(cudaMalloc(&pdeg.p, nn * sizeof(int64_t)));
+    PG_CUDA(cudaMalloc(&ustart.p, nn * sizeof(int64_t)));
+    PG_CUDA(cudaMalloc(&pstart.p, nn * sizeof(int64_t)));
+    PG_CUDA(cudaMalloc(&g->rank, nn * sizeof(int)));
+    PG_CUDA(cudaMalloc(&g->vinfo, nn * sizeof(int4)));
+    PG_CUDA(cudaMalloc(&maxes_b.p, 3 * sizeof(int)));
+    int *maxes = (int *)maxes_b.p;
+    PG_CUDA(cudaMemsetAsync(maxes, 0, 3 * sizeof(int), s));
+
+    // rank by (degree desc, id asc)
+    k_degree_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(d_off, n, (unsigned long long *)vkeys.p);
+    size_t tmp_bytes = 0, need = 0;
+    cub::DeviceRadixSort::SortKeys(nullptr, need, (unsigned long long *)vkeys.p,
+                                   (unsigned long long *)vkeys2.p, (int64_t)n, 0, 64, s);
+    tmp_bytes = need;
+    cub::DeviceScan::ExclusiveSum(nullptr, need, (int64_t *)pdeg.p, (int64_t *)pstart.p, (int64_t)n, s);
+    tmp_bytes = std::max(tmp_bytes, need);
+    const int64_t ne = nnz > 0 ? nnz : 1;
+    int bits_n = 1;
+    while ((1ll << bits_n) < n) ++bits_n;
+    cub::DeviceRadixSort::SortKeys(nullptr, need, (unsigned long long *)nullptr,
+                                   (unsigned long long *)nullptr, (int64_t)nnz, 0, 32 + bits_n, s);
+    tmp_bytes = std::max(tmp_bytes, need);
+    PG_CUDA(cudaMalloc(&tmp.p, tmp_bytes + 16));
+
+    need = tmp_bytes;
+    PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, need, (unsigned long long *)vkeys.p,
+                                           (unsigned long long *)vkeys2.p, (int64_t)n, 0, 64, s));
+    const unsigned long long *sorted = (const unsigned long long *)vkeys2.p;
+    k_rank<<<grid_for(n, kBlock), kBlock, 0, s>>>(sorted, d_off, n, g->rank, (int64_t *)pdeg.p,
+                                                  (int64_t *)udeg.p);
+    need = tmp_bytes;
+    PG_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, need, (int64_t *)pdeg.p, (int64_t *)pstart.p, (int64_t)n, s));
+    need = tmp_bytes;
+    PG_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, need, (int64_t *)udeg.p, (int64_t *)ustart.p, (int64_t)n, s));
+
+    // padded size = last start + last padded degree
+    int64_t last_start = 0, last_pdeg = 0;
+    if (n > 0) {
+        PG_CUDA(cudaMemcpyAsync(&last_start, (int64_t *)pstart.p + (n - 1), sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaMemcpyAsync(&last_pdeg, (int64_t *)pdeg.p + (n - 1), sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+    }
+    g->adj_entries = last_start + last_pdeg;
+    if (g->adj_entries / 4 > 0xffffffffll) return pg_set_error(PG_EINVAL, "graph too large for 32-bit list starts");
+    PG_CUDA(cudaMalloc(&g->adj, (g->adj_entries > 0 ? g->adj_entries : 4) * sizeof(int)));
+
+    // rewrite adjacency in ranks, sort by (rank_u, rank_w)
+    PG_CUDA(cudaMalloc(&ekeys.p, ne * sizeof(unsigned long long)));
+    PG_CUDA(cudaMalloc(&ekeys2.p, ne * sizeof(unsigned long long)));
+    if (nnz > 0) {
+        k_edge_keys<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, n, g->rank,
+                                                                (unsigned long long *)ekeys.p);
+        need = tmp_bytes;
+        PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, need, (unsigned long long *)ekeys.p,
+                                               (unsigned long long *)ekeys2.p, (int64_t)nnz, 0, 32 + bits_n, s));
+        k_scatter<<<grid_for(nnz, kBlock), kBlock, 0, s>>>((unsigned long long *)ekeys2.p, nnz,
+                                                           (int64_t *)ustart.p, (int64_t *)pstart.p, g->adj);
+    }
+    if (n > 0)
+        k_finish<<<grid_for(n, kBlock), kBlock, 0, s>>>(g->adj, (int64_t *)pstart.p, (int64_t *)udeg.p,
+                                                        (int64_t *)pdeg.p, sorted, d_labels, n, g->vinfo, maxes);
+    PG_CUDA(cudaGetLastError());
+    int hm[3] = {0, 0, 0};
+    PG_CUDA(cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    g->max_deg = hm[0];
+    g->max_out = hm[1];
+    g->n_labels = d_labels ? hm[2] + 1 : 0;
+    g->bytes_device = (int64_t)(nn * (sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int));
+    return PG_OK;
+}

@@ -1,0 +1,81 @@
+// Internal types shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pg.h"
+#include "plan.h"
+
+// Device view of a resident graph.  Vertices are degree-ranked ids (rank 0 =
+// highest degree; ties by original id).  vinfo[v] = {start / 4, degree,
+// out-degree, label}: the list of v is adj[4*start4 .. 4*start4 + degree),
+// sorted ascending and padded with PG_PAD up to a multiple of 4 entries (16
+// bytes); out-degree counts the neighbours with smaller rank (higher degree).
+struct DevGraph {
+    const int4 *vinfo;
+    const int *adj;
+    int n;
+    int max_deg;
+    int max_out;
+    int labeled;
+};
+
+#define PG_PAD 0x7fffffff
+
+struct pg_graph {
+    DevGraph d{};
+    int4 *vinfo = nullptr;
+    int *adj = nullptr;
+    int *rank = nullptr; // original id -> rank
+    int64_t n = 0, m = 0, adj_entries = 0;
+    int64_t max_deg = 0, max_out = 0;
+    int32_t labeled = 0, n_labels = 0;
+    int device = 0;
+    int num_sms = 0;
+    // scratch arena (grown on demand) and per-launch work-queue counters
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    unsigned long long *queues = nullptr; // PG_MAX_QUEUES counters
+    unsigned long long *tmp_counts = nullptr; // 2 * PG_MAX_QUEUES words
+    int64_t bytes_device = 0;
+};
+
+#define PG_MAX_QUEUES 64
+
+struct pg_plan {
+    PgPlanHost h;
+    PgOrder *d_orders = nullptr; // device copy of h.orders
+    int kernel_auto = PG_KERNEL_GENERIC;
+};
+
+// error reporting (thread-local message)
+int pg_set_error(int code, const std::string &msg);
+int pg_cuda_error(cudaError_t e, const char *what);
+
+#define PG_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return pg_cuda_error(_e, #call);        \
+    } while (0)
+
+// graph.cu
+int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int64_t nnz,
+                   const int32_t *d_labels, cudaStream_t s);
+
+// scratch management (api.cu)
+int pg_ensure_scratch(pg_graph *g, size_t bytes, cudaStream_t s);
+int pg_plan_upload(pg_plan *p);
+
+// count_generic.cu (persistent = dynamic task queue over a resident grid;
+// otherwise one warp per task, one launch per pattern)
+int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev,
+                      int queue_slot, bool persistent, cudaStream_t s);
+size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persistent);
+
+// count_clique.cu: sizes kmin..kmax in one launch, counts_dev[2*(k-kmin)]
+int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
+                     int queue_slot, cudaStream_t s);
+size_t pg_clique_scratch_bytes(const pg_graph *g);

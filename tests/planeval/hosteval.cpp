@@ -1,0 +1,135 @@
+// Test aid: a sequential CPU interpreter of the compiled level program.
+//
+// It links the library's host plan compiler (plan.cpp) and walks every
+// (start vertex, matching order) task with plain std::vector set operations,
+// so that the plan compiler can be checked against the oracle on machines
+// without a GPU.  It is not part of the library and never runs on its path.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/pg.h"
+#include "../../paper_2004_02369_b300/csrc/plan.h"
+
+namespace {
+
+struct RankedGraph {
+    int n = 0;
+    std::vector<int64_t> off;
+    std::vector<int32_t> adj, label;
+};
+
+RankedGraph rank_graph(const int64_t *off, int64_t n, const int32_t *adj, const int32_t *labels) {
+    std::vector<int> order(n), rank(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (off[a + 1] - off[a]) > (off[b + 1] - off[b]);
+    });
+    for (int r = 0; r < n; ++r) rank[order[r]] = r;
+    RankedGraph g;
+    g.n = (int)n;
+    g.off.assign(n + 1, 0);
+    g.label.assign(n, 0);
+    for (int r = 0; r < n; ++r) {
+        int v = order[r];
+        g.off[r + 1] = g.off[r] + (off[v + 1] - off[v]);
+        if (labels) g.label[r] = labels[v];
+    }
+    g.adj.resize(g.off[n]);
+    for (int r = 0; r < n; ++r) {
+        int v = order[r];
+        int64_t w = g.off[r];
+        for (int64_t e = off[v]; e < off[v + 1]; ++e) g.adj[w++] = rank[adj[e]];
+        std::sort(g.adj.begin() + g.off[r], g.adj.begin() + g.off[r + 1]);
+    }
+    return g;
+}
+
+bool has(const RankedGraph &g, int v, int x) {
+    return std::binary_search(g.adj.begin() + g.off[v], g.adj.begin() + g.off[v + 1], x);
+}
+
+std::vector<int> level_set(const RankedGraph &g, const PgLevel &L, const int *m) {
+    int lo = -1, hi = 0x7fffffff;
+    for (int i = 0; i < L.n_lo; ++i) lo = std::max(lo, m[L.lo_src[i]]);
+    for (int i = 0; i < L.n_hi; ++i) hi = std::min(hi, m[L.hi_src[i]]);
+    std::vector<int> out;
+    const int a = m[L.int_src[0]];
+    for (int64_t e = g.off[a]; e < g.off[a + 1]; ++e) {
+        int x = g.adj[e];
+        if (x <= lo || x >= hi) continue;
+        bool ok = true;
+        for (int i = 1; i < L.n_int && ok; ++i) ok = has(g, m[L.int_src[i]], x);
+        for (int i = 0; i < L.n_diff && ok; ++i) ok = !has(g, m[L.diff_src[i]], x);
+        for (int i = 0; i < L.n_excl && ok; ++i) ok = x != m[L.excl_src[i]];
+        if (ok && L.label >= 0) ok = g.label[x] == L.label;
+        if (ok) out.push_back(x);
+    }
+    return out;
+}
+
+unsigned __int128 choose(uint64_t s, int k) {
+    if ((int64_t)s < k) return 0;
+    unsigned __int128 r = 1;
+    for (int i = 0; i < k; ++i) r = r * (s - i) / (i + 1);
+    return r;
+}
+
+unsigned __int128 walk(const RankedGraph &g, const PgOrder &o, int l, int *m) {
+    const PgLevel &L = o.lv[l];
+    std::vector<int> s = level_set(g, L, m);
+    if (l == o.n_levels - 1) return choose(s.size(), L.group);
+    unsigned __int128 t = 0;
+    for (int x : s) {
+        m[l] = x;
+        t += walk(g, o, l + 1, m);
+    }
+    return t;
+}
+
+}  // namespace
+
+extern "C" int pe_count(const int64_t *off, int64_t n, const int32_t *adj, const int32_t *labels,
+                        const pg_pattern_desc *d, uint64_t *out2, int32_t *info) {
+    PgPattern p;
+    p.k = d->k;
+    for (int i = 0; i < d->n_edges; ++i) {
+        int u = d->edges[2 * i], w = d->edges[2 * i + 1];
+        p.rel[u][w] = p.rel[w][u] = 1;
+    }
+    for (int i = 0; i < d->n_anti; ++i) {
+        int u = d->anti_edges[2 * i], w = d->anti_edges[2 * i + 1];
+        p.rel[u][w] = p.rel[w][u] = 2;
+    }
+    for (int u = 0; u < d->k; ++u) {
+        p.label[u] = d->labels ? d->labels[u] : -1;
+        p.anti_vertex[u] = d->anti_vertex ? d->anti_vertex[u] : 0;
+    }
+    PgPlanHost h;
+    std::string err;
+    int rc = pg_plan_compile(p, d->vertex_induced != 0, h, err);
+    if (rc) return rc;
+    RankedGraph g = rank_graph(off, n, adj, labels);
+    unsigned __int128 total = 0;
+    int m[PGP_MAXK];
+    for (const PgOrder &o : h.orders) {
+        for (int v = 0; v < g.n; ++v) {
+            if (o.lv[0].label >= 0 && g.label[v] != o.lv[0].label) continue;
+            if (o.n_levels == 1) { total += 1; continue; }
+            m[0] = v;
+            total += walk(g, o, 1, m);
+        }
+    }
+    out2[0] = (uint64_t)total;
+    out2[1] = (uint64_t)(total >> 64);
+    if (info) {
+        info[0] = (int32_t)h.orders.size();
+        info[1] = (int32_t)h.core_mask;
+        info[2] = h.counted_group;
+        info[3] = h.orders.empty() ? 0 : h.orders[0].n_levels;
+    }
+    return 0;
+}
