@@ -247,6 +247,11 @@ def run_ours(args):
     ms_step_max = max_over_ranks(world, ms_step, dev)
     value = sum_over_ranks(world, matches, dev) / (ms_step_max / 1e3)
 
+    if args.only_kernel:
+        if rank == 0:
+            print(json.dumps({"only_kernel": True, "ms_per_step": ms_step, "counts": got}), flush=True)
+        return 0
+
     # ---- end to end: host CSR in pinned memory -> load -> count -> host ----
     off_h = torch.from_numpy(g.offsets).pin_memory()
     adj_h = torch.from_numpy(g.adj).pin_memory()
@@ -336,6 +341,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kernel", type=int, default=0, help="PG_KERNEL_* (0 = auto)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    ap.add_argument("--only-kernel", action="store_true",
+                    help="time the counting steps only (for profiler runs)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch from an ncu capture of this kernel")
     args = ap.parse_args()

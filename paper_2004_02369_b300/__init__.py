@@ -2,7 +2,7 @@
 
 Argument marshalling only: every step of matching runs in the library's CUDA
 kernels.  The shared library must have been built in-tree
-(``python -m paper_2004_02369_b300.build``); importing this package without it
+(``python paper_2004_02369_b300/build.py``); importing this package without it
 raises ImportError instead of falling back to anything else.
 
 PyTorch supplies device memory and streams: graph inputs may be torch CUDA
@@ -24,7 +24,7 @@ KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_MOTIF4_F
 MAX_PATTERN = 8
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2004_02369_b300.build`")
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2004_02369_b300/build.py`")
 
 
 class PgError(RuntimeError):

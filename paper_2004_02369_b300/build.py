@@ -1,6 +1,8 @@
 """Build libpg.so (CUDA, sm_103a) in-tree with nvcc.
 
-Usage: python -m paper_2004_02369_b300.build [--force]
+Usage: python paper_2004_02369_b300/build.py [--force] [-v]
+
+(Run it by path: importing the package loads libpg.so, which this script builds.)
 """
 from __future__ import annotations
 
