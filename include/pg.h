@@ -184,6 +184,34 @@ int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *coun
 int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev,
                 int32_t kernel, void *stream);
 
+/*
+ * pg_count_cliques_noalloc - k-clique counts for every k in kmin..kmax
+ * (3 <= kmin <= kmax <= 8), computed by the same kernel as PG_KERNEL_CLIQUE,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate while they count,
+ * e.g. a process whose device memory is reserved up front by another
+ * allocator (where a cudaMalloc at query time can fail or fragment the pool)
+ * or a latency-bound caller that cannot take the implicit synchronisation of
+ * cudaMalloc / cudaFree.
+ *   g           a graph loaded earlier (its memory was allocated at load).
+ *   counts_dev  uint64[2 * (kmax - kmin + 1)], device, caller-owned: the
+ *               (low, high) words of the count of k-cliques at index
+ *               2 * (k - kmin); zeroed by the call on `stream`.
+ * Scratch comes from a fixed 32 MiB array compiled into the library (every
+ * device that loads libpg holds it until the process exits).  The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the array and each call clears what must start at zero, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  Asynchronous: only enqueues work on `stream`.
+ * Errors: PG_EINVAL (NULL argument, bad sizes, graph on another device, or a
+ * graph whose maximum out-degree needs per-warp slabs that do not fit the
+ * array for at least one 4-warp block per SM: roughly out-degree above 1200
+ * on a 148-SM B300), PG_EDEVICE.  Never calls cudaMalloc or cudaFree.
+ */
+int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax, uint64_t *counts_dev,
+                             void *stream);
+
 /* pg_last_error - message of the last failed call on this host thread. */
 const char *pg_last_error(void);
 

@@ -68,6 +68,7 @@ _lib.pg_free_plan.argtypes = [_vp]
 _lib.pg_free_plan.restype = None
 _lib.pg_count.argtypes = [_vp, _vp, _i32, _vp, _vp]
 _lib.pg_count_ex.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp]
+_lib.pg_count_cliques_noalloc.argtypes = [_vp, _i32, _i32, _vp, _vp]
 _lib.pg_last_error.restype = ctypes.c_char_p
 
 
@@ -229,6 +230,15 @@ def count_async(graph: Graph, plans, out, kernel: int = KERNEL_AUTO, stream=None
         raise ValueError("out must be a CUDA tensor with 2*len(plans) 64-bit elements")
     _check(_lib.pg_count_ex(graph.handle, _plan_array(plans), len(plans), out.data_ptr(),
                             kernel, _stream_ptr(stream)))
+
+
+def count_cliques_noalloc(graph: Graph, kmin: int, kmax: int, out, stream=None):
+    """k-clique counts for k = kmin..kmax into ``out`` (torch CUDA int64,
+    2*(kmax-kmin+1) elements) using the library's fixed scratch array: no
+    device allocation.  Calls that overlap on the GPU race (shared array)."""
+    if out.numel() < 2 * (kmax - kmin + 1) or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor with 2*(kmax-kmin+1) 64-bit elements")
+    _check(_lib.pg_count_cliques_noalloc(graph.handle, kmin, kmax, out.data_ptr(), _stream_ptr(stream)))
 
 
 def decode_counts(words) -> list[int]:

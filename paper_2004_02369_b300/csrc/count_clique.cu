@@ -230,3 +230,33 @@ int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
+
+// Launch of the same kernel on caller-supplied scratch: `queue` is one zeroed
+// 64-bit counter and `slabs` holds `max_warps` per-warp slabs of
+// pg_clique_slab_bytes() bytes; the grid is cut so that no warp indexes a
+// slab beyond max_warps.  Used by the entry point that allocates nothing.
+size_t pg_clique_slab_bytes(const pg_graph *g) {
+    int gws;
+    return (size_t)slab_words(g, &gws) * sizeof(unsigned);
+}
+
+int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
+                        unsigned long long *queue, void *slabs, long long max_warps, cudaStream_t s) {
+    if (kmin < 3 || kmax > kMaxK || kmin > kmax) return pg_set_error(PG_EINVAL, "clique sizes must be 3..8");
+    if (g->n == 0) return PG_OK;
+    CliqueArgs a;
+    a.g = g->d;
+    a.kmin = kmin;
+    a.kmax = kmax;
+    a.slab_words = slab_words(g, &a.gws);
+    a.gscratch = a.slab_words ? (unsigned *)slabs : nullptr;
+    a.queue = queue;
+    a.n = (int)g->n;
+    a.counts = counts_dev;
+    long long blocks = clique_grid(g);
+    if (a.slab_words && blocks * kWarps > max_warps) blocks = max_warps / kWarps;
+    if (blocks < 1) return pg_set_error(PG_EINVAL, "scratch holds fewer slabs than one block needs");
+    k_count_clique<<<(unsigned)blocks, kBlock, 0, s>>>(a);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}

@@ -44,6 +44,7 @@ struct pg_graph {
 };
 
 #define PG_MAX_QUEUES 64
+#define PG_STATIC_SCRATCH_BYTES (32u << 20) // fixed scratch of pg_count_cliques_noalloc
 
 struct pg_plan {
     PgPlanHost h;
@@ -79,3 +80,6 @@ size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persis
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
                      int queue_slot, cudaStream_t s);
 size_t pg_clique_scratch_bytes(const pg_graph *g);
+size_t pg_clique_slab_bytes(const pg_graph *g);
+int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
+                        unsigned long long *queue, void *slabs, long long max_warps, cudaStream_t s);
