@@ -205,9 +205,9 @@ int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *c
  * calls that overlap on the GPU (other streams, other host threads) race:
  * serialise them.  Asynchronous: only enqueues work on `stream`.
  * Errors: PG_EINVAL (NULL argument, bad sizes, graph on another device, or a
- * graph whose maximum out-degree needs per-warp slabs that do not fit the
- * array for at least one 4-warp block per SM: roughly out-degree above 1200
- * on a 148-SM B300), PG_EDEVICE.  Never calls cudaMalloc or cudaFree.
+ * graph whose maximum out-degree needs per-block slabs that do not fit the
+ * array for at least one block per SM: roughly out-degree above 1300 on a
+ * 148-SM B300), PG_EDEVICE.  Never calls cudaMalloc or cudaFree.
  */
 int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax, uint64_t *counts_dev,
                              void *stream);

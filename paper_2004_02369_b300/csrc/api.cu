@@ -114,6 +114,7 @@ extern "C" void pg_free_graph(pg_graph *g) {
     if (g->scratch) cudaFree(g->scratch);
     if (g->queues) cudaFree(g->queues);
     if (g->tmp_counts) cudaFree(g->tmp_counts);
+    if (g->heavy) cudaFree(g->heavy);
     delete g;
 }
 

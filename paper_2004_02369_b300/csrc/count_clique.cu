@@ -8,255 +8,432 @@
 // N+(v) with the out-lists of already bound vertices, restricted by the
 // order bounds, and the last level is counted by cardinality (Section 5.1).
 //
-// B300 mapping: one warp per start vertex v, handed out by a device atomic
-// counter in rank order (highest degree first, Section 5.2).  The warp loads
-// N+(v) (d entries) and builds the bitmap rows R[i] = { j < i : N+(v)[j] in
-// N+(N+(v)[i]) } -- the level-1 intersections, each read once from L2/HBM --
-// in shared memory (or a per-warp global scratch slab when d exceeds the
-// shared-memory tile).  All deeper levels are word-wise ANDs of rows with
-// __popc for the counted level: a depth-D prefix (i, j, ...) leaves the
-// candidate set AND_s R[r_s], and its popcount is the number of
-// (D+2)-cliques through that prefix, so one traversal yields the counts of
-// every clique size up to kmax (several clique patterns share one launch).
-// Pairs (i, j in R[i]) are compacted through a per-warp queue so that all 32
-// lanes do work.
+// B300 mapping.  For a start vertex v with d = |N+(v)| the kernel builds the
+// bitmap rows R[i] = { j < i : N+(v)[j] in N+(N+(v)[i]) } (the level-1
+// intersections, each out-list read once from L2/HBM) and then runs every
+// deeper level as word-wise ANDs of rows; a prefix of p sub-graph vertices
+// with candidate set C leaves popc(C) cliques of size p + 2, so one traversal
+// counts every clique size kmin..kmax (several clique patterns share one
+// launch).
+//  * Heavy vertices (d > PG_CLIQUE_LIGHT_D, sorted by d, largest first) are
+//    processed by a whole CTA: 8 warps share one tile in shared memory (or a
+//    per-CTA global slab when the tile does not fit), take rows from a CTA
+//    counter for the row build and the traversal.
+//  * Light vertices are processed by single warps on per-warp tiles, taken in
+//    rank order (highest degree first, Section 5.2) from a device counter.
+//  * Traversal: warp-uniform loops over all levels but the last; the last
+//    level is lane-parallel over a compacted candidate list, so every lane
+//    does one popcount-of-AND row product per candidate.
 #include "device_sets.cuh"
 
 namespace {
 
-constexpr int kWarps = 4;
+constexpr int kWarps = 8;
 constexpr int kBlock = kWarps * 32;
-constexpr int kSmemD = 256;                 // out-degree handled in shared memory
-constexpr int kSmemWs = (kSmemD / 32) | 1;  // odd row stride (bank spread)
-constexpr int kQueue = 64;
+constexpr int kLightD = PG_CLIQUE_LIGHT_D;
+constexpr int kLightWs = (kLightD / 32) | 1;
+// per-warp light tile: list, rows, row start / length / element prefix
+constexpr int kLightTile = kLightD + kLightD * kLightWs + 3 * kLightD + 1;
+constexpr int kItems = 256; // queued (candidate set, vertex) products per warp
 constexpr int kMaxK = 8;
-
-struct WarpSmem {
-    int list[kSmemD];
-    unsigned rows[kSmemD * kSmemWs];
-    int qi[kQueue], qj[kQueue];
-};
+constexpr int kCtl = 8;
+constexpr size_t kSmemBudget = 96 * 1024;
 
 struct CliqueArgs {
     DevGraph g;
-    int kmin, kmax;       // counted clique sizes kmin..kmax (3 <= kmin <= kmax <= 8)
-    unsigned *gscratch;   // per-warp slab for out-degree > kSmemD
-    long long slab_words; // words per warp slab
-    int gws;              // row stride of the global slab
-    unsigned long long *queue;
+    int kmin, kmax;
+    const int *heavy;
+    int n_heavy;
     int n;
-    unsigned long long *counts; // 2 words per size kmin..kmax
+    int dpad, hws;           // heavy tile: list entries (padded), row stride in words
+    int heavy_in_smem;       // 1: heavy tile in shared memory, else in the CTA slab
+    int cws;                 // candidate bitmap stride (words)
+    int nslots;              // candidate bitmaps kept per warp between flushes
+    int region_words;        // shared union of the heavy tile and the light tiles
+    int warp_words;          // per-warp scratch: level bitmaps, slot ring, items
+    unsigned *slabs;         // per-CTA global slabs (may be null)
+    long long slab_words;
+    unsigned long long *queue; // [0] light cursor, [1] heavy cursor
+    unsigned long long *counts;
 };
 
-// Depth-first count below a prefix whose candidate set is AND of rows r[0..D).
-// Adds popc(candidates) to cnt[D] (the (D+2)-cliques in the full graph) and
-// recurses while D + 2 < kmax.
-// cnt[s] accumulates (s + 3)-cliques; dfs<D> adds to cnt[D - 1].
-template <int D>
-__device__ __forceinline__ void dfs(const unsigned *rows, int ws, int *r, int limit_bits, int kmax,
-                                    unsigned long long *cnt) {
-    if constexpr (D >= kMaxK - 1) {
+// Sub-graph tile of one start vertex: list = N+(v) (d entries), rows[i] =
+// bitmap of j < i adjacent to i, and per-row build bookkeeping.
+struct Tile {
+    int *list;
+    unsigned *rows;
+    int ws;
+    int *rstart; // list start of N+(list[i]) in 16-byte units
+    int *rlen;   // |N+(list[i])|
+    int *pre;    // exclusive prefix of per-row work elements (d + 1 entries)
+};
+
+// Per-warp traversal scratch.
+struct Walker {
+    unsigned *cbuf; // kMaxK level bitmaps of cws words
+    unsigned *ring; // nslots candidate bitmaps
+    int *items;     // kItems packed (slot << 16 | l)
+    int cws, nslots;
+    int m;          // queued items
+    int used;       // ring slots in use
+};
+
+// Group-wide barrier: the CTA for heavy vertices, the warp for light ones.
+template <bool CTA>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (CTA) __syncthreads(); else __syncwarp();
+}
+
+// Level-1 intersections of the tile (Section 5.1 candidate sets restricted to
+// N+(v)): rows[i] = { j < i : list[j] in N+(list[i]) }.  Work is flattened
+// over the group: row i costs |N+(list[i])| lookups of its elements in
+// list[0, i) (shared memory) or, when that list is much longer than i, i
+// lookups of list[j] in N+(list[i]) (global binary search).
+template <bool CTA>
+__device__ void build_rows(const DevGraph &g, const Tile &t, int d, int tid, int nthreads,
+                           unsigned long long &tri) {
+    const int lane = threadIdx.x & 31;
+    for (int i = tid; i < d; i += nthreads) {
+        const int4 ui = __ldg(&g.vinfo[t.list[i]]);
+        t.rstart[i] = ui.x;
+        t.rlen[i] = ui.z;
+    }
+    for (int w = tid; w < d * t.ws; w += nthreads) t.rows[w] = 0u;
+    group_sync<CTA>();
+    // exclusive prefix of per-row elements (first warp of the group)
+    if (tid < 32) {
+        int carry = 0;
+        for (int base = 0; base < d; base += 32) {
+            const int i = base + lane;
+            int e = 0;
+            if (i > 0 && i < d) {
+                const int du = t.rlen[i];
+                e = du <= 4 * i + 32 ? du : i;
+            }
+            int incl = e;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(PG_FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (i < d) t.pre[i] = carry + incl - e;
+            carry += __shfl_sync(PG_FULL, incl, 31);
+        }
+        if (lane == 0) t.pre[d] = carry;
+    }
+    group_sync<CTA>();
+    const int total = t.pre[d];
+    for (int e = tid; e < total; e += nthreads) {
+        // row of element e: last i with pre[i] <= e
+        int lo = 1, hi = d - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (t.pre[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const int i = lo;
+        const int k = e - t.pre[i];
+        const int du = t.rlen[i];
+        const int *nu = g.adj + ((size_t)(unsigned)t.rstart[i] << 2);
+        if (du <= 4 * i + 32) {
+            const int x = __ldg(nu + k);
+            int a = 0, b = i;
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (t.list[mid] < x) a = mid + 1; else b = mid;
+            }
+            if (a < i && t.list[a] == x) atomicOr(&t.rows[(size_t)i * t.ws + (a >> 5)], 1u << (a & 31));
+        } else if (contains_g(nu, du, t.list[k])) {
+            atomicOr(&t.rows[(size_t)i * t.ws + (k >> 5)], 1u << (k & 31));
+        }
+    }
+    group_sync<CTA>();
+    unsigned long long c = 0;
+    for (int w = tid; w < d * t.ws; w += nthreads) c += __popc(t.rows[w]);
+    tri += c;
+}
+
+// Run the queued products: item (s, l) adds popc(ring[s] & rows[l]).
+__device__ __forceinline__ unsigned long long flush(const Tile &t, Walker &wk, int lane) {
+    __syncwarp();
+    unsigned long long acc = 0;
+    for (int e = lane; e < wk.m; e += 32) {
+        const int it = wk.items[e];
+        const unsigned *C = wk.ring + (size_t)(it >> 16) * wk.cws;
+        const int l = it & 0xffff;
+        const unsigned *rl = t.rows + (size_t)l * t.ws;
+        const int nl = (l + 31) >> 5;
+        unsigned s = 0;
+        for (int w = 0; w < nl; ++w) s += __popc(C[w] & rl[w]);
+        acc += s;
+    }
+    __syncwarp();
+    wk.m = 0;
+    return acc;
+}
+
+// Queue one product per candidate l of C (bits below `limit`) for the last
+// level; the result counts into cnt[P].
+template <int P>
+__device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *C, int limit, int lane,
+                                     unsigned long long *cnt) {
+    const int nw = (limit + 31) >> 5;
+    if (wk.used == wk.nslots) {
+        cnt[P] += flush(t, wk, lane);
+        wk.used = 0;
+    }
+    const int slot = wk.used++;
+    unsigned *S = wk.ring + (size_t)slot * wk.cws;
+    for (int w = lane; w < nw; w += 32) S[w] = C[w];
+    __syncwarp();
+    for (int w = 0; w < nw; ++w) {
+        const unsigned x = S[w];
+        const int c = __popc(x);
+        if (wk.m + c > kItems) cnt[P] += flush(t, wk, lane);
+        if ((x >> lane) & 1u) wk.items[wk.m + __popc(x & ((1u << lane) - 1))] = (slot << 16) | (w * 32 + lane);
+        wk.m += c;
+    }
+}
+
+// Candidate set C after a prefix of P sub-graph vertices (bits below
+// `limit`): popc(C) has been counted as (P + 2)-cliques by the caller; count
+// every larger size up to kmax.  All levels but the last are warp-uniform
+// loops; the last level is queued as lane-parallel products.
+template <int P>
+__device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, int kmax, int lane,
+                     unsigned long long *cnt) {
+    if constexpr (P >= kMaxK - 2) {
         return;
     } else {
-        const int nwords = (limit_bits + 31) >> 5;
-        for (int t = 0; t < nwords; ++t) {
-            unsigned x = rows[r[0] * ws + t];
-#pragma unroll
-            for (int s = 1; s < D; ++s) x &= rows[r[s] * ws + t];
-            if (!x) continue;
-            cnt[D - 1] += __popc(x);
-            if (D + 2 < kmax) {
-                while (x) {
-                    const int b = __ffs(x) - 1;
-                    x &= x - 1;
-                    r[D] = t * 32 + b;
-                    dfs<D + 1>(rows, ws, r, r[D], kmax, cnt);
+        if (P + 3 > kmax) return;
+        if (P + 3 == kmax) {
+            emit<P>(t, wk, C, limit, lane, cnt);
+            return;
+        }
+        const int nw = (limit + 31) >> 5;
+        unsigned *N = wk.cbuf + (size_t)P * wk.cws;
+        for (int w = 0; w < nw; ++w) {
+            unsigned x = C[w];
+            while (x) {
+                const int l = w * 32 + __ffs(x) - 1;
+                x &= x - 1;
+                const unsigned *rl = t.rows + (size_t)l * t.ws;
+                const int nl = (l + 31) >> 5;
+                unsigned c = 0;
+                for (int v = lane; v < nl; v += 32) {
+                    const unsigned y = C[v] & rl[v];
+                    N[v] = y;
+                    c += __popc(y);
                 }
+                cnt[P] += c;
+                __syncwarp();
+                walk<P + 1>(t, wk, N, l, kmax, lane, cnt);
+                __syncwarp();
             }
         }
     }
 }
 
-__device__ void process_vertex(const CliqueArgs &a, int v, WarpSmem &sm, unsigned *slab, int lane,
-                               unsigned long long *cnt) {
-    const DevGraph &g = a.g;
-    const int4 vi = __ldg(&g.vinfo[v]);
-    const int d = vi.z; // out-degree
-    if (d < a.kmin - 1) return;
-    const bool in_smem = d <= kSmemD;
-    int *list = in_smem ? sm.list : (int *)slab;
-    unsigned *rows = in_smem ? sm.rows : slab + ((d + 3) & ~3);
-    const int ws = in_smem ? kSmemWs : a.gws;
-    const int *nv = adj_of(g, vi);
-    for (int i = lane; i < d; i += 32) list[i] = __ldg(nv + i);
-    __syncwarp();
-    // ---- level-1 intersections into bitmap rows -------------------------
-    for (int i = 1; i < d; ++i) {
-        const int nw = (i + 31) >> 5;
-        for (int t = lane; t < nw; t += 32) rows[i * ws + t] = 0u;
-        __syncwarp();
-        const int u = list[i];
-        const int4 ui = __ldg(&g.vinfo[u]);
-        const int du = ui.z;
-        const int *nu = adj_of(g, ui);
-        if (du <= 4 * i + 32) {
-            // scan N+(u), look each element up in list[0, i)
-            for (int c = lane; c < du; c += 32) {
-                const int x = __ldg(nu + c);
-                int lo = 0, hi = i;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (list[mid] < x) lo = mid + 1; else hi = mid;
-                }
-                if (lo < i && list[lo] == x) atomicOr(&rows[i * ws + (lo >> 5)], 1u << (lo & 31));
-            }
-        } else {
-            // look each list[j], j < i, up in N+(u)
-            for (int j = lane; j < i; j += 32)
-                if (contains_g(nu, du, list[j])) atomicOr(&rows[i * ws + (j >> 5)], 1u << (j & 31));
-        }
-        __syncwarp();
+// Pending products of the last level belong to size kmax: cnt[kmax - 3].
+__device__ __forceinline__ void drain(const Tile &t, Walker &wk, int kmax, int lane, unsigned long long *cnt) {
+    if (wk.m == 0) {
+        wk.used = 0;
+        return;
     }
-    // ---- 3-cliques: edges of the sub-graph ------------------------------
-    {
-        unsigned long long c = 0;
-        for (int i = 1 + lane; i < d; i += 32) {
-            const int nw = (i + 31) >> 5;
-            for (int t = 0; t < nw; ++t) c += __popc(rows[i * ws + t]);
-        }
-        cnt[0] += c;
+    const unsigned long long s = flush(t, wk, lane);
+    switch (kmax) {
+        case 4: cnt[1] += s; break;
+        case 5: cnt[2] += s; break;
+        case 6: cnt[3] += s; break;
+        case 7: cnt[4] += s; break;
+        default: cnt[5] += s; break;
     }
-    if (a.kmax < 4) return;
-    // ---- pairs (i, j in R[i]) through a warp queue ---------------------
-    int qn = 0;
-    int r[kMaxK];
-    auto drain = [&](int count) {
-        if (lane < count) {
-            r[0] = sm.qi[lane];
-            r[1] = sm.qj[lane];
-            dfs<2>(rows, ws, r, r[1], a.kmax, cnt);
-        }
-    };
-    for (int i = 2; i < d; ++i) {
-        const int nw = (i + 31) >> 5;
-        for (int t = 0; t < nw; ++t) {
-            const unsigned w = rows[i * ws + t];
-            if (!w) continue;
-            const bool mine = (w >> lane) & 1u;
-            const unsigned bal = __ballot_sync(PG_FULL, mine);
-            const int pos = qn + __popc(bal & ((1u << lane) - 1));
-            if (mine) {
-                sm.qi[pos] = i;
-                sm.qj[pos] = t * 32 + lane;
-            }
-            qn += __popc(bal);
-            __syncwarp();
-            if (qn >= 32) {
-                drain(32);
-                __syncwarp();
-                // move the overflow to the queue front
-                const int rest = qn - 32;
-                if (lane < rest) {
-                    sm.qi[lane] = sm.qi[32 + lane];
-                    sm.qj[lane] = sm.qj[32 + lane];
-                }
-                __syncwarp();
-                qn = rest;
-            }
-        }
-    }
-    drain(qn);
-    __syncwarp();
+    wk.used = 0;
 }
 
-__global__ void __launch_bounds__(kBlock) k_count_clique(CliqueArgs a) {
-    __shared__ WarpSmem smem[kWarps];
+__global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
+    extern __shared__ __align__(16) unsigned smem[];
+    int *ctl = (int *)smem;
+    unsigned *region = smem + kCtl;
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    unsigned *slab = a.gscratch ? a.gscratch + gw * a.slab_words : nullptr;
+    const int warp = threadIdx.x >> 5;
+    const DevGraph &g = a.g;
+    unsigned *slab = a.slabs ? a.slabs + (size_t)blockIdx.x * a.slab_words : nullptr;
+
+    Walker wk;
+    wk.cws = a.cws;
+    wk.nslots = a.nslots;
+    wk.cbuf = smem + kCtl + a.region_words + (size_t)warp * a.warp_words;
+    wk.ring = wk.cbuf + (size_t)kMaxK * a.cws;
+    wk.items = (int *)(wk.ring + (size_t)a.nslots * a.cws);
+    wk.m = 0;
+    wk.used = 0;
+
     unsigned long long cnt[kMaxK];
     for (int s = 0; s < kMaxK; ++s) cnt[s] = 0;
-    for (;;) {
-        int v = 0;
-        if (lane == 0) v = (int)atomicAdd(a.queue, 1ull);
-        v = __shfl_sync(PG_FULL, v, 0);
-        if (v >= a.n) break;
-        process_vertex(a, v, smem[wib], slab, lane, cnt);
+
+    // ---- heavy vertices: one CTA each --------------------------------------
+    Tile ht;
+    {
+        unsigned *base = a.heavy_in_smem ? region : slab;
+        ht.list = (int *)base;
+        ht.rstart = ht.list + a.dpad;
+        ht.rlen = ht.rstart + a.dpad;
+        ht.pre = ht.rlen + a.dpad;
+        ht.rows = (unsigned *)(ht.pre + a.dpad + 4);
+        ht.ws = a.hws;
     }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long h = atomicAdd(a.queue + 1, 1ull);
+            ctl[0] = h < (unsigned long long)a.n_heavy ? a.heavy[h] : -1;
+            ctl[1] = 0; // rows traversed
+        }
+        __syncthreads();
+        const int v = ctl[0];
+        if (v < 0) break;
+        const int4 vi = __ldg(&g.vinfo[v]);
+        const int d = vi.z;
+        const int *nv = adj_of(g, vi);
+        for (int i = threadIdx.x; i < d; i += kBlock) ht.list[i] = __ldg(nv + i);
+        __syncthreads();
+        build_rows<true>(g, ht, d, threadIdx.x, kBlock, cnt[0]);
+        if (a.kmax >= 4) {
+            for (;;) {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(&ctl[1], 1);
+                r = __shfl_sync(PG_FULL, r, 0);
+                const int i = d - 1 - r; // longest rows first
+                if (i < 2) break;
+                walk<1>(ht, wk, ht.rows + (size_t)i * ht.ws, i, a.kmax, lane, cnt);
+            }
+            drain(ht, wk, a.kmax, lane, cnt);
+        }
+        __syncthreads();
+    }
+
+    // ---- light vertices: one warp each, rank order -------------------------
+    Tile lt;
+    {
+        unsigned *base = region + (size_t)warp * kLightTile;
+        lt.list = (int *)base;
+        lt.rstart = lt.list + kLightD;
+        lt.rlen = lt.rstart + kLightD;
+        lt.pre = lt.rlen + kLightD;
+        lt.rows = (unsigned *)(lt.pre + kLightD + 1);
+        lt.ws = kLightWs;
+    }
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.queue, 4ull);
+        base = __shfl_sync(PG_FULL, base, 0);
+        if (base >= (unsigned long long)a.n) break;
+        for (int q = 0; q < 4; ++q) {
+            const int v = (int)base + q;
+            if (v >= a.n) break;
+            const int4 vi = __ldg(&g.vinfo[v]);
+            const int d = vi.z;
+            if (d < a.kmin - 1 || d > kLightD) continue;
+            const int *nv = adj_of(g, vi);
+            for (int i = lane; i < d; i += 32) lt.list[i] = __ldg(nv + i);
+            __syncwarp();
+            build_rows<false>(g, lt, d, lane, 32, cnt[0]);
+            if (a.kmax >= 4) {
+                for (int i = d - 1; i >= 2; --i) walk<1>(lt, wk, lt.rows + (size_t)i * lt.ws, i, a.kmax, lane, cnt);
+                drain(lt, wk, a.kmax, lane, cnt);
+            }
+            __syncwarp();
+        }
+    }
+
     for (int k = a.kmin; k <= a.kmax; ++k) {
-        const int s = k - 3;
-        const unsigned long long tot = warp_sum_u64(cnt[s]);
+        const unsigned long long tot = warp_sum_u64(cnt[k - 3]);
         if (lane == 0 && tot) atomic_add_u128(a.counts + 2 * (k - a.kmin), tot);
     }
 }
 
-int clique_grid(const pg_graph *g) {
+// ---------------------------------------------------------------- host ----
+
+struct Layout {
+    CliqueArgs a;
+    size_t smem_bytes;
+};
+
+Layout layout_for(const pg_graph *g) {
+    Layout L{};
+    CliqueArgs &a = L.a;
+    const long long D = std::max<long long>(g->max_out, 1);
+    a.dpad = (int)((D + 3) & ~3ll);
+    a.hws = (int)(((D + 31) / 32) | 1);
+    a.cws = std::max(a.hws, kLightWs);
+    a.nslots = (int)std::min<long long>(32, std::max<long long>(2, 1024 / a.cws));
+    a.warp_words = (int)(((size_t)kMaxK * a.cws + (size_t)a.nslots * a.cws + kItems + 3) & ~3ull);
+    const size_t heavy_words = (size_t)4 * a.dpad + 4 + (size_t)D * a.hws;
+    const size_t light_words = (size_t)kWarps * kLightTile;
+    const size_t warps_words = (size_t)kWarps * a.warp_words;
+    a.heavy_in_smem = (kCtl + std::max(heavy_words, light_words) + warps_words) * 4 <= kSmemBudget;
+    a.region_words = (int)(((a.heavy_in_smem ? std::max(heavy_words, light_words) : light_words) + 3) & ~3ull);
+    a.slab_words = a.heavy_in_smem ? 0 : (long long)((heavy_words + 3) & ~3ull);
+    L.smem_bytes = (kCtl + (size_t)a.region_words + warps_words) * 4;
+    return L;
+}
+
+int clique_grid(const pg_graph *g, size_t smem) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_count_clique, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_clique, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_clique, kBlock, smem);
     if (per_sm < 1) per_sm = 1;
     return per_sm * g->num_sms;
 }
 
-long long slab_words(const pg_graph *g, int *gws) {
-    const long long D = g->max_out;
-    *gws = (int)(((D + 31) / 32) | 1);
-    if (D <= kSmemD) return 0;
-    return ((D + 3) & ~3ll) + D * (*gws);
+int launch(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, unsigned long long *queue,
+           void *slabs, long long max_slabs, cudaStream_t s) {
+    if (kmin < 3 || kmax > kMaxK || kmin > kmax) return pg_set_error(PG_EINVAL, "clique sizes must be 3..8");
+    if (g->n == 0) return PG_OK;
+    if (g->max_out >= 65536) return pg_set_error(PG_EUNSUPPORTED, "clique kernel needs out-degrees below 65536");
+    Layout L = layout_for(g);
+    CliqueArgs a = L.a;
+    a.g = g->d;
+    a.kmin = kmin;
+    a.kmax = kmax;
+    a.heavy = g->heavy;
+    a.n_heavy = (int)g->n_heavy;
+    a.n = (int)g->n;
+    a.slabs = a.slab_words ? (unsigned *)slabs : nullptr;
+    a.queue = queue;
+    a.counts = counts_dev;
+    long long blocks = clique_grid(g, L.smem_bytes);
+    if (a.slab_words && blocks > max_slabs) blocks = max_slabs;
+    if (blocks < 1) return pg_set_error(PG_EINVAL, "scratch holds no slab for a single block");
+    PG_CUDA(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s));
+    k_count_clique<<<(unsigned)blocks, kBlock, L.smem_bytes, s>>>(a);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
 }
 
 }  // namespace
 
+size_t pg_clique_slab_bytes(const pg_graph *g) { return (size_t)layout_for(g).a.slab_words * sizeof(unsigned); }
+
 size_t pg_clique_scratch_bytes(const pg_graph *g) {
-    int gws;
-    return (size_t)clique_grid(g) * kWarps * (size_t)slab_words(g, &gws) * sizeof(unsigned);
+    const Layout L = layout_for(g);
+    return (size_t)clique_grid(g, L.smem_bytes) * (size_t)L.a.slab_words * sizeof(unsigned);
 }
 
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, int queue_slot,
                      cudaStream_t s) {
-    if (kmin < 3 || kmax > kMaxK || kmin > kmax) return pg_set_error(PG_EINVAL, "clique sizes must be 3..8");
-    if (g->n == 0) return PG_OK;
-    CliqueArgs a;
-    a.g = g->d;
-    a.kmin = kmin;
-    a.kmax = kmax;
-    a.slab_words = slab_words(g, &a.gws);
-    a.gscratch = a.slab_words ? (unsigned *)g->scratch : nullptr;
-    a.queue = g->queues + queue_slot;
-    a.n = (int)g->n;
-    a.counts = counts_dev;
-    PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
-    k_count_clique<<<clique_grid(g), kBlock, 0, s>>>(a);
-    PG_CUDA(cudaGetLastError());
-    return PG_OK;
+    if (queue_slot + 1 >= PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "queue slot out of range");
+    return launch(g, kmin, kmax, counts_dev, g->queues + queue_slot, g->scratch,
+                  (long long)(g->scratch_bytes / std::max<size_t>(pg_clique_slab_bytes(g), 1)), s);
 }
 
-// Launch of the same kernel on caller-supplied scratch: `queue` is one zeroed
-// 64-bit counter and `slabs` holds `max_warps` per-warp slabs of
-// pg_clique_slab_bytes() bytes; the grid is cut so that no warp indexes a
-// slab beyond max_warps.  Used by the entry point that allocates nothing.
-size_t pg_clique_slab_bytes(const pg_graph *g) {
-    int gws;
-    return (size_t)slab_words(g, &gws) * sizeof(unsigned);
-}
-
+// Same kernel on caller-supplied scratch: `queue` = two 64-bit counters
+// (zeroed here on the stream), `slabs` = room for `max_slabs` per-CTA slabs of
+// pg_clique_slab_bytes() bytes; the grid is cut to max_slabs CTAs.
 int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
-                        unsigned long long *queue, void *slabs, long long max_warps, cudaStream_t s) {
-    if (kmin < 3 || kmax > kMaxK || kmin > kmax) return pg_set_error(PG_EINVAL, "clique sizes must be 3..8");
-    if (g->n == 0) return PG_OK;
-    CliqueArgs a;
-    a.g = g->d;
-    a.kmin = kmin;
-    a.kmax = kmax;
-    a.slab_words = slab_words(g, &a.gws);
-    a.gscratch = a.slab_words ? (unsigned *)slabs : nullptr;
-    a.queue = queue;
-    a.n = (int)g->n;
-    a.counts = counts_dev;
-    long long blocks = clique_grid(g);
-    if (a.slab_words && blocks * kWarps > max_warps) blocks = max_warps / kWarps;
-    if (blocks < 1) return pg_set_error(PG_EINVAL, "scratch holds fewer slabs than one block needs");
-    k_count_clique<<<(unsigned)blocks, kBlock, 0, s>>>(a);
-    PG_CUDA(cudaGetLastError());
-    return PG_OK;
+                        unsigned long long *queue, void *slabs, long long max_slabs, cudaStream_t s) {
+    return launch(g, kmin, kmax, counts_dev, queue, slabs, max_slabs, s);
 }

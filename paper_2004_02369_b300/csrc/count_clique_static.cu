@@ -18,7 +18,7 @@ static __device__ __align__(256) unsigned char g_pg_static_scratch[PG_STATIC_SCR
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr size_t kQueueBytes = 256; // work-queue counter, padded to keep slabs aligned
+constexpr size_t kQueueBytes = 256; // work-queue counters, padded to keep slabs aligned
 
 std::mutex g_mu;
 void *g_base[kMaxDevices] = {};
@@ -49,21 +49,21 @@ extern "C" int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax,
     if (dev != g->device) return pg_set_error(PG_EINVAL, "the graph lives on another device than the current one");
     const size_t slab = pg_clique_slab_bytes(g);
     const size_t room = PG_STATIC_SCRATCH_BYTES - kQueueBytes;
-    long long max_warps = slab ? (long long)(room / slab) : (1ll << 40);
-    if (slab && max_warps < 4LL * g->num_sms)
+    long long max_slabs = slab ? (long long)(room / slab) : (1ll << 40);
+    if (slab && max_slabs < g->num_sms)
         return pg_set_error(PG_EINVAL,
                             "graph too large for the static scratch: its maximum out-degree " +
                                 std::to_string(g->max_out) + " needs " + std::to_string(slab) +
-                                " bytes per warp, and the " + std::to_string(PG_STATIC_SCRATCH_BYTES >> 20) +
-                                " MiB array holds fewer than one 4-warp block per SM");
+                                " bytes per block, and the " + std::to_string(PG_STATIC_SCRATCH_BYTES >> 20) +
+                                " MiB array holds fewer than one block per SM");
     void *base = nullptr;
     int rc = static_scratch_base(dev, &base);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // the queue counter and the output start at zero; slab contents left by
-    // an earlier call are overwritten before they are read
-    PG_CUDA(cudaMemsetAsync(base, 0, sizeof(unsigned long long), s));
+    // the output and the queue counters (zeroed by the launcher) start at
+    // zero; slab contents left by an earlier call are overwritten before
+    // they are read
     PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * (size_t)(kmax - kmin + 1), s));
     return pg_launch_clique_on(g, kmin, kmax, (unsigned long long *)counts_dev, (unsigned long long *)base,
-                               (unsigned char *)base + kQueueBytes, max_warps, s);
+                               (unsigned char *)base + kQueueBytes, max_slabs, s);
 }

@@ -113,6 +113,25 @@ __global__ void k_finish(int *adj, const int64_t *pstart, const int64_t *udeg, c
     atomicMax(maxes + 2, lab);
 }
 
+// heavy clique start vertices: out-degree > PG_CLIQUE_LIGHT_D, keyed by
+// (out-degree descending, rank ascending); others get the largest key
+__global__ void k_heavy_keys(const int4 *vinfo, int64_t n, unsigned long long *keys, unsigned *count) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int dplus = vinfo[r].z;
+    if (dplus > PG_CLIQUE_LIGHT_D) {
+        keys[r] = ((0xffffffffull - (unsigned long long)dplus) << 32) | (unsigned long long)r;
+        atomicAdd(count, 1u);
+    } else {
+        keys[r] = ~0ull;
+    }
+}
+
+__global__ void k_heavy_ids(const unsigned long long *sorted, int64_t count, int *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (int)(sorted[i] & 0xffffffffull);
+}
+
 inline unsigned grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
@@ -226,6 +245,23 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     g->max_deg = hm[0];
     g->max_out = hm[1];
     g->n_labels = d_labels ? hm[2] + 1 : 0;
+
+    // heavy clique start vertices (reuse the vertex key buffers)
+    if (n > 0) {
+        PG_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+        k_heavy_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(g->vinfo, n, (unsigned long long *)vkeys.p, err);
+        need = tmp_bytes;
+        PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, need, (unsigned long long *)vkeys.p,
+                                               (unsigned long long *)vkeys2.p, (int64_t)n, 0, 64, s));
+        unsigned nh = 0;
+        PG_CUDA(cudaMemcpyAsync(&nh, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        g->n_heavy = nh;
+        PG_CUDA(cudaMalloc(&g->heavy, (nh > 0 ? nh : 1) * sizeof(int)));
+        if (nh > 0) k_heavy_ids<<<grid_for(nh, kBlock), kBlock, 0, s>>>((unsigned long long *)vkeys2.p, nh, g->heavy);
+        PG_CUDA(cudaGetLastError());
+        PG_CUDA(cudaStreamSynchronize(s));
+    }
     g->bytes_device = (int64_t)(nn * (sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int));
     return PG_OK;
 }

@@ -24,6 +24,7 @@ struct DevGraph {
 };
 
 #define PG_PAD 0x7fffffff
+#define PG_CLIQUE_LIGHT_D 64 // out-degree up to which one warp handles a clique start vertex
 
 struct pg_graph {
     DevGraph d{};
@@ -40,6 +41,9 @@ struct pg_graph {
     size_t scratch_bytes = 0;
     unsigned long long *queues = nullptr; // PG_MAX_QUEUES counters
     unsigned long long *tmp_counts = nullptr; // 2 * PG_MAX_QUEUES words
+    // vertices with out-degree > PG_CLIQUE_LIGHT_D, by out-degree descending
+    int *heavy = nullptr;
+    int64_t n_heavy = 0;
     int64_t bytes_device = 0;
 };
 

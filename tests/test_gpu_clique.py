@@ -42,13 +42,15 @@ def test_clique_kernel_small_graphs(pg, seed):
     assert _count(pg, G, [4, 5], pg.KERNEL_GENERIC) == want[1:3]
 
 
-def test_clique_kernel_global_slab_path(pg):
-    """Complete graph on 300 vertices: out-degrees up to 299 exceed the
-    shared-memory tile, rows span 10 words."""
-    n = 300
+@pytest.mark.parametrize("n", [65, 300, 900])
+def test_clique_kernel_complete_graphs(pg, n):
+    """Complete graphs: every start vertex of out-degree > 64 goes through the
+    CTA-wide tile; n = 300 keeps it in shared memory (rows of 10 words), n = 900
+    exceeds the shared-memory budget and uses the per-block global slab."""
     G = pg.Graph.from_synth(sg.complete_graph(n))
     assert G.info().max_out_degree == n - 1
-    assert _count(pg, G, [3, 4, 5], pg.KERNEL_CLIQUE) == [comb(n, 3), comb(n, 4), comb(n, 5)]
+    ks = [3, 4, 5, 6] if n <= 300 else [3, 4]
+    assert _count(pg, G, ks, pg.KERNEL_CLIQUE) == [comb(n, k) for k in ks]
 
 
 def test_clique_kernel_dense_random(pg):

@@ -40,8 +40,8 @@ def _noalloc(pg, G, kmin, kmax):
 @pytest.mark.parametrize("which", ["shared_memory_tile", "global_slab"])
 def test_noalloc_matches_regular_entry_point(pg, which):
     if which == "global_slab":
-        g = sg.complete_graph(300)  # out-degrees up to 299 > 256: per-warp slabs in the array
-        kmin, kmax = 3, 5
+        g = sg.complete_graph(900)  # out-degree 899: the block tile lives in a slab of the array
+        kmin, kmax = 3, 4
     else:
         g = sg.chung_lu(3000, 30000, 2.1, 500.0, 201)
         kmin, kmax = 3, 8
@@ -55,7 +55,7 @@ def test_noalloc_matches_regular_entry_point(pg, which):
 
 def test_noalloc_rejects_oversized_and_bad_sizes(pg):
     import torch
-    G = pg.Graph.from_synth(sg.complete_graph(1400))  # out-degree 1399: slabs too large
+    G = pg.Graph.from_synth(sg.complete_graph(1400))  # out-degree 1399: fewer slabs than SMs
     out = torch.zeros(16, dtype=torch.int64, device="cuda")
     with pytest.raises(pg.PgError) as e:
         pg.count_cliques_noalloc(G, 3, 3, out)
