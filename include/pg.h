@@ -45,6 +45,7 @@ extern "C" {
 
 typedef struct pg_graph pg_graph; /* device-resident data graph (opaque) */
 typedef struct pg_plan pg_plan;   /* compiled exploration plan (opaque, host) */
+typedef struct pg_batch pg_batch; /* several plans merged for one launch (opaque) */
 
 /*
  * Pattern description (Section 3.1, "Pattern Interface" figure; anti-edges
@@ -101,7 +102,7 @@ typedef struct {
 #define PG_KERNEL_GENERIC 1       /* plan interpreter, any pattern */
 #define PG_KERNEL_CLIQUE_PLAIN 2  /* plan interpreter, one warp per task, one launch per pattern */
 #define PG_KERNEL_CLIQUE 3        /* k-clique, persistent, bitmap sub-graph */
-#define PG_KERNEL_MOTIF4_FUSED 4  /* the six induced 4-vertex motifs in one launch */
+#define PG_KERNEL_BATCHED 4       /* all plans in one launch over their shared prefix tree */
 
 /*
  * pg_load_graph - make a data graph resident on the current device.
@@ -152,6 +153,13 @@ int pg_compile_pattern(const pg_pattern_desc *desc, pg_plan **out);
 
 /* pg_plan_get_info - inspect a plan (host struct out). */
 int pg_plan_get_info(const pg_plan *p, pg_plan_info *out);
+
+/* pg_plan_describe - the plan as text: automorphism count, partial order,
+ * core, and per matching order the level program (for every level: bound
+ * pattern vertex, intersected / subtracted / bounding / excluded earlier
+ * levels, label, counted group size).  Writes at most `size` bytes including
+ * the terminating NUL into host buffer `buf`; PG_ETRUNC if it did not fit. */
+int pg_plan_describe(const pg_plan *p, char *buf, int64_t size);
 
 /* pg_free_plan - release a plan and its device copies (NULL is a no-op). */
 void pg_free_plan(pg_plan *p);
@@ -211,6 +219,43 @@ int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *c
  */
 int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax, uint64_t *counts_dev,
                              void *stream);
+
+/*
+ * pg_compile_batch - merge the matching-order programs of n_plans plans
+ * (1..64) into one prefix tree for a single launch (shared start vertex and
+ * shared candidate sets of identical level prefixes; Section 5.1 processing
+ * model applied to several patterns at once).  Host object with a device
+ * copy on the current device; plans may be freed afterwards.
+ *   flags  PG_BATCH_EXPAND_ANTI: count a plan with anti-edges (no
+ *          anti-vertices, at most 6 anti-edges) as the signed sum over its
+ *          edge-induced supergraphs, maps(E, A) = sum over T in A of
+ *          (-1)^|T| maps(E + T) (inclusion-exclusion over anti-edges, the
+ *          pattern-level form of Section 4.2's set differences; with the
+ *          Theorem of Section 3.1.3 it covers vertex-induced patterns);
+ *          isomorphic terms of all plans are counted once.  0: anti-edges
+ *          are applied as set differences inside each plan.
+ * At most 64 distinct counted patterns per batch after expansion.
+ * Errors: PG_EINVAL, PG_EUNSUPPORTED (too many counted patterns),
+ * PG_ENOMEM, PG_EDEVICE.
+ */
+#define PG_BATCH_EXPAND_ANTI 1
+int pg_compile_batch(pg_plan *const *plans, int32_t n_plans, int32_t flags, pg_batch **out);
+
+/* pg_batch_get_info - tree nodes, merged programs, and the total number of
+ * levels of the programs before merging (host ints out). */
+int pg_batch_get_info(const pg_batch *b, int32_t *n_nodes, int32_t *n_programs, int32_t *n_levels_total);
+
+/*
+ * pg_count_batch - counts of every plan of the batch in one persistent
+ * launch.  counts_dev: uint64[2 * n_plans] device, (low, high) words in the
+ * plans' order; zeroed on `stream`.  Asynchronous; allocates only when the
+ * graph's scratch arena must grow (first call for this batch size).
+ * Errors: PG_EINVAL (labeled plan on unlabeled graph), PG_ENOMEM, PG_EDEVICE.
+ */
+int pg_count_batch(pg_graph *g, const pg_batch *b, uint64_t *counts_dev, void *stream);
+
+/* pg_free_batch - release a batch (NULL is a no-op). */
+void pg_free_batch(pg_batch *b);
 
 /* pg_last_error - message of the last failed call on this host thread. */
 const char *pg_last_error(void);

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpg.so")
 
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETRUNC, PG_ETIMEOUT, PG_EDEVICE, PG_EUNSUPPORTED = range(7)
-KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_MOTIF4_FUSED = range(5)
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_BATCHED = range(5)
 MAX_PATTERN = 8
 
 if not os.path.exists(LIB_PATH):
@@ -64,11 +64,17 @@ _lib.pg_free_graph.argtypes = [_vp]
 _lib.pg_free_graph.restype = None
 _lib.pg_compile_pattern.argtypes = [ctypes.POINTER(_PatternDesc), ctypes.POINTER(_vp)]
 _lib.pg_plan_get_info.argtypes = [_vp, ctypes.POINTER(PlanInfo)]
+_lib.pg_plan_describe.argtypes = [_vp, ctypes.c_char_p, _i64]
 _lib.pg_free_plan.argtypes = [_vp]
 _lib.pg_free_plan.restype = None
 _lib.pg_count.argtypes = [_vp, _vp, _i32, _vp, _vp]
 _lib.pg_count_ex.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp]
 _lib.pg_count_cliques_noalloc.argtypes = [_vp, _i32, _i32, _vp, _vp]
+_lib.pg_compile_batch.argtypes = [_vp, _i32, _i32, ctypes.POINTER(_vp)]
+_lib.pg_batch_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
+_lib.pg_count_batch.argtypes = [_vp, _vp, _vp, _vp]
+_lib.pg_free_batch.argtypes = [_vp]
+_lib.pg_free_batch.restype = None
 _lib.pg_last_error.restype = ctypes.c_char_p
 
 
@@ -195,6 +201,11 @@ class Plan:
         _check(_lib.pg_plan_get_info(self._h, ctypes.byref(out)))
         return out
 
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(_lib.pg_plan_describe(self._h, buf, len(buf)))
+        return buf.value.decode()
+
     def close(self):
         if getattr(self, "_h", None):
             _lib.pg_free_plan(self._h)
@@ -202,6 +213,44 @@ class Plan:
 
     def __del__(self):
         self.close()
+
+
+class Batch:
+    """Several plans merged into one prefix tree, counted in one launch."""
+
+    EXPAND_ANTI = 1
+
+    def __init__(self, plans, expand_anti_edges: bool = True):
+        self.plans = list(plans)
+        h = _vp()
+        _check(_lib.pg_compile_batch(_plan_array(self.plans), len(self.plans),
+                                     self.EXPAND_ANTI if expand_anti_edges else 0, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        a, b, c = _i32(), _i32(), _i32()
+        _check(_lib.pg_batch_get_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"nodes": a.value, "programs": b.value, "levels_total": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pg_free_batch(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def count_batch(graph: Graph, batch: Batch, out, stream=None):
+    """Enqueue the counts of every plan of ``batch`` into ``out`` (torch CUDA
+    int64, 2*len(plans) words) in one launch; no host sync."""
+    if out.numel() < 2 * len(batch.plans) or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor with 2*len(plans) 64-bit elements")
+    _check(_lib.pg_count_batch(graph.handle, batch.handle, out.data_ptr(), _stream_ptr(stream)))
 
 
 def _plan_array(plans):

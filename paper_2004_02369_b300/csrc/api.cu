@@ -1,6 +1,7 @@
 // C-ABI entry points (include/pg.h): argument checking, ownership, kernel
 // dispatch.  No compute happens here; every step of the path runs in the
 // library's kernels.
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -84,6 +85,9 @@ extern "C" int pg_load_graph(const int64_t *offsets, int64_t n, const int32_t *a
     g->d.max_deg = (int)g->max_deg;
     g->d.max_out = (int)g->max_out;
     g->d.labeled = g->labeled;
+    g->d.hubbits = g->hubbits;
+    g->d.n_hubs = g->n_hubs;
+    g->d.hub_stride = g->hub_stride;
     *out = g;
     return PG_OK;
 }
@@ -111,10 +115,12 @@ extern "C" void pg_free_graph(pg_graph *g) {
     if (g->vinfo) cudaFree(g->vinfo);
     if (g->adj) cudaFree(g->adj);
     if (g->rank) cudaFree(g->rank);
+    if (g->hubbits) cudaFree(g->hubbits);
     if (g->scratch) cudaFree(g->scratch);
     if (g->queues) cudaFree(g->queues);
     if (g->tmp_counts) cudaFree(g->tmp_counts);
     if (g->heavy) cudaFree(g->heavy);
+    if (g->batch_cache) pg_batch_free(g->batch_cache);
     delete g;
 }
 
@@ -168,7 +174,9 @@ extern "C" int pg_compile_pattern(const pg_pattern_desc *d, pg_plan **out) {
         delete pl;
         return pg_set_error(rc, err);
     }
-    pl->kernel_auto = (pl->h.is_clique && pl->h.pat.k >= 3) ? PG_KERNEL_CLIQUE : PG_KERNEL_GENERIC;
+    static std::atomic<uint64_t> next_serial{1};
+    pl->serial = next_serial++;
+    pl->kernel_auto = (pl->h.is_clique && pl->h.pat.k >= 3) ? PG_KERNEL_CLIQUE : PG_KERNEL_BATCHED;
     *out = pl;
     return PG_OK;
 }
@@ -192,6 +200,39 @@ extern "C" int pg_plan_get_info(const pg_plan *pl, pg_plan_info *out) {
     out->kernel = pl->kernel_auto;
     out->compile_ms = h.compile_ms;
     return PG_OK;
+}
+
+extern "C" int pg_plan_describe(const pg_plan *pl, char *buf, int64_t size) {
+    if (!pl || (!buf && size > 0) || size < 0) return pg_set_error(PG_EINVAL, "bad argument");
+    const PgPlanHost &h = pl->h;
+    std::string out;
+    auto vlist = [](const int8_t *src, int n) {
+        std::string s = "[";
+        for (int i = 0; i < n; ++i) s += (i ? "," : "") + std::to_string(src[i]);
+        return s + "]";
+    };
+    out += "k=" + std::to_string(h.pat.k) + " aut=" + std::to_string(h.aut) + " core_mask=" +
+           std::to_string(h.core_mask) + " orders=" + std::to_string(h.orders.size()) + " po=";
+    for (auto &e : h.po) out += "(" + std::to_string(e.first) + "<" + std::to_string(e.second) + ")";
+    out += "\n";
+    for (size_t o = 0; o < h.orders.size(); ++o) {
+        const PgOrder &ord = h.orders[o];
+        out += "order " + std::to_string(o) + ":\n";
+        for (int l = 0; l < ord.n_levels; ++l) {
+            const PgLevel &L = ord.lv[l];
+            out += "  L" + std::to_string(l) + " u" + std::to_string(L.pattern_vertex) + (L.is_core ? " core" : " noncore") +
+                   " int=" + vlist(L.int_src, L.n_int) + " diff=" + vlist(L.diff_src, L.n_diff) + " lo=" +
+                   vlist(L.lo_src, L.n_lo) + " hi=" + vlist(L.hi_src, L.n_hi) + " excl=" + vlist(L.excl_src, L.n_excl) +
+                   " label=" + std::to_string(L.label) + " group=" + std::to_string(L.group) +
+                   (L.out_bounded ? " out" : "") + (L.joint ? " joint" : "") + "\n";
+        }
+    }
+    if (size > 0) {
+        const size_t n = std::min<size_t>(out.size(), (size_t)size - 1);
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return out.size() + 1 <= (size_t)size ? PG_OK : pg_set_error(PG_ETRUNC, "buffer too small for the plan text");
 }
 
 extern "C" void pg_free_plan(pg_plan *pl) {
@@ -227,11 +268,29 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         kmin = std::min(kmin, h.pat.k);
         kmax = std::max(kmax, h.pat.k);
     }
-    if (kernel == PG_KERNEL_AUTO) kernel = all_clique ? PG_KERNEL_CLIQUE : PG_KERNEL_GENERIC;
+    if (all_clique && g->max_out >= 65536) all_clique = false;
+    if (kernel == PG_KERNEL_AUTO) kernel = all_clique ? PG_KERNEL_CLIQUE : PG_KERNEL_BATCHED;
     if (kernel == PG_KERNEL_CLIQUE && !all_clique)
         return pg_set_error(PG_EINVAL, "PG_KERNEL_CLIQUE needs unlabeled k-clique patterns, k >= 3");
-    if (kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN && kernel != PG_KERNEL_CLIQUE)
-        return pg_set_error(PG_EUNSUPPORTED, "kernel family not built");
+    if (kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN && kernel != PG_KERNEL_CLIQUE &&
+        kernel != PG_KERNEL_BATCHED)
+        return pg_set_error(PG_EINVAL, "unknown kernel family");
+    if (kernel == PG_KERNEL_BATCHED) {
+        std::vector<uint64_t> key;
+        for (int i = 0; i < n_plans; ++i) key.push_back(plans[i]->serial);
+        if (!g->batch_cache || g->batch_key != key) {
+            pg_batch *b = nullptr;
+            int rc = pg_batch_build(plans, n_plans, PG_BATCH_EXPAND_ANTI, &b);
+            if (rc) return rc;
+            if (g->batch_cache) {
+                PG_CUDA(cudaDeviceSynchronize()); // earlier launches may still read it
+                pg_batch_free(g->batch_cache);
+            }
+            g->batch_cache = b;
+            g->batch_key = key;
+        }
+        return pg_count_batch(g, g->batch_cache, counts_dev, stream);
+    }
     size_t need = 0;
     for (int i = 0; i < n_plans; ++i) {
         int rc = pg_plan_upload(plans[i]);
@@ -259,6 +318,37 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         if (rc) return rc;
     }
     return PG_OK;
+}
+
+extern "C" int pg_compile_batch(pg_plan *const *plans, int32_t n_plans, int32_t flags, pg_batch **out) {
+    if (!plans || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    *out = nullptr;
+    for (int i = 0; i < n_plans; ++i)
+        if (!plans[i]) return pg_set_error(PG_EINVAL, "NULL plan");
+    return pg_batch_build(plans, n_plans, flags, out);
+}
+
+extern "C" int pg_batch_get_info(const pg_batch *b, int32_t *n_nodes, int32_t *n_programs, int32_t *n_levels_total) {
+    if (!b || !n_nodes || !n_programs || !n_levels_total) return pg_set_error(PG_EINVAL, "NULL argument");
+    int a, p, l;
+    pg_batch_stats(b, &a, &p, &l);
+    *n_nodes = a;
+    *n_programs = p;
+    *n_levels_total = l;
+    return PG_OK;
+}
+
+extern "C" void pg_free_batch(pg_batch *b) { pg_batch_free(b); }
+
+extern "C" int pg_count_batch(pg_graph *g, const pg_batch *b, uint64_t *counts_dev, void *stream) {
+    if (!g || !b || !counts_dev) return pg_set_error(PG_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = pg_ensure_scratch(g, pg_batch_scratch_bytes(g, b), s);
+    if (rc) return rc;
+    if (pg_batch_labeled(b) && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+    const int n_slots = pg_batch_slots(b);
+    PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * n_slots, s));
+    return pg_launch_batched(g, b, (unsigned long long *)counts_dev, 0, s);
 }
 
 extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_out, void *stream) {

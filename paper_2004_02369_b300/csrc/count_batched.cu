@@ -1,0 +1,543 @@
+// Batched counting: many plans in one persistent launch over a shared
+// exploration tree.
+//
+// Every plan contributes one level program per matching order (Section 4.1);
+// every program starts at the task's start vertex (Section 5.1).  Programs of
+// all plans in a batch are merged into a prefix tree: two programs share a
+// node at depth l when their level specifications 1..l are identical (same
+// intersected / subtracted / bounding / excluded earlier levels and label),
+// so the candidate set of a shared prefix is computed once per start vertex
+// and its candidates are extended into every program below it.  A node where
+// one or more programs end is counted once by cardinality and adds
+// C(|S|, g) into each such plan's counter.  For the six induced 4-vertex
+// motifs the 22 programs share their first level (the start vertex's
+// out-neighbourhood) and most of their second.
+//
+// GPU mapping: one warp per start vertex (device atomic queue, highest
+// degree first, Section 5.2); depth-first walk of the tree with an explicit
+// per-depth stack; per-depth candidate buffers in a per-warp scratch region;
+// per-warp 128-bit counters per plan in shared memory, flushed once per warp.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "level_ops.cuh"
+
+using namespace pgk;
+
+// Children of a node: n_children plain ones from first_child, then n_joint
+// joint leaves (counted together with this node's vertex, see plan.h).
+struct PgTrieNode {
+    PgLevel spec;
+    int32_t depth;
+    int32_t first_child, n_children;
+    int32_t first_term, n_terms;
+    int32_t n_joint;
+};
+
+struct PgTrieTerm {
+    int32_t slot;
+    int32_t group;
+};
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kBlock = kWarps * 32;
+constexpr int kMaxSlots = PG_MAX_QUEUES;
+
+struct BatchArgs {
+    DevGraph g;
+    const PgTrieNode *nodes;
+    const PgTrieTerm *terms;
+    int n_roots; // roots are nodes[0 .. n_roots)
+    int n_slots;
+    int *scratch;
+    long long warp_stride;
+    long long lvl_off[PGP_MAXK];
+    unsigned long long *queue;
+    int n;
+    unsigned long long *counts; // 2 words per slot
+};
+
+__device__ __forceinline__ void add_slot(unsigned long long *acc, int slot, unsigned __int128 x) {
+    // acc: per-warp (low, high) pairs in shared memory, single writer (lane 0)
+    unsigned long long lo = acc[2 * slot];
+    const unsigned long long add = (unsigned long long)x;
+    acc[2 * slot] = lo + add;
+    acc[2 * slot + 1] += (unsigned long long)(x >> 64) + (lo + add < lo ? 1ull : 0ull);
+}
+
+__device__ void count_terms(const BatchArgs &a, const PgTrieNode &C, const int *m, int lane,
+                            unsigned long long *acc) {
+    const unsigned long long c = count_last(a.g, C.spec, m, lane);
+    if (lane == 0 && c)
+        for (int t = 0; t < C.n_terms; ++t) {
+            const PgTrieTerm tm = a.terms[C.first_term + t];
+            add_slot(acc, tm.slot, choose_u128(c, tm.group));
+        }
+}
+
+__global__ void __launch_bounds__(kBlock) k_count_batched(BatchArgs a) {
+    __shared__ unsigned long long s_acc[kWarps][2 * kMaxSlots];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    int *wbuf = a.scratch + gw * a.warp_stride;
+    unsigned long long *acc = s_acc[wib];
+    for (int i = lane; i < 2 * kMaxSlots; i += 32) acc[i] = 0;
+    __syncwarp();
+    const DevGraph &g = a.g;
+    int m[PGP_MAXK], node[PGP_MAXK], sz[PGP_MAXK], ci[PGP_MAXK], ch[PGP_MAXK];
+    for (;;) {
+        int v = 0;
+        if (lane == 0) v = (int)atomicAdd(a.queue, 1ull);
+        v = __shfl_sync(PG_FULL, v, 0);
+        if (v >= a.n) break;
+        const int label = g.labeled ? __ldg(&g.vinfo[v].w) : 0;
+        for (int r = 0; r < a.n_roots; ++r) {
+            const PgTrieNode &R = a.nodes[r];
+            if (R.spec.label >= 0 && R.spec.label != label) continue;
+            if (lane == 0)
+                for (int t = 0; t < R.n_terms; ++t) add_slot(acc, a.terms[R.first_term + t].slot, 1);
+            if (R.n_children == 0) continue;
+            int l = 0;
+            node[0] = r;
+            sz[0] = 1;
+            ci[0] = 0;
+            ch[0] = 0;
+            m[0] = v;
+            for (;;) {
+                const PgTrieNode &N = a.nodes[node[l]];
+                if (ch[l] >= N.n_children) {
+                    ch[l] = 0;
+                    if (++ci[l] >= sz[l]) {
+                        if (l == 0) break;
+                        --l;
+                        ++ch[l];
+                        continue;
+                    }
+                }
+                if (l > 0) m[l] = wbuf[a.lvl_off[l] + ci[l]];
+                const int child = N.first_child + ch[l];
+                const PgTrieNode &C = a.nodes[child];
+                if (C.n_terms) count_terms(a, C, m, lane, acc);
+                for (int j = 0; j < C.n_joint; ++j) {
+                    const PgTrieNode &J = a.nodes[C.first_child + C.n_children + j];
+                    const unsigned long long c =
+                        count_joint(g, C.spec, J.spec, l + 1, m, wbuf + a.lvl_off[l + 1], wbuf + a.lvl_off[l + 2], lane);
+                    if (lane == 0 && c)
+                        for (int t = 0; t < J.n_terms; ++t) add_slot(acc, a.terms[J.first_term + t].slot, c);
+                }
+                if (C.n_children) {
+                    const int s = fill_level(g, C.spec, m, wbuf + a.lvl_off[l + 1], lane);
+                    if (s > 0) {
+                        ++l;
+                        node[l] = child;
+                        sz[l] = s;
+                        ci[l] = 0;
+                        ch[l] = 0;
+                        continue;
+                    }
+                }
+                ++ch[l];
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < a.n_slots) {
+        const unsigned __int128 x =
+            ((unsigned __int128)acc[2 * lane + 1] << 64) | (unsigned __int128)acc[2 * lane];
+        if (x) atomic_add_u128(a.counts + 2 * lane, x);
+    }
+    if (a.n_slots > 32 && lane + 32 < a.n_slots) {
+        const int s = lane + 32;
+        const unsigned __int128 x = ((unsigned __int128)acc[2 * s + 1] << 64) | (unsigned __int128)acc[2 * s];
+        if (x) atomic_add_u128(a.counts + 2 * s, x);
+    }
+}
+
+// Output counts from slot counts: out[i] = (sum_t coef_t * slot[t]) / div[i]
+// in wrapping 128-bit arithmetic (the true value is non-negative, < 2^128).
+__global__ void k_combine(const unsigned long long *slot_counts, const int *term_slot, const long long *term_coef,
+                          const int *out_first, const int *out_n, const unsigned long long *out_div, int n_out,
+                          unsigned long long *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_out) return;
+    unsigned __int128 acc = 0;
+    for (int t = out_first[i]; t < out_first[i] + out_n[i]; ++t) {
+        const int s = term_slot[t];
+        const unsigned __int128 c = ((unsigned __int128)slot_counts[2 * s + 1] << 64) | slot_counts[2 * s];
+        acc += (unsigned __int128)(__int128)term_coef[t] * c;
+    }
+    acc /= out_div[i];
+    out[2 * i] = (unsigned long long)acc;
+    out[2 * i + 1] = (unsigned long long)(acc >> 64);
+}
+
+int batched_grid(const pg_graph *g) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * g->num_sms;
+}
+
+// ---- trie construction (host) --------------------------------------------
+
+PgLevel normalized(const PgLevel &L) {
+    PgLevel n;
+    std::memset(&n, 0, sizeof(n));
+    n.n_int = L.n_int;
+    n.n_diff = L.n_diff;
+    n.n_lo = L.n_lo;
+    n.n_hi = L.n_hi;
+    n.n_excl = L.n_excl;
+    n.group = 1;
+    n.joint = L.joint;
+    n.label = L.label;
+    std::memcpy(n.int_src, L.int_src, L.n_int);
+    std::memcpy(n.diff_src, L.diff_src, L.n_diff);
+    std::memcpy(n.lo_src, L.lo_src, L.n_lo);
+    std::memcpy(n.hi_src, L.hi_src, L.n_hi);
+    std::memcpy(n.excl_src, L.excl_src, L.n_excl);
+    std::sort(n.int_src, n.int_src + n.n_int);
+    std::sort(n.diff_src, n.diff_src + n.n_diff);
+    std::sort(n.lo_src, n.lo_src + n.n_lo);
+    std::sort(n.hi_src, n.hi_src + n.n_hi);
+    std::sort(n.excl_src, n.excl_src + n.n_excl);
+    return n;
+}
+
+bool same_spec(const PgLevel &x, const PgLevel &y) { return std::memcmp(&x, &y, sizeof(PgLevel)) == 0; }
+
+}  // namespace
+
+struct pg_batch {
+    // counted patterns ("slots"): the plans themselves, or the edge-induced
+    // terms their anti-edges expand into; output i = sum over its terms of
+    // coef * slot count, divided by div[i]
+    std::vector<PgPlanHost> slot_plans;
+    std::vector<int> clique_k;          // per slot: k when counted by the clique kernel, else 0
+    int clique_kmin = 0, clique_kmax = 0;
+    std::vector<int> out_first, out_n;  // per output plan: range in out_terms
+    std::vector<int> term_slot;
+    std::vector<long long> term_coef;   // signed, includes |Aut| of the term pattern
+    std::vector<unsigned long long> out_div;
+    int n_out = 0;
+    int *d_term_slot = nullptr;
+    long long *d_term_coef = nullptr;
+    int *d_out_first = nullptr, *d_out_n = nullptr;
+    unsigned long long *d_out_div = nullptr;
+    unsigned long long *d_slot_counts = nullptr; // 2 words per slot
+    std::vector<PgTrieNode> nodes;
+    std::vector<PgTrieTerm> terms;
+    int n_roots = 0;
+    int n_slots = 0;
+    int n_programs = 0;
+    int n_levels_total = 0;     // sum over programs of their levels
+    bool labeled = false;
+    bool out_bounded[PGP_MAXK] = {};
+    bool any_level[PGP_MAXK] = {};
+    PgTrieNode *d_nodes = nullptr;
+    PgTrieTerm *d_terms = nullptr;
+};
+
+namespace {
+
+// Canonical form of a pattern under vertex permutations (labels and
+// relations), for merging isomorphic expansion terms.
+std::vector<int> canonical(const PgPattern &q) {
+    std::vector<int> best;
+    int a[PGP_MAXK];
+    for (int i = 0; i < q.k; ++i) a[i] = i;
+    do {
+        std::vector<int> code;
+        code.reserve(q.k + q.k * q.k);
+        for (int i = 0; i < q.k; ++i) code.push_back(q.label[a[i]]);
+        for (int i = 0; i < q.k; ++i)
+            for (int j = i + 1; j < q.k; ++j) code.push_back(q.rel[a[i]][a[j]]);
+        if (best.empty() || code < best) best = code;
+    } while (std::next_permutation(a, a + q.k));
+    return best;
+}
+
+}  // namespace
+
+// Anti-edge expansion (flags & PG_BATCH_EXPAND_ANTI): a plan whose regular
+// vertices carry anti-edges A is counted as
+//   maps(E, A) = sum over T subset of A of (-1)^|T| maps(E + T, no anti-edges)
+// (inclusion-exclusion over the events "an anti-edge pair is adjacent", the
+// pattern-level form of the set differences of Section 4.2; with the Theorem
+// of Section 3.1.3 this covers vertex-induced patterns), maps(q) = |Aut(q)|
+// count(q), and count = maps / |Aut|.  Isomorphic terms of all plans are
+// merged and counted once by their own (edge-induced) plans.
+int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out) {
+    if (n_plans < 1 || n_plans > kMaxSlots) return pg_set_error(PG_EINVAL, "a batch holds 1..64 plans");
+    pg_batch *bb = new (std::nothrow) pg_batch();
+    if (!bb) return pg_set_error(PG_ENOMEM, "host allocation failed");
+    std::map<std::vector<int>, int> slot_of;
+    auto slot_for = [&](const PgPattern &q, bool is_plain_plan, const PgPlanHost *ready, int *slot) -> int {
+        std::vector<int> key = canonical(q);
+        key.push_back(is_plain_plan ? 0 : 1);
+        auto it = slot_of.find(key);
+        if (it != slot_of.end()) { *slot = it->second; return PG_OK; }
+        if ((int)bb->slot_plans.size() >= kMaxSlots) return PG_EUNSUPPORTED;
+        PgPlanHost h;
+        if (ready) {
+            h = *ready;
+        } else {
+            std::string err;
+            int rc = pg_plan_compile(q, false, h, err);
+            if (rc) return pg_set_error(rc, err);
+        }
+        bb->slot_plans.push_back(h);
+        *slot = (int)bb->slot_plans.size() - 1;
+        slot_of[key] = *slot;
+        return PG_OK;
+    };
+    bb->n_out = n_plans;
+    for (int p = 0; p < n_plans; ++p) {
+        const PgPlanHost &h = plans[p]->h;
+        std::vector<std::pair<int, int>> anti;
+        bool has_anti_vertex = false;
+        for (int u = 0; u < h.pat.k; ++u) {
+            has_anti_vertex |= h.pat.anti_vertex[u] != 0;
+            for (int w = u + 1; w < h.pat.k; ++w)
+                if (h.pat.rel[u][w] == 2) anti.push_back({u, w});
+        }
+        bb->out_first.push_back((int)bb->term_slot.size());
+        bool expanded = false;
+        // room for this plan's terms while keeping one slot per later plan
+        const int room = kMaxSlots - (int)bb->slot_plans.size() - (n_plans - p - 1);
+        if ((flags & PG_BATCH_EXPAND_ANTI) && !anti.empty() && !has_anti_vertex && anti.size() <= 6 &&
+            room >= (1 << anti.size())) {
+            // signed terms, merged by isomorphism class
+            std::map<int, long long> coef;
+            bool ok = true;
+            for (unsigned T = 0; T < (1u << anti.size()) && ok; ++T) {
+                PgPattern q = h.pat;
+                for (size_t i = 0; i < anti.size(); ++i)
+                    q.rel[anti[i].first][anti[i].second] = q.rel[anti[i].second][anti[i].first] =
+                        (T >> i & 1) ? 1 : 0;
+                int slot;
+                int rc = slot_for(q, false, nullptr, &slot);
+                if (rc == PG_EUNSUPPORTED) { ok = false; break; }
+                if (rc) { pg_batch_free(bb); return rc; }
+                coef[slot] += (__builtin_popcount(T) & 1) ? -1 : 1;
+            }
+            if (ok) {
+                for (auto &kv : coef)
+                    if (kv.second) {
+                        bb->term_slot.push_back(kv.first);
+                        bb->term_coef.push_back(kv.second * (long long)bb->slot_plans[kv.first].aut);
+                    }
+                bb->out_div.push_back(h.aut);
+                expanded = true;
+            } else {
+                bb->term_slot.resize(bb->out_first.back());
+                bb->term_coef.resize(bb->out_first.back());
+            }
+        }
+        if (!expanded) {
+            int slot;
+            int rc = slot_for(h.pat, true, &h, &slot);
+            if (rc) { pg_batch_free(bb); return rc == PG_EUNSUPPORTED ? pg_set_error(rc, "batch needs more than 64 counted patterns") : rc; }
+            bb->term_slot.push_back(slot);
+            bb->term_coef.push_back(1);
+            bb->out_div.push_back(1);
+        }
+        bb->out_n.push_back((int)bb->term_slot.size() - bb->out_first.back());
+    }
+    int rc = pg_batch_build_trie(bb);
+    if (rc) { pg_batch_free(bb); return rc; }
+    *out = bb;
+    return PG_OK;
+}
+
+int pg_batch_build_trie(pg_batch *b) {
+    const int n_plans = (int)b->slot_plans.size();
+    // tree with child lists, then laid out so that siblings are contiguous
+    struct TNode {
+        PgLevel spec;
+        int depth;
+        std::vector<int> kids;
+        std::vector<PgTrieTerm> terms;
+    };
+    std::vector<TNode> t;
+    std::vector<int> roots;
+    for (int i = 0; i < PGP_MAXK; ++i) b->out_bounded[i] = true;
+    b->n_slots = n_plans;
+    b->clique_k.assign(n_plans, 0);
+    for (int p = 0; p < n_plans; ++p) {
+        b->labeled = b->labeled || b->slot_plans[p].labeled;
+        const PgPlanHost &sp = b->slot_plans[p];
+        if (sp.is_clique && sp.pat.k >= 3) {
+            // unlabeled k-cliques go to the bitmap clique kernel (one launch
+            // for all clique sizes of the batch)
+            b->clique_k[p] = sp.pat.k;
+            b->clique_kmin = b->clique_kmin ? std::min(b->clique_kmin, sp.pat.k) : sp.pat.k;
+            b->clique_kmax = std::max(b->clique_kmax, sp.pat.k);
+            continue;
+        }
+        for (const PgOrder &o : b->slot_plans[p].orders) {
+            b->n_programs++;
+            b->n_levels_total += o.n_levels;
+            PgLevel root_spec;
+            std::memset(&root_spec, 0, sizeof(root_spec));
+            root_spec.group = 1;
+            root_spec.label = o.lv[0].label;
+            int cur = -1;
+            for (int r : roots)
+                if (same_spec(t[r].spec, root_spec)) cur = r;
+            if (cur < 0) {
+                t.push_back({root_spec, 0, {}, {}});
+                cur = (int)t.size() - 1;
+                roots.push_back(cur);
+            }
+            for (int l = 1; l < o.n_levels; ++l) {
+                const PgLevel spec = normalized(o.lv[l]);
+                const bool is_last = l == o.n_levels - 1;
+                const bool joint_pair = o.lv[o.n_levels - 1].joint && l >= o.n_levels - 2;
+                if (joint_pair) {
+                    b->any_level[l] = true; // both sets may be materialised
+                    b->out_bounded[l] = false;
+                } else if (!is_last) {
+                    b->any_level[l] = true;
+                    b->out_bounded[l] = b->out_bounded[l] && o.lv[l].out_bounded;
+                }
+                int nxt = -1;
+                for (int k : t[cur].kids)
+                    if (same_spec(t[k].spec, spec)) nxt = k;
+                if (nxt < 0) {
+                    t.push_back({spec, l, {}, {}});
+                    nxt = (int)t.size() - 1;
+                    t[cur].kids.push_back(nxt);
+                }
+                cur = nxt;
+            }
+            t[cur].terms.push_back({p, o.n_levels == 1 ? 1 : o.lv[o.n_levels - 1].group});
+        }
+    }
+    // layout: roots first, then breadth-first so each node's children are contiguous
+    for (auto &n : t)
+        std::stable_partition(n.kids.begin(), n.kids.end(), [&](int k) { return !t[k].spec.joint; });
+    std::vector<int> order(roots.begin(), roots.end());
+    for (size_t i = 0; i < order.size(); ++i)
+        for (int k : t[order[i]].kids) order.push_back(k);
+    std::vector<int> pos(t.size());
+    for (size_t i = 0; i < order.size(); ++i) pos[order[i]] = (int)i;
+    b->nodes.resize(order.size());
+    for (size_t i = 0; i < order.size(); ++i) {
+        const TNode &n = t[order[i]];
+        PgTrieNode &d = b->nodes[i];
+        std::memset(&d, 0, sizeof(d));
+        d.spec = n.spec;
+        d.depth = n.depth;
+        int nj = 0;
+        for (int k : n.kids) nj += t[k].spec.joint ? 1 : 0;
+        d.n_children = (int)n.kids.size() - nj;
+        d.n_joint = nj;
+        d.first_child = n.kids.empty() ? 0 : pos[n.kids[0]];
+        for (size_t k = 1; k < n.kids.size(); ++k)
+            if (pos[n.kids[k]] != d.first_child + (int)k) return pg_set_error(PG_EINVAL, "internal: trie layout");
+        d.first_term = (int)b->terms.size();
+        d.n_terms = (int)n.terms.size();
+        for (auto &tm : n.terms) b->terms.push_back(tm);
+    }
+    b->n_roots = (int)roots.size();
+    const size_t nb = b->nodes.size() * sizeof(PgTrieNode), tb = std::max<size_t>(1, b->terms.size()) * sizeof(PgTrieTerm);
+    auto up = [](void **dst, const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(dst, bytes ? bytes : 16);
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        return e;
+    };
+    cudaError_t e;
+    if ((e = up((void **)&b->d_nodes, b->nodes.data(), nb)) != cudaSuccess ||
+        (e = up((void **)&b->d_terms, b->terms.data(), b->terms.size() * sizeof(PgTrieTerm))) != cudaSuccess ||
+        (e = up((void **)&b->d_term_slot, b->term_slot.data(), b->term_slot.size() * sizeof(int))) != cudaSuccess ||
+        (e = up((void **)&b->d_term_coef, b->term_coef.data(), b->term_coef.size() * sizeof(long long))) != cudaSuccess ||
+        (e = up((void **)&b->d_out_first, b->out_first.data(), b->out_first.size() * sizeof(int))) != cudaSuccess ||
+        (e = up((void **)&b->d_out_n, b->out_n.data(), b->out_n.size() * sizeof(int))) != cudaSuccess ||
+        (e = up((void **)&b->d_out_div, b->out_div.data(), b->out_div.size() * sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_slot_counts, 2 * sizeof(unsigned long long) * (size_t)b->n_slots)) != cudaSuccess)
+        return pg_cuda_error(e, "batch upload");
+    (void)tb;
+    return PG_OK;
+}
+
+void pg_batch_free(pg_batch *b) {
+    if (!b) return;
+    for (void *p : {(void *)b->d_nodes, (void *)b->d_terms, (void *)b->d_term_slot, (void *)b->d_term_coef,
+                    (void *)b->d_out_first, (void *)b->d_out_n, (void *)b->d_out_div, (void *)b->d_slot_counts})
+        if (p) cudaFree(p);
+    delete b;
+}
+
+int pg_batch_slots(const pg_batch *b) { return b->n_out; }
+bool pg_batch_labeled(const pg_batch *b) { return b->labeled; }
+
+void pg_batch_stats(const pg_batch *b, int *nodes, int *programs, int *levels_total) {
+    *nodes = (int)b->nodes.size();
+    *programs = b->n_programs;
+    *levels_total = b->n_levels_total;
+}
+
+namespace {
+long long batch_layout(const pg_graph *g, const pg_batch *b, long long *off) {
+    const long long cap_out = (g->max_out + 31) & ~31ll, cap_all = (g->max_deg + 31) & ~31ll;
+    long long total = 0;
+    for (int l = 0; l < PGP_MAXK; ++l) {
+        off[l] = total;
+        if (b->any_level[l]) total += b->out_bounded[l] ? cap_out : cap_all;
+    }
+    return total;
+}
+}  // namespace
+
+size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b) {
+    long long off[PGP_MAXK];
+    size_t bytes = (size_t)batched_grid(g) * kWarps * (size_t)batch_layout(g, b, off) * sizeof(int);
+    if (b->clique_kmax) bytes = std::max(bytes, pg_clique_scratch_bytes(g));
+    return bytes;
+}
+
+int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts_dev, int queue_slot,
+                      cudaStream_t s) {
+    if (g->n == 0) {
+        PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_out, s));
+        return PG_OK;
+    }
+    BatchArgs a;
+    a.g = g->d;
+    a.nodes = b->d_nodes;
+    a.terms = b->d_terms;
+    a.n_roots = b->n_roots;
+    a.n_slots = b->n_slots;
+    a.scratch = (int *)g->scratch;
+    a.warp_stride = batch_layout(g, b, a.lvl_off);
+    a.queue = g->queues + queue_slot;
+    a.n = (int)g->n;
+    a.counts = b->d_slot_counts;
+    PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
+    if (b->n_roots > 0) {
+        PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+        k_count_batched<<<batched_grid(g), kBlock, 0, s>>>(a);
+        PG_CUDA(cudaGetLastError());
+    }
+    if (b->clique_kmax) {
+        if (g->max_out >= 65536) return pg_set_error(PG_EUNSUPPORTED, "clique kernel needs out-degrees below 65536");
+        const int span = b->clique_kmax - b->clique_kmin + 1;
+        PG_CUDA(cudaMemsetAsync(g->tmp_counts, 0, 2 * sizeof(unsigned long long) * span, s));
+        int rc = pg_launch_clique(g, b->clique_kmin, b->clique_kmax, g->tmp_counts, queue_slot + 2, s);
+        if (rc) return rc;
+        for (int p = 0; p < b->n_slots; ++p)
+            if (b->clique_k[p])
+                PG_CUDA(cudaMemcpyAsync(b->d_slot_counts + 2 * p, g->tmp_counts + 2 * (b->clique_k[p] - b->clique_kmin),
+                                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    }
+    k_combine<<<(b->n_out + 63) / 64, 64, 0, s>>>(b->d_slot_counts, b->d_term_slot, b->d_term_coef, b->d_out_first,
+                                                 b->d_out_n, b->d_out_div, b->n_out, counts_dev);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}

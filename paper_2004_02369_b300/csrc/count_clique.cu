@@ -142,7 +142,7 @@ __device__ void build_rows(const DevGraph &g, const Tile &t, int d, int tid, int
                 if (t.list[mid] < x) a = mid + 1; else b = mid;
             }
             if (a < i && t.list[a] == x) atomicOr(&t.rows[(size_t)i * t.ws + (a >> 5)], 1u << (a & 31));
-        } else if (contains_g(nu, du, t.list[k])) {
+        } else if (in_slice(g, Slice{nu, du, t.list[i]}, t.list[k])) {
             atomicOr(&t.rows[(size_t)i * t.ws + (k >> 5)], 1u << (k & 31));
         }
     }

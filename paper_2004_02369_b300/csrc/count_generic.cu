@@ -18,9 +18,11 @@
 // with __ballot_sync/__popc) into a per-warp scratch buffer.  The last level
 // is counted, by inclusion-exclusion over its difference lists when that
 // touches fewer elements than filtering the driver list.
-#include "device_sets.cuh"
+#include "level_ops.cuh"
 
 namespace {
+
+using namespace pgk;
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kBlock = kWarpsPerBlock * 32;
@@ -37,148 +39,6 @@ struct GenericArgs {
     int persistent;             // 0: one task per warp, no queue
     unsigned long long *counts; // (low, high)
 };
-
-struct LevelRange {
-    int lo, hi; // open interval (lo, hi); lo = -1 / hi = INT_MAX when unbounded
-};
-
-__device__ __forceinline__ LevelRange level_range(const PgLevel &L, const int *m) {
-    LevelRange r{-1, 0x7fffffff};
-    for (int i = 0; i < L.n_lo; ++i) r.lo = max(r.lo, m[L.lo_src[i]]);
-    for (int i = 0; i < L.n_hi; ++i) r.hi = min(r.hi, m[L.hi_src[i]]);
-    return r;
-}
-
-// x passes label and exclusion tests of level L
-__device__ __forceinline__ bool pass_label_excl(const DevGraph &g, const PgLevel &L, const int *m, int x) {
-    bool ok = true;
-    for (int i = 0; i < L.n_excl; ++i) ok &= (x != m[L.excl_src[i]]);
-    if (ok && L.label >= 0) ok = (__ldg(&g.vinfo[x].w) == L.label);
-    return ok;
-}
-
-// Materialise the candidate set of (non-last) level L into buf; returns size.
-__device__ int fill_level(const DevGraph &g, const PgLevel &L, const int *m, int *buf, int lane) {
-    const LevelRange r = level_range(L, m);
-    if (r.lo + 1 >= r.hi) return 0;
-    Slice s[PGP_MAXK];
-    int drv = 0;
-    for (int i = 0; i < L.n_int; ++i) {
-        const int4 vi = __ldg(&g.vinfo[m[L.int_src[i]]]);
-        s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi);
-        if (s[i].len < s[drv].len) drv = i;
-    }
-    const Slice d = s[drv];
-    int n_out = 0;
-    for (int base = 0; base < d.len; base += 32) {
-        const int idx = base + lane;
-        bool ok = idx < d.len;
-        int x = 0;
-        if (ok) {
-            x = __ldg(d.p + idx);
-            for (int i = 0; i < L.n_int && ok; ++i)
-                if (i != drv) ok = contains_g(s[i].p, s[i].len, x);
-            for (int i = 0; i < L.n_diff && ok; ++i) {
-                const int4 vi = __ldg(&g.vinfo[m[L.diff_src[i]]]);
-                ok = !contains_g(adj_of(g, vi), vi.y, x);
-            }
-            if (ok) ok = pass_label_excl(g, L, m, x);
-        }
-        const unsigned bal = __ballot_sync(PG_FULL, ok);
-        if (ok) buf[n_out + __popc(bal & ((1u << lane) - 1))] = x;
-        n_out += __popc(bal);
-    }
-    __syncwarp();
-    return n_out;
-}
-
-// |S| of the last level (before C(|S|, g)).
-__device__ unsigned long long count_last(const DevGraph &g, const PgLevel &L, const int *m, int lane) {
-    const LevelRange r = level_range(L, m);
-    if (r.lo + 1 >= r.hi) return 0;
-    Slice s[2 * PGP_MAXK];
-    const int ni = L.n_int, nd = L.n_diff;
-    int drv = 0;
-    for (int i = 0; i < ni; ++i) {
-        const int4 vi = __ldg(&g.vinfo[m[L.int_src[i]]]);
-        s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi);
-        if (s[i].len < s[drv].len) drv = i;
-    }
-    for (int j = 0; j < nd; ++j) {
-        const int4 vi = __ldg(&g.vinfo[m[L.diff_src[j]]]);
-        s[ni + j] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi);
-    }
-    const bool labeled = L.label >= 0;
-    // cost of filtering the driver directly vs inclusion-exclusion
-    long long direct = (long long)s[drv].len * (ni - 1 + nd + (labeled ? 1 : 0));
-    long long ie = 0;
-    for (unsigned T = 1; T < (1u << nd); ++T) {
-        int mn = s[drv].len, terms = ni - 1 + (labeled ? 1 : 0);
-        for (int j = 0; j < nd; ++j)
-            if (T >> j & 1) { mn = min(mn, s[ni + j].len); ++terms; }
-        ie += (long long)mn * terms;
-    }
-    if (labeled || ni > 1) ie += (long long)s[drv].len * (ni - 1 + (labeled ? 1 : 0));
-    long long total = 0;
-    if (nd == 0 || direct <= ie) {
-        const Slice d = s[drv];
-        unsigned long long c = 0;
-        for (int base = 0; base < d.len; base += 32) {
-            const int idx = base + lane;
-            bool ok = idx < d.len;
-            if (ok) {
-                const int x = __ldg(d.p + idx);
-                for (int i = 0; i < ni && ok; ++i)
-                    if (i != drv) ok = contains_g(s[i].p, s[i].len, x);
-                for (int j = 0; j < nd && ok; ++j) ok = !contains_g(s[ni + j].p, s[ni + j].len, x);
-                if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
-            }
-            c += __popc(__ballot_sync(PG_FULL, ok));
-        }
-        total = (long long)c;
-    } else {
-        // |A \ (B1 u ... u Bd)| = sum over T subset of diffs of (-1)^|T| |A n B_T|
-        for (unsigned T = 0; T < (1u << nd); ++T) {
-            int dd = drv;
-            for (int j = 0; j < nd; ++j)
-                if ((T >> j & 1) && s[ni + j].len < s[dd].len) dd = ni + j;
-            const Slice d = s[dd];
-            long long term;
-            if (ni == 1 && T == 0 && !labeled) {
-                term = d.len;
-            } else {
-                unsigned long long c = 0;
-                for (int base = 0; base < d.len; base += 32) {
-                    const int idx = base + lane;
-                    bool ok = idx < d.len;
-                    if (ok) {
-                        const int x = __ldg(d.p + idx);
-                        for (int i = 0; i < ni && ok; ++i)
-                            if (i != dd) ok = contains_g(s[i].p, s[i].len, x);
-                        for (int j = 0; j < nd && ok; ++j)
-                            if ((T >> j & 1) && ni + j != dd) ok = contains_g(s[ni + j].p, s[ni + j].len, x);
-                        if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
-                    }
-                    c += __popc(__ballot_sync(PG_FULL, ok));
-                }
-                term = (long long)c;
-            }
-            total += (__popc(T) & 1) ? -term : term;
-        }
-    }
-    // injectivity: remove earlier images that fall inside S
-    // (earlier images are pairwise distinct, so each is removed at most once)
-    bool in = false;
-    if (lane < L.n_excl) {
-        const int x = m[L.excl_src[lane]];
-        in = x > r.lo && x < r.hi;
-        for (int i = 0; i < ni && in; ++i) in = contains_g(s[i].p, s[i].len, x);
-        for (int j = 0; j < nd && in; ++j) in = !contains_g(s[ni + j].p, s[ni + j].len, x);
-        if (in && labeled) in = (__ldg(&g.vinfo[x].w) == L.label);
-    }
-    total -= (long long)__popc(__ballot_sync(PG_FULL, in));
-    return (unsigned long long)total;
-}
 
 __device__ unsigned __int128 run_task(const GenericArgs &a, int v, const PgOrder &ord, int *wbuf, int lane) {
     const DevGraph &g = a.g;

@@ -10,6 +10,7 @@
 struct Slice {
     const int *p;
     int len;
+    int owner; // vertex whose adjacency list this is, -1 for scratch
 };
 
 __device__ __forceinline__ const int *adj_of(const DevGraph &g, int4 vi) {
@@ -39,14 +40,39 @@ __device__ __forceinline__ bool contains_g(const int *__restrict__ a, int len, i
     return __ldg(base) == x;
 }
 
+// Same searches on scratch written earlier in this kernel (coherent loads,
+// never the read-only path).
+__device__ __forceinline__ int lower_bound_s(const int *a, int len, int x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool contains_s(const int *a, int len, int x) {
+    const int i = lower_bound_s(a, len, x);
+    return i < len && a[i] == x;
+}
+
 // Restrict a sorted list to values in the open interval (lo, hi).
-__device__ __forceinline__ Slice bound_slice(const int *p, int len, int lo, int hi) {
+__device__ __forceinline__ Slice bound_slice(const int *p, int len, int lo, int hi, int owner = -1) {
     const int b = lo < 0 ? 0 : lower_bound_g(p, len, lo + 1);
     const int e = hi == 0x7fffffff ? len : lower_bound_g(p, len, hi);
     Slice s;
     s.p = p + b;
     s.len = e > b ? e - b : 0;
+    s.owner = owner;
     return s;
+}
+
+// x in the slice, for x known to lie inside the slice's value bounds: a bit
+// test when the slice belongs to a hub, else a binary search.
+__device__ __forceinline__ bool in_slice(const DevGraph &g, const Slice &s, int x) {
+    if (s.owner >= 0 && s.owner < g.n_hubs)
+        return (__ldg(g.hubbits + (size_t)s.owner * g.hub_stride + (x >> 5)) >> (x & 31)) & 1u;
+    return contains_g(s.p, s.len, x);
 }
 
 // 128-bit exact accumulation into two 64-bit words (low, high).

@@ -10,6 +10,8 @@
 // and scan: this runs once per graph load, outside the matching path.
 #include <cub/cub.cuh>
 
+#include <vector>
+
 #include "pg_internal.h"
 
 namespace {
@@ -132,6 +134,20 @@ __global__ void k_heavy_ids(const unsigned long long *sorted, int64_t count, int
     if (i < count) out[i] = (int)(sorted[i] & 0xffffffffull);
 }
 
+// hub bitmaps: one warp per hub row, bits of its neighbours
+__global__ void k_hub_bits(const int4 *vinfo, const int *adj, int n_hubs, int stride, unsigned *bits) {
+    const int lane = threadIdx.x & 31;
+    const int r = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (r >= n_hubs) return;
+    const int4 vi = vinfo[r];
+    const int *a = adj + ((size_t)(unsigned)vi.x << 2);
+    unsigned *row = bits + (size_t)r * stride;
+    for (int i = lane; i < vi.y; i += 32) {
+        const int x = a[i];
+        atomicOr(row + (x >> 5), 1u << (x & 31));
+    }
+}
+
 inline unsigned grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;
     if (g < 1) g = 1;
@@ -246,6 +262,25 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     g->max_out = hm[1];
     g->n_labels = d_labels ? hm[2] + 1 : 0;
 
+    // hub bitmaps for the highest-degree ranks
+    if (n > 0) {
+        std::vector<int4> head(std::min<int64_t>(n, PG_MAX_HUBS));
+        PG_CUDA(cudaMemcpyAsync(head.data(), g->vinfo, head.size() * sizeof(int4), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        int h = 0;
+        while (h < (int)head.size() && head[h].y >= PG_HUB_MIN_DEGREE) ++h;
+        const int stride = (int)((n + 31) / 32);
+        while (h > 0 && (int64_t)h * stride * 4 > (2ll << 30)) --h; // at most 2 GiB
+        g->n_hubs = h;
+        g->hub_stride = stride;
+        if (h > 0) {
+            PG_CUDA(cudaMalloc(&g->hubbits, (size_t)h * stride * sizeof(unsigned)));
+            PG_CUDA(cudaMemsetAsync(g->hubbits, 0, (size_t)h * stride * sizeof(unsigned), s));
+            k_hub_bits<<<grid_for((int64_t)h * 32, kBlock), kBlock, 0, s>>>(g->vinfo, g->adj, h, stride, g->hubbits);
+            PG_CUDA(cudaGetLastError());
+        }
+    }
+
     // heavy clique start vertices (reuse the vertex key buffers)
     if (n > 0) {
         PG_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
@@ -262,6 +297,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
         PG_CUDA(cudaGetLastError());
         PG_CUDA(cudaStreamSynchronize(s));
     }
-    g->bytes_device = (int64_t)(nn * (sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int));
+    g->bytes_device = (int64_t)(nn * (sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int)) +
+                      (int64_t)g->n_hubs * g->hub_stride * 4 + g->n_heavy * 4;
     return PG_OK;
 }

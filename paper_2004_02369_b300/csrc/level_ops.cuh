@@ -1,0 +1,258 @@
+// Level operations of the plan interpreter, shared by the single-plan and
+// the batched (trie) kernels.  A level's candidate set is
+//   S = (/\ adj(m[int_src])) \ (\/ adj(m[diff_src])) within (max m[lo_src],
+//       min m[hi_src]), label-filtered, without m[excl_src]
+// (Section 4.1 matching orders with partial-order bounds; Section 4.2
+// anti-edges as set differences; Section 5.1 sorted-list set operations).
+#pragma once
+#include "device_sets.cuh"
+
+namespace pgk {
+
+struct LevelRange {
+    int lo, hi; // open interval (lo, hi); lo = -1 / hi = INT_MAX when unbounded
+};
+
+__device__ __forceinline__ LevelRange level_range(const PgLevel &L, const int *m) {
+    LevelRange r{-1, 0x7fffffff};
+    for (int i = 0; i < L.n_lo; ++i) r.lo = max(r.lo, m[L.lo_src[i]]);
+    for (int i = 0; i < L.n_hi; ++i) r.hi = min(r.hi, m[L.hi_src[i]]);
+    return r;
+}
+
+// x passes label and exclusion tests of level L
+__device__ __forceinline__ bool pass_label_excl(const DevGraph &g, const PgLevel &L, const int *m, int x) {
+    bool ok = true;
+    for (int i = 0; i < L.n_excl; ++i) ok &= (x != m[L.excl_src[i]]);
+    if (ok && L.label >= 0) ok = (__ldg(&g.vinfo[x].w) == L.label);
+    return ok;
+}
+
+// Materialise the candidate set of (non-last) level L into buf; returns size.
+static __device__ __noinline__ int fill_level(const DevGraph &g, const PgLevel &L, const int *m, int *buf, int lane) {
+    const LevelRange r = level_range(L, m);
+    if (r.lo + 1 >= r.hi) return 0;
+    Slice s[PGP_MAXK];
+    int drv = 0;
+    for (int i = 0; i < L.n_int; ++i) {
+        const int w = m[L.int_src[i]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi, w);
+        if (s[i].len < s[drv].len) drv = i;
+    }
+    const Slice d = s[drv];
+    int n_out = 0;
+    for (int base = 0; base < d.len; base += 32) {
+        const int idx = base + lane;
+        bool ok = idx < d.len;
+        int x = 0;
+        if (ok) {
+            x = __ldg(d.p + idx);
+            for (int i = 0; i < L.n_int && ok; ++i)
+                if (i != drv) ok = in_slice(g, s[i], x);
+            for (int i = 0; i < L.n_diff && ok; ++i) {
+                const int w = m[L.diff_src[i]];
+                const int4 vi = __ldg(&g.vinfo[w]);
+                ok = !in_slice(g, Slice{adj_of(g, vi), vi.y, w}, x);
+            }
+            if (ok) ok = pass_label_excl(g, L, m, x);
+        }
+        const unsigned bal = __ballot_sync(PG_FULL, ok);
+        if (ok) buf[n_out + __popc(bal & ((1u << lane) - 1))] = x;
+        n_out += __popc(bal);
+    }
+    __syncwarp();
+    return n_out;
+}
+
+// |S| of the last level (before C(|S|, g)).
+static __device__ __noinline__ unsigned long long count_last(const DevGraph &g, const PgLevel &L, const int *m, int lane) {
+    const LevelRange r = level_range(L, m);
+    if (r.lo + 1 >= r.hi) return 0;
+    Slice s[2 * PGP_MAXK];
+    const int ni = L.n_int, nd = L.n_diff;
+    int drv = 0;
+    for (int i = 0; i < ni; ++i) {
+        const int w = m[L.int_src[i]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi, w);
+        if (s[i].len < s[drv].len) drv = i;
+    }
+    for (int j = 0; j < nd; ++j) {
+        const int w = m[L.diff_src[j]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        s[ni + j] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi, w);
+    }
+    const bool labeled = L.label >= 0;
+    // cost of filtering the driver directly vs inclusion-exclusion
+    long long direct = (long long)s[drv].len * (ni - 1 + nd + (labeled ? 1 : 0));
+    long long ie = 0;
+    for (unsigned T = 1; T < (1u << nd); ++T) {
+        int mn = s[drv].len, terms = ni - 1 + (labeled ? 1 : 0);
+        for (int j = 0; j < nd; ++j)
+            if (T >> j & 1) { mn = min(mn, s[ni + j].len); ++terms; }
+        ie += (long long)mn * terms;
+    }
+    if (labeled || ni > 1) ie += (long long)s[drv].len * (ni - 1 + (labeled ? 1 : 0));
+    long long total = 0;
+    if (nd == 0 || direct <= ie) {
+        const Slice d = s[drv];
+        unsigned long long c = 0;
+        for (int base = 0; base < d.len; base += 32) {
+            const int idx = base + lane;
+            bool ok = idx < d.len;
+            if (ok) {
+                const int x = __ldg(d.p + idx);
+                for (int i = 0; i < ni && ok; ++i)
+                    if (i != drv) ok = in_slice(g, s[i], x);
+                for (int j = 0; j < nd && ok; ++j) ok = !in_slice(g, s[ni + j], x);
+                if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
+            }
+            c += __popc(__ballot_sync(PG_FULL, ok));
+        }
+        total = (long long)c;
+    } else {
+        // |A \ (B1 u ... u Bd)| = sum over T subset of diffs of (-1)^|T| |A n B_T|
+        for (unsigned T = 0; T < (1u << nd); ++T) {
+            int dd = drv;
+            for (int j = 0; j < nd; ++j)
+                if ((T >> j & 1) && s[ni + j].len < s[dd].len) dd = ni + j;
+            const Slice d = s[dd];
+            long long term;
+            if (ni == 1 && T == 0 && !labeled) {
+                term = d.len;
+            } else {
+                unsigned long long c = 0;
+                for (int base = 0; base < d.len; base += 32) {
+                    const int idx = base + lane;
+                    bool ok = idx < d.len;
+                    if (ok) {
+                        const int x = __ldg(d.p + idx);
+                        for (int i = 0; i < ni && ok; ++i)
+                            if (i != dd) ok = in_slice(g, s[i], x);
+                        for (int j = 0; j < nd && ok; ++j)
+                            if ((T >> j & 1) && ni + j != dd) ok = in_slice(g, s[ni + j], x);
+                        if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
+                    }
+                    c += __popc(__ballot_sync(PG_FULL, ok));
+                }
+                term = (long long)c;
+            }
+            total += (__popc(T) & 1) ? -term : term;
+        }
+    }
+    // injectivity: remove earlier images that fall inside S
+    // (earlier images are pairwise distinct, so each is removed at most once)
+    bool in = false;
+    if (lane < L.n_excl) {
+        const int x = m[L.excl_src[lane]];
+        in = x > r.lo && x < r.hi;
+        for (int i = 0; i < ni && in; ++i) in = in_slice(g, s[i], x);
+        for (int j = 0; j < nd && in; ++j) in = !in_slice(g, s[ni + j], x);
+        if (in && labeled) in = (__ldg(&g.vinfo[x].w) == L.label);
+    }
+    total -= (long long)__popc(__ballot_sync(PG_FULL, in));
+    return (unsigned long long)total;
+}
+
+
+// A set given by a level spec is a plain bounded slice of one adjacency list
+// (minus excluded images) when it has one intersected list, no differences
+// and no label: its elements and ranks are read off the list directly.
+__device__ __forceinline__ bool is_slice(const PgLevel &L) {
+    return L.n_int == 1 && L.n_diff == 0 && L.label < 0;
+}
+
+__device__ __forceinline__ Slice level_slice(const DevGraph &g, const PgLevel &L, const int *m) {
+    const LevelRange r = level_range(L, m);
+    const int w = m[L.int_src[0]];
+    const int4 vi = __ldg(&g.vinfo[w]);
+    if (r.lo + 1 >= r.hi) return Slice{adj_of(g, vi), 0, w};
+    return bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi, w);
+}
+
+// Joint count of the last two levels: X (single non-core vertex x at level
+// xl) and Y (single non-core vertex y whose spec refers to x only through
+// the partial order or injectivity).  With Y' = Y without those references:
+//   no order between x, y:  |SX| |SY'| - |SX n SY'|   (x != y)
+//   y > x (or y < x):       sum over x in SX of |SY' above (below) x|
+// computed by walking the smaller set and rank queries in the larger one
+// (binary search in the list slice, or in the materialised set).
+static __device__ __noinline__ unsigned long long count_joint(const DevGraph &g, const PgLevel &X, const PgLevel &Y,
+                                                              int xl, const int *m, int *bufA, int *bufB, int lane) {
+    PgLevel Yp = Y;
+    int rel = 0;
+    bool excl_xy = false;
+    {
+        int n = 0;
+        for (int i = 0; i < Y.n_lo; ++i)
+            if (Y.lo_src[i] == xl) rel = 1; else Yp.lo_src[n++] = Y.lo_src[i];
+        Yp.n_lo = (int8_t)n;
+        n = 0;
+        for (int i = 0; i < Y.n_hi; ++i)
+            if (Y.hi_src[i] == xl) rel = -1; else Yp.hi_src[n++] = Y.hi_src[i];
+        Yp.n_hi = (int8_t)n;
+        n = 0;
+        for (int i = 0; i < Y.n_excl; ++i)
+            if (Y.excl_src[i] == xl) excl_xy = true; else Yp.excl_src[n++] = Y.excl_src[i];
+        Yp.n_excl = (int8_t)n;
+    }
+    const unsigned long long nX = count_last(g, X, m, lane);
+    if (nX == 0) return 0;
+    const unsigned long long nY = count_last(g, Yp, m, lane);
+    if (nY == 0) return 0;
+    if (rel == 0 && !excl_xy) return nX * nY;
+    const bool iterX = nX <= nY;
+    const PgLevel &I = iterX ? X : Yp;
+    const PgLevel &Q = iterX ? Yp : X;
+    // elements of I
+    Slice is;
+    const bool islice = is_slice(I);
+    if (islice) is = level_slice(g, I, m);
+    else is = Slice{bufA, fill_level(g, I, m, bufA, lane), -1};
+    // query structure of Q, and Q's excluded images that sit in its slice
+    Slice qs;
+    const bool qslice = is_slice(Q);
+    int qx[PGP_MAXK];
+    int nqx = 0;
+    if (qslice) {
+        qs = level_slice(g, Q, m);
+        const LevelRange r = level_range(Q, m);
+        for (int i = 0; i < Q.n_excl; ++i) {
+            const int v = m[Q.excl_src[i]];
+            if (v > r.lo && v < r.hi && contains_g(qs.p, qs.len, v)) qx[nqx++] = v;
+        }
+    } else {
+        qs = Slice{bufB, fill_level(g, Q, m, bufB, lane), -1};
+    }
+    // side: count Q elements greater than e, or smaller than e
+    const bool greater = (iterX && rel > 0) || (!iterX && rel < 0);
+    unsigned long long acc = 0;
+    for (int base = 0; base < is.len; base += 32) {
+        const int idx = base + lane;
+        if (idx < is.len) {
+            const int e = islice ? __ldg(is.p + idx) : is.p[idx];
+            bool skip = false;
+            if (islice)
+                for (int i = 0; i < I.n_excl; ++i) skip |= e == m[I.excl_src[i]];
+            if (!skip) {
+                if (rel == 0) {
+                    bool in = qslice ? contains_g(qs.p, qs.len, e) : contains_s(qs.p, qs.len, e);
+                    for (int i = 0; i < nqx; ++i) in &= e != qx[i];
+                    acc += in ? 1 : 0;
+                } else {
+                    // elements < e
+                    const int pos = qslice ? lower_bound_g(qs.p, qs.len, e) : lower_bound_s(qs.p, qs.len, e);
+                    const bool has = pos < qs.len && (qslice ? __ldg(qs.p + pos) : qs.p[pos]) == e;
+                    long long c = greater ? (long long)(qs.len - pos - (has ? 1 : 0)) : (long long)pos;
+                    for (int i = 0; i < nqx; ++i) c -= greater ? (qx[i] > e) : (qx[i] < e);
+                    acc += (unsigned long long)c;
+                }
+            }
+        }
+    }
+    acc = warp_sum_u64(acc);
+    return rel == 0 ? nX * nY - acc : acc;
+}
+
+}  // namespace pgk

@@ -21,7 +21,16 @@ struct DevGraph {
     int max_deg;
     int max_out;
     int labeled;
+    // Membership bitmaps of the n_hubs highest-degree vertices (ranks
+    // 0..n_hubs-1): bit x of row r is set iff x is in adj(r).  Lets set
+    // operations test "x in adj(hub)" with one load instead of a binary search.
+    const unsigned *hubbits;
+    int n_hubs;
+    int hub_stride; // words per row = ceil(n / 32)
 };
+
+#define PG_HUB_MIN_DEGREE 1024
+#define PG_MAX_HUBS 512
 
 #define PG_PAD 0x7fffffff
 #define PG_CLIQUE_LIGHT_D 64 // out-degree up to which one warp handles a clique start vertex
@@ -31,8 +40,10 @@ struct pg_graph {
     int4 *vinfo = nullptr;
     int *adj = nullptr;
     int *rank = nullptr; // original id -> rank
+    unsigned *hubbits = nullptr;
     int64_t n = 0, m = 0, adj_entries = 0;
     int64_t max_deg = 0, max_out = 0;
+    int n_hubs = 0, hub_stride = 0;
     int32_t labeled = 0, n_labels = 0;
     int device = 0;
     int num_sms = 0;
@@ -44,14 +55,20 @@ struct pg_graph {
     // vertices with out-degree > PG_CLIQUE_LIGHT_D, by out-degree descending
     int *heavy = nullptr;
     int64_t n_heavy = 0;
+    // last batch built by pg_count_ex for a plan list (keyed by plan serials)
+    pg_batch *batch_cache = nullptr;
+    std::vector<uint64_t> batch_key;
     int64_t bytes_device = 0;
 };
 
 #define PG_MAX_QUEUES 64
 #define PG_STATIC_SCRATCH_BYTES (32u << 20) // fixed scratch of pg_count_cliques_noalloc
 
+struct pg_batch;
+
 struct pg_plan {
     PgPlanHost h;
+    uint64_t serial = 0;         // unique per compiled plan (batch cache key)
     PgOrder *d_orders = nullptr; // device copy of h.orders
     int kernel_auto = PG_KERNEL_GENERIC;
 };
@@ -85,5 +102,16 @@ int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts
                      int queue_slot, cudaStream_t s);
 size_t pg_clique_scratch_bytes(const pg_graph *g);
 size_t pg_clique_slab_bytes(const pg_graph *g);
+
+// count_batched.cu: many plans, one launch over a shared prefix tree
+int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out);
+int pg_batch_build_trie(pg_batch *b);
+void pg_batch_free(pg_batch *b);
+void pg_batch_stats(const pg_batch *b, int *nodes, int *programs, int *levels_total);
+int pg_batch_slots(const pg_batch *b);
+bool pg_batch_labeled(const pg_batch *b);
+size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b);
+int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts_dev, int queue_slot,
+                      cudaStream_t s);
 int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
                         unsigned long long *queue, void *slabs, long long max_warps, cudaStream_t s);

@@ -127,6 +127,45 @@ std::vector<std::vector<int>> noncore_groups(const PgPattern &p, const Closure &
     return groups;
 }
 
+// Core levels, summed over all matching orders of `core`, that have no
+// earlier-bound true neighbour placed above them in the order.  The start
+// vertex binds the highest position, then the highest-position core vertex
+// adjacent to a bound one (the exploration order used below); a level with a
+// bound neighbour above it draws candidates from that neighbour's
+// out-neighbourhood.
+int core_scan_cost(const PgPattern &p, const Closure &cl, uint32_t core_mask) {
+    std::vector<int> seq;
+    for (int u = 0; u < p.k; ++u)
+        if (core_mask >> u & 1) seq.push_back(u);
+    const int c = (int)seq.size();
+    int cost = 0;
+    do {
+        int pos[PGP_MAXK];
+        for (int i = 0; i < c; ++i) pos[seq[i]] = i;
+        bool ok = true;
+        for (int a : seq)
+            for (int b : seq)
+                if (cl.less[a][b] && pos[a] > pos[b]) ok = false;
+        if (!ok) continue;
+        uint32_t bound = 1u << seq[c - 1];
+        for (int step = 1; step < c; ++step) {
+            int pick = -1;
+            for (int i = c - 1; i >= 0 && pick < 0; --i) {
+                const int u = seq[i];
+                if (bound >> u & 1) continue;
+                for (int x = 0; x < p.k; ++x)
+                    if ((bound >> x & 1) && p.rel[u][x] == 1) { pick = u; break; }
+            }
+            bool cheap = false;
+            for (int x = 0; x < p.k; ++x)
+                if ((bound >> x & 1) && p.rel[pick][x] == 1 && pos[x] > pos[pick]) cheap = true;
+            cost += cheap ? 0 : 1;
+            bound |= 1u << pick;
+        }
+    } while (std::next_permutation(seq.begin(), seq.end()));
+    return cost;
+}
+
 }  // namespace
 
 int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, std::string &err) {
@@ -201,15 +240,18 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
 
     // ---- minConnectedVertexCover (Sections 4.1, 4.2) ------------------------
     // covers every edge and every anti-edge between regular vertices, connected
-    // through true edges; ties broken by fewest non-core groups, then by
-    // preferring non-core vertices below core vertices in the partial order
-    // (their candidate sets are then bounded above: higher-degree neighbours
-    // under the degree ranking), then by the smallest vertex mask.
+    // through true edges.  Among minimum covers: fewest core levels, over all
+    // matching orders, whose candidates cannot be drawn from the
+    // out-neighbourhood of an already bound neighbour (under the degree
+    // ranking such a level scans a high-degree vertex's lower-degree
+    // neighbours); then fewest non-core groups; then non-core vertices below
+    // core vertices in the partial order (their sets are bounded above); then
+    // the smallest vertex mask.
     uint32_t best = 0;
     if (out.n_regular == 1) {
         best = reg;
     } else {
-        int best_groups = 1 << 30, best_below = -(1 << 30);
+        int best_cost = 1 << 30, best_groups = 1 << 30, best_below = -(1 << 30);
         for (int size = 1; size <= out.n_regular && !best; ++size) {
             for (uint32_t mask = 1; mask < (1u << k); ++mask) {
                 if ((mask & ~reg) || popcount(mask) != size) continue;
@@ -220,14 +262,17 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
                             covers = false;
                 if (!covers || !connected_by_edges(p, mask)) continue;
                 uint32_t nc = reg & ~mask;
+                const int cost = core_scan_cost(p, cl, mask);
                 int ng = (int)noncore_groups(p, cl, nc).size();
                 int below = 0;
                 for (int u = 0; u < k; ++u)
                     if (nc >> u & 1)
                         for (int x = 0; x < k; ++x)
                             if (mask >> x & 1) below += (int)cl.less[u][x] - (int)cl.less[x][u];
-                if (!best || ng < best_groups || (ng == best_groups && below > best_below)) {
+                if (!best || cost < best_cost || (cost == best_cost && ng < best_groups) ||
+                    (cost == best_cost && ng == best_groups && below > best_below)) {
                     best = mask;
+                    best_cost = cost;
                     best_groups = ng;
                     best_below = below;
                 }
@@ -243,6 +288,20 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
     for (int i = 0; i < (int)groups.size(); ++i)
         if (counted < 0 || groups[i].size() > groups[counted].size()) counted = i;
     out.counted_group = counted < 0 ? 1 : (int)groups[counted].size();
+    // joint partner: another single-vertex group (fewest regular neighbours,
+    // i.e. the set most expensive to enumerate)
+    int partner = -1;
+    if (counted >= 0 && groups[counted].size() == 1) {
+        auto nbrs = [&](int u) {
+            int c = 0;
+            for (int w = 0; w < k; ++w) c += p.rel[u][w] == 1;
+            return c;
+        };
+        for (int i = 0; i < (int)groups.size(); ++i)
+            if (i != counted && groups[i].size() == 1 &&
+                (partner < 0 || nbrs(groups[i][0]) < nbrs(groups[partner][0])))
+                partner = i;
+    }
 
     // ---- computeMatchingOrders (Section 4.1) ----------------------------
     std::vector<int> core;
@@ -281,11 +340,14 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
             lvl_of[pick] = (int)bound_order.size();
             bound_order.push_back(pick);
         }
-        // non-core: enumerated groups first (chain order), counted group last
+        // non-core: enumerated groups first (chain order), counted group last;
+        // a single counted vertex is paired with another single non-core
+        // vertex placed right before it (joint counting of the last two)
         std::vector<int> nc_order;
         for (int i = 0; i < (int)groups.size(); ++i)
-            if (i != counted)
+            if (i != counted && i != partner)
                 for (int u : groups[i]) nc_order.push_back(u);
+        if (partner >= 0) nc_order.push_back(groups[partner][0]);
         for (int u : nc_order) {
             lvl_of[u] = (int)bound_order.size();
             bound_order.push_back(u);
@@ -308,6 +370,7 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
             L.is_core = (int8_t)((best >> u) & 1);
             L.label = p.label[u];
             L.group = (int8_t)((u == counted_first) ? out.counted_group : 1);
+            L.joint = (int8_t)(u == counted_first && partner >= 0);
             if (l == 0) continue;
             const bool core_level = L.is_core;
             int lo_core = -1, hi_core = -1; // tightest core bounds (by position)
@@ -334,14 +397,18 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
             }
             if (lo_core >= 0) L.lo_src[L.n_lo++] = (int8_t)lo_core;
             if (hi_core >= 0) L.hi_src[L.n_hi++] = (int8_t)hi_core;
-            // candidates adjacent to the start vertex and ranked below it lie
-            // in its out-neighbourhood (the start binds the highest core position)
+            // candidates adjacent to a bound vertex x and ranked below it lie
+            // in N+(x): at most max out-degree of them
             {
-                bool adj_start = false;
-                for (int i = 0; i < L.n_int; ++i) adj_start |= L.int_src[i] == 0;
-                const bool below_start = core_level || cl.less[u][bound_order[0]] ||
-                                         (hi_core >= 0);
-                L.out_bounded = (int8_t)(adj_start && below_start);
+                bool bounded = false;
+                for (int i = 0; i < L.n_int && !bounded; ++i) {
+                    const int x = bound_order[L.int_src[i]];
+                    const bool x_core = (best >> x) & 1;
+                    if (cl.less[u][x]) bounded = true;
+                    if (x_core && hi_core >= 0 && pos[bound_order[hi_core]] <= pos[x]) bounded = true;
+                    if (core_level && x_core && pos[x] > pos[u]) bounded = true;
+                }
+                L.out_bounded = (int8_t)bounded;
             }
             // injectivity: exclude every earlier image not already ruled out
             for (int j = 0; j < l; ++j) {

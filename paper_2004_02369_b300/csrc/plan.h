@@ -13,7 +13,14 @@
 //       restricted to  max(m[lo_src]) < x < min(m[hi_src]),
 //       label(x) == label (if label >= 0),  x != m[excl_src]
 //
-// where m[j] is the data vertex bound at level j.  Intersections implement
+// where m[j] is the data vertex bound at level j.
+//
+// A last level marked `joint` belongs to a single non-core vertex y whose
+// only ties to the previous level's single non-core vertex x are the
+// partial order and injectivity (non-core vertices share no edge or
+// anti-edge).  A kernel may then count the pairs (x, y) from the two sets'
+// cardinalities and ranks instead of enumerating x; enumerating x and
+// counting y level by level gives the same number.  Intersections implement
 // true edges and differences anti-edges (Section 4.2); the bounds implement
 // the symmetry-breaking partial order on degree-ranked ids (Section 5.2).
 #pragma once
@@ -28,6 +35,8 @@ struct PgLevel {
     int8_t pattern_vertex; // pattern vertex bound here
     int8_t is_core;
     int8_t out_bounded;    // candidates lie in N+(start): at most max out-degree
+    int8_t joint;          // last level only: counted jointly with the previous
+                           // level (two single non-core vertices, see plan.cpp)
     int8_t int_src[PGP_MAXK];
     int8_t diff_src[PGP_MAXK];
     int8_t lo_src[PGP_MAXK];

@@ -181,3 +181,47 @@ def test_invalid_csr_rejected(pg):
         pg.Graph(off, adj)
     with pytest.raises(pg.PgError):
         pg.count(pg.Graph.from_synth(sg.erdos_renyi(10, 0.5, 1)), [pg.Plan(2, [(0, 1)], labels=[0, 1])])
+
+
+def test_batched_matches_generic_and_oracle(pg):
+    import torch
+    g = sg.rmat(9, 8, 0.57, 0.19, 0.19, 77)
+    G = pg.Graph.from_synth(g)
+    pats = sg.motif4_patterns() + sg.motif3_patterns() + [sg.pattern(4, sg.TAILED_TRIANGLE, anti_edges=[(3, 1)]),
+                                                          sg.pattern(4, sg.DIAMOND), sg.pattern(5, sg.cycle_edges(5))]
+    plans = [pg.Plan.from_dict(p) for p in pats]
+    batch = pg.Batch(plans)
+    info = batch.info()
+    assert info["nodes"] < info["levels_total"]  # prefixes are shared
+    direct_info = pg.Batch(plans, expand_anti_edges=False).info()
+    # unlabeled k-cliques are counted by the clique kernel, outside the tree
+    is_clique = [p["k"] >= 3 and len(p["edges"]) == p["k"] * (p["k"] - 1) // 2 for p in pats]
+    assert direct_info["programs"] == sum(pl.info().n_orders for pl, c in zip(plans, is_clique) if not c)
+    assert direct_info["nodes"] < direct_info["levels_total"]
+    out = torch.zeros(2 * len(plans), dtype=torch.int64, device="cuda")
+    pg.count_batch(G, batch, out)
+    torch.cuda.synchronize()
+    got = pg.decode_counts(out)
+    out2 = torch.zeros_like(out)
+    pg.count_async(G, plans, out2, kernel=pg.KERNEL_GENERIC)
+    torch.cuda.synchronize()
+    assert got == pg.decode_counts(out2)
+    # anti-edges as set differences inside the batch (no pattern expansion)
+    direct = pg.Batch(plans, expand_anti_edges=False)
+    out3 = torch.zeros_like(out)
+    pg.count_batch(G, direct, out3)
+    torch.cuda.synchronize()
+    assert got == pg.decode_counts(out3)
+    for p, c in zip(pats, got):
+        assert c == expected(g, p, 5), p
+
+
+def test_batched_labeled_mix(pg):
+    g = _graphs()[3]
+    G = pg.Graph.from_synth(g)
+    pats = [sg.pattern(3, sg.clique_edges(3), labels=[0, 1, -1]),
+            sg.pattern(4, sg.star_edges(4), labels=[2, -1, -1, 0]),
+            sg.pattern(4, sg.chain_edges(4), labels=[1, 0, -1, 2], vertex_induced=True),
+            sg.pattern(1, [], labels=[1]), sg.pattern(2, [(0, 1)])]
+    got = pg.count(G, [pg.Plan.from_dict(p) for p in pats])
+    assert got == [oracle.count(g, p) for p in pats]
