@@ -257,6 +257,42 @@ int pg_count_batch(pg_graph *g, const pg_batch *b, uint64_t *counts_dev, void *s
 /* pg_free_batch - release a batch (NULL is a no-op). */
 void pg_free_batch(pg_batch *b);
 
+/*
+ * pg_fsm - labeled frequent subgraph mining with MNI support (Section 2.1
+ * FSM and minimum node image support; Section 3.2 "FSM" program with label
+ * discovery; Section 5.5 domains).  Finds every connected labeled pattern
+ * with 1..max_edges edges (max_edges <= 3) whose MNI support (the smallest,
+ * over pattern vertices, number of distinct data vertices that vertex maps
+ * to in edge-induced matches) is >= threshold.  MNI support is
+ * anti-monotone, so this is the set the paper's extend-by-edge loop returns.
+ *   out        host array of `capacity` records, filled in canonical order
+ *              (shape, then labels); *n_frequent = size of the frequent set.
+ * Shapes and canonical label tuples (pattern vertices in tuple order):
+ *   PG_FSM_EDGE     (x, y), x <= y            edge 0-1
+ *   PG_FSM_WEDGE    (c, x, y), x <= y         centre 0, leaves 1, 2
+ *   PG_FSM_TRIANGLE (x, y, z), sorted         triangle 0-1-2
+ *   PG_FSM_PATH     (a, b, c, d) = min of the tuple and its reverse, path 0-1-2-3
+ *   PG_FSM_STAR     (c, x, y, z), x <= y <= z  centre 0, leaves 1, 2, 3
+ * Unused label slots are -1.  Synchronous.  Needs a labeled graph with at
+ * most 32 labels.  Errors: PG_EINVAL, PG_EUNSUPPORTED (> 32 labels),
+ * PG_ETRUNC (capacity too small; *n_frequent still exact), PG_ENOMEM,
+ * PG_EDEVICE.
+ */
+#define PG_FSM_EDGE 1
+#define PG_FSM_WEDGE 2
+#define PG_FSM_TRIANGLE 3
+#define PG_FSM_PATH 4
+#define PG_FSM_STAR 5
+typedef struct {
+    int32_t shape;
+    int32_t labels[4];
+    int32_t pad;
+    uint64_t support;
+} pg_fsm_pattern;
+
+int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *out, int64_t capacity,
+           int64_t *n_frequent, void *stream);
+
 /* pg_last_error - message of the last failed call on this host thread. */
 const char *pg_last_error(void);
 

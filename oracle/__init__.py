@@ -70,6 +70,7 @@ def lib():
         L.or_kcliques.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_int64, u64p]
         L.or_motif4_noninduced.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, u64p]
+        L.or_fsm_domains.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 8
         _lib = L
     return _lib
 
@@ -214,3 +215,73 @@ def stars(g, leaves: int) -> int:
     """Edge-induced stars with the given number of leaves = sum_v C(d_v, leaves)."""
     d = np.diff(g.offsets)
     return int(sum(comb(int(x), leaves) for x in d))
+
+
+FSM_SHAPES = ("edge", "wedge", "triangle", "path", "star")
+
+
+def fsm_domain_tables(g, n_labels: int, threads: int = 0) -> dict:
+    """Per-vertex-label domain counts of every labeled position (oracle.c)."""
+    gr = _GraphRef(g)
+    L = n_labels
+    t = {"E": np.zeros((L, L), np.uint64), "WC": np.zeros((L, L, L), np.uint64),
+         "WL": np.zeros((L, L, L), np.uint64), "T": np.zeros((L, L, L), np.uint64),
+         "SC": np.zeros((L, L, L, L), np.uint64), "SL": np.zeros((L, L, L, L), np.uint64),
+         "PE": np.zeros((L, L, L, L), np.uint64), "PI": np.zeros((L, L, L, L), np.uint64)}
+    _check(lib().or_fsm_domains(ctypes.byref(gr.s), L, threads,
+                                *[t[k].ctypes.data for k in ("E", "WC", "WL", "T", "SC", "SL", "PE", "PI")]))
+    return t
+
+
+def fsm_supports(g, n_labels: int, threads: int = 0) -> dict:
+    """MNI support of every labeled connected pattern with 1..3 edges, keyed
+    by (shape, canonical label tuple):
+      edge (x, y) x<=y; wedge (c, x, y) x<=y; triangle (x, y, z) sorted;
+      path (a, b, c, d) = min of the tuple and its reverse; star (c, x, y, z).
+    Support = min over pattern positions of the domain size (MNI)."""
+    t = fsm_domain_tables(g, n_labels, threads)
+    E, WC, WL, T, SC, SL, PE, PI = (t[k] for k in ("E", "WC", "WL", "T", "SC", "SL", "PE", "PI"))
+    L = n_labels
+    out = {}
+    R = range(L)
+    for x in R:
+        for y in R:
+            if x <= y:
+                out[("edge", (x, y))] = int(min(E[x, y], E[y, x]))
+    for c in R:
+        for x in R:
+            for y in R:
+                if x <= y:
+                    out[("wedge", (c, x, y))] = int(min(WC[c, x, y], WL[x, c, y], WL[y, c, x]))
+    for x in R:
+        for y in R:
+            for z in R:
+                if x <= y <= z:
+                    out[("triangle", (x, y, z))] = int(min(T[x, y, z], T[y, x, z], T[z, x, y]))
+                for c in R:
+                    if x <= y <= z:
+                        out[("star", (c, x, y, z))] = int(min(SC[c, x, y, z], SL[x, c, y, z],
+                                                              SL[y, c, x, z], SL[z, c, x, y]))
+    for a in R:
+        for b in R:
+            for c in R:
+                for d in R:
+                    key = min((a, b, c, d), (d, c, b, a))
+                    if key != (a, b, c, d):
+                        continue
+                    out[("path", key)] = int(min(PE[a, b, c, d], PE[d, c, b, a], PI[b, a, c, d], PI[c, d, b, a]))
+    return out
+
+
+def fsm(g, n_labels: int, threshold: int, threads: int = 0) -> dict:
+    """Frequent labeled patterns (support >= threshold) with 1..3 edges."""
+    return {k: v for k, v in fsm_supports(g, n_labels, threads).items() if v >= threshold}
+
+
+def fsm_pattern(shape: str, labels) -> dict:
+    """Pattern description of an FSM key (vertex 0 first in the tuple order)."""
+    edges = {"edge": [(0, 1)], "wedge": [(0, 1), (0, 2)], "triangle": [(0, 1), (1, 2), (0, 2)],
+             "path": [(0, 1), (1, 2), (2, 3)], "star": [(0, 1), (0, 2), (0, 3)]}[shape]
+    k = 1 + max(max(e) for e in edges)
+    return dict(k=k, edges=edges, anti_edges=[], labels=list(labels), anti_vertex=None,
+                vertex_induced=False)

@@ -29,6 +29,8 @@
  *  or_mni_bruteforce MNI support (Section 2.1, minimum node image): for every
  *                    pattern vertex the set of data vertices some valid map
  *                    sends it to; support = the smallest such set.
+ *  or_fsm_domains    domain sizes of every labeled pattern with 1..3 edges by
+ *                    per-vertex search (see the function).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -549,3 +551,163 @@ int or_motif4_noninduced(const or_graph *g, int nthreads, uint64_t *out) {
 }
 
 int or_version(void) { return 1; }
+
+/* ---------------------------- FSM (MNI, <= 3 edges) ----------------------- */
+
+/*
+ * Labeled frequent subgraph mining up to three edges (Section 2.1 FSM with the
+ * MNI support; Section 3.2.1 label discovery): for every connected labeled
+ * edge-induced pattern with 1..3 edges, the MNI support = min over pattern
+ * vertices u of |{phi(u)}| over all valid maps phi.  A data vertex v lies in
+ * the domain of position u iff some valid map sends u to v; this oracle
+ * decides that per vertex by direct search over v's neighbourhood, using
+ * neighbour label counts only for the last (leaf) vertex of a shape, with the
+ * vertices already used subtracted explicitly.
+ *
+ * Output per label tuple (L = number of labels, v's own label first):
+ *   E[L][L]        v has a neighbour labeled y                      (edge end)
+ *   WC[L][L][L]    v has distinct neighbours labeled x, y           (wedge centre)
+ *   WL[L][L][L]    v - w(c) - u(y), u != v                          (wedge leaf)
+ *   T[L][L][L]     v in a triangle with neighbours labeled y, z     (triangle)
+ *   SC[L][L][L][L] v has distinct neighbours labeled x, y, z        (star centre)
+ *   SL[L][L][L][L] v - w(c), w has two more neighbours y, z (!= v)  (star leaf)
+ *   PE[L][L][L][L] v - w(b) - u(c) - x(d), all distinct             (path end)
+ *   PI[L][L][L][L] a'(a) - v - c'(c) - d'(d), all distinct          (path inner)
+ * Each entry counts the vertices with label = first index satisfying it.
+ * Only index combinations with the listed meaning are filled (x <= y etc. are
+ * not assumed: all orderings are filled).
+ */
+static int has_edge(const or_graph *g, int64_t a, int64_t b) { return adjacent(g, a, b); }
+
+int or_fsm_domains(const or_graph *g, int nl, int nthreads, uint64_t *E, uint64_t *WC, uint64_t *WL,
+                   uint64_t *T, uint64_t *SC, uint64_t *SL, uint64_t *PE, uint64_t *PI) {
+    if (!g->label || nl < 1 || nl > 32) return OR_EINVAL;
+    const int64_t n = g->n;
+    const int L = nl, L2 = nl * nl, L3 = nl * nl * nl;
+    size_t sE = (size_t)L2, s3 = (size_t)L3, s4 = (size_t)L3 * L;
+    memset(E, 0, sE * 8); memset(WC, 0, s3 * 8); memset(WL, 0, s3 * 8); memset(T, 0, s3 * 8);
+    memset(SC, 0, s4 * 8); memset(SL, 0, s4 * 8); memset(PE, 0, s4 * 8); memset(PI, 0, s4 * 8);
+    /* neighbour label counts */
+    int32_t *H = (int32_t *)calloc((size_t)n * L + 1, sizeof(int32_t));
+    if (!H) return OR_ENOMEM;
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t e = g->off[v]; e < g->off[v + 1]; ++e) H[v * L + g->label[g->adj[e]]]++;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        uint8_t *fWL = (uint8_t *)malloc((size_t)L2), *fT = (uint8_t *)malloc((size_t)L2);
+        uint8_t *fSL = (uint8_t *)malloc((size_t)L3), *fPE = (uint8_t *)malloc((size_t)L3);
+        uint8_t *fPI = (uint8_t *)malloc((size_t)L3);
+        uint64_t *lE = (uint64_t *)calloc(sE, 8), *lWC = (uint64_t *)calloc(s3, 8), *lWL = (uint64_t *)calloc(s3, 8);
+        uint64_t *lT = (uint64_t *)calloc(s3, 8), *lSC = (uint64_t *)calloc(s4, 8), *lSL = (uint64_t *)calloc(s4, 8);
+        uint64_t *lPE = (uint64_t *)calloc(s4, 8), *lPI = (uint64_t *)calloc(s4, 8);
+        if (!fWL || !fT || !fSL || !fPE || !fPI || !lE || !lWC || !lWL || !lT || !lSC || !lSL || !lPE || !lPI) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 64)
+            for (int64_t v = 0; v < n; ++v) {
+                const int lv = g->label[v];
+                const int32_t *Hv = H + v * L;
+                /* edge end, wedge centre, star centre: from v's own counts */
+                for (int y = 0; y < L; ++y) {
+                    if (Hv[y] >= 1) lE[lv * L + y]++;
+                    for (int x = 0; x < L; ++x) {
+                        const int ok = (x == y) ? (Hv[x] >= 2) : (Hv[x] >= 1 && Hv[y] >= 1);
+                        if (ok) lWC[(size_t)lv * L2 + x * L + y]++;
+                        for (int z = 0; z < L; ++z) {
+                            int cnt[32] = {0};
+                            cnt[x]++; cnt[y]++; cnt[z]++;
+                            if (Hv[x] >= cnt[x] && Hv[y] >= cnt[y] && Hv[z] >= cnt[z])
+                                lSC[(size_t)lv * L3 + (size_t)x * L2 + y * L + z]++;
+                        }
+                    }
+                }
+                memset(fWL, 0, L2); memset(fT, 0, L2); memset(fSL, 0, L3); memset(fPE, 0, L3); memset(fPI, 0, L3);
+                for (int64_t e = g->off[v]; e < g->off[v + 1]; ++e) {
+                    const int64_t w = g->adj[e];
+                    const int lw = g->label[w];
+                    const int32_t *Hw = H + w * L;
+                    /* wedge leaf and star leaf: centre w, other leaves among adj(w) \ {v} */
+                    for (int y = 0; y < L; ++y) {
+                        int hy = Hw[y] - (y == lv);
+                        if (hy >= 1) fWL[lw * L + y] = 1;
+                        for (int z = 0; z < L; ++z) {
+                            int hz = Hw[z] - (z == lv);
+                            int ok = (y == z) ? (hy >= 2) : (hy >= 1 && hz >= 1);
+                            if (ok) fSL[(size_t)lw * L2 + y * L + z] = 1;
+                        }
+                    }
+                    /* triangle: u in adj(v) n adj(w), by merging the two lists */
+                    {
+                        int64_t i = g->off[v], j = g->off[w];
+                        while (i < g->off[v + 1] && j < g->off[w + 1]) {
+                            if (g->adj[i] < g->adj[j]) ++i;
+                            else if (g->adj[i] > g->adj[j]) ++j;
+                            else { fT[lw * L + g->label[g->adj[i]]] = 1; ++i; ++j; }
+                        }
+                    }
+                    /* path end: v - w - u - x with u != v, x not in {v, w}.
+                     * Labels d with a neighbour x of u other than w: count
+                     * Hu[d] - [d == lw] >= 1; when it is exactly 1 for d = lv
+                     * the single candidate may be v itself (if v ~ u). */
+                    for (int64_t f = g->off[w]; f < g->off[w + 1]; ++f) {
+                        const int64_t u = g->adj[f];
+                        if (u == v) continue;
+                        const int lu = g->label[u];
+                        const int32_t *Hu = H + u * L;
+                        uint8_t *row = fPE + (size_t)lw * L2 + lu * L;
+                        for (int d = 0; d < L; ++d) {
+                            int c = Hu[d] - (d == lw);
+                            if (d == lv && c == 1 && has_edge(g, v, u)) c = 0;
+                            if (c >= 1) row[d] = 1;
+                        }
+                    }
+                    /* path inner: a' - v - w(=c') - d', a' != w, d' not in {v, a'} */
+                    for (int a = 0; a < L; ++a) {
+                        int na = Hv[a] - (a == lw); /* a' in adj(v) \ {w} */
+                        if (na < 1) continue;
+                        for (int d = 0; d < L; ++d) {
+                            int nd = Hw[d] - (d == lv); /* d' in adj(w) \ {v} */
+                            if (nd < 1) continue;
+                            int ok = 1;
+                            if (a == d && na == 1 && nd == 1) {
+                                /* the single a' and the single d' coincide iff
+                                 * some common neighbour of v and w has label a */
+                                for (int64_t f = g->off[v]; f < g->off[v + 1]; ++f) {
+                                    const int64_t u = g->adj[f];
+                                    if (u != w && g->label[u] == a && has_edge(g, w, u)) { ok = 0; break; }
+                                }
+                            }
+                            if (ok) fPI[(size_t)a * L2 + lw * L + d] = 1;
+                        }
+                    }
+                }
+                for (int i = 0; i < L2; ++i) {
+                    if (fWL[i]) lWL[(size_t)lv * L2 + i]++;
+                    if (fT[i]) lT[(size_t)lv * L2 + i]++;
+                }
+                for (int i = 0; i < L3; ++i) {
+                    if (fSL[i]) lSL[(size_t)lv * L3 + i]++;
+                    if (fPE[i]) lPE[(size_t)lv * L3 + i]++;
+                    if (fPI[i]) lPI[(size_t)lv * L3 + i]++;
+                }
+            }
+#pragma omp critical
+            {
+                for (size_t i = 0; i < sE; ++i) E[i] += lE[i];
+                for (size_t i = 0; i < s3; ++i) { WC[i] += lWC[i]; WL[i] += lWL[i]; T[i] += lT[i]; }
+                for (size_t i = 0; i < s4; ++i) { SC[i] += lSC[i]; SL[i] += lSL[i]; PE[i] += lPE[i]; PI[i] += lPI[i]; }
+            }
+        }
+        free(fWL); free(fT); free(fSL); free(fPE); free(fPI);
+        free(lE); free(lWC); free(lWL); free(lT); free(lSC); free(lSL); free(lPE); free(lPI);
+    }
+    free(H);
+    return err ? OR_ENOMEM : OR_OK;
+}

@@ -69,6 +69,7 @@ _lib.pg_free_plan.argtypes = [_vp]
 _lib.pg_free_plan.restype = None
 _lib.pg_count.argtypes = [_vp, _vp, _i32, _vp, _vp]
 _lib.pg_count_ex.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp]
+_lib.pg_fsm.argtypes = [_vp, _i32, ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_count_cliques_noalloc.argtypes = [_vp, _i32, _i32, _vp, _vp]
 _lib.pg_compile_batch.argtypes = [_vp, _i32, _i32, ctypes.POINTER(_vp)]
 _lib.pg_batch_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
@@ -288,6 +289,35 @@ def count_cliques_noalloc(graph: Graph, kmin: int, kmax: int, out, stream=None):
     if out.numel() < 2 * (kmax - kmin + 1) or not out.is_cuda:
         raise ValueError("out must be a CUDA tensor with 2*(kmax-kmin+1) 64-bit elements")
     _check(_lib.pg_count_cliques_noalloc(graph.handle, kmin, kmax, out.data_ptr(), _stream_ptr(stream)))
+
+
+class FsmPattern(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("labels", ctypes.c_int32 * 4), ("pad", ctypes.c_int32),
+                ("support", ctypes.c_uint64)]
+
+
+FSM_SHAPE_NAMES = {1: "edge", 2: "wedge", 3: "triangle", 4: "path", 5: "star"}
+
+
+def fsm(graph: Graph, threshold: int, max_edges: int = 3, stream=None) -> dict:
+    """Frequent labeled patterns with 1..max_edges edges and their MNI
+    supports: {(shape_name, label tuple): support}."""
+    cap = 1 << 16
+    while True:
+        arr = (FsmPattern * cap)()
+        n = _i64()
+        rc = _lib.pg_fsm(graph.handle, max_edges, threshold, arr, cap, ctypes.byref(n), _stream_ptr(stream))
+        if rc == PG_ETRUNC:
+            cap = int(n.value) + 1
+            continue
+        _check(rc)
+        break
+    out = {}
+    width = {1: 2, 2: 3, 3: 3, 4: 4, 5: 4}
+    for i in range(n.value):
+        r = arr[i]
+        out[(FSM_SHAPE_NAMES[r.shape], tuple(r.labels[j] for j in range(width[r.shape])))] = int(r.support)
+    return out
 
 
 def decode_counts(words) -> list[int]:

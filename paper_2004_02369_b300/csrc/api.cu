@@ -363,3 +363,9 @@ extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uin
     PG_CUDA(cudaStreamSynchronize(s));
     return PG_OK;
 }
+
+extern "C" int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *out, int64_t capacity,
+                      int64_t *n_frequent, void *stream) {
+    if (!g || !n_frequent || (capacity > 0 && !out) || capacity < 0) return pg_set_error(PG_EINVAL, "bad argument");
+    return pg_fsm_run(g, max_edges, threshold, out, capacity, n_frequent, (cudaStream_t)stream);
+}

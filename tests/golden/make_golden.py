@@ -9,6 +9,8 @@ and commit the resulting workload_counts.json.  Workloads:
   motif3   ER G(2000, 0.005): induced triangles and wedges
   cliques  Chung-Lu 1M / 10M, gamma 2.1: 3-, 4- and 5-cliques
   motif4   R-MAT scale 20, edge factor 16: the six induced 4-vertex motifs
+  fsm      Chung-Lu 500K / 5M, gamma 2.3, Zipf(1.2) labels over 20: frequent
+           labeled patterns with 1..3 edges, MNI support >= 1000
 """
 import json
 import os
@@ -36,6 +38,10 @@ def run(name):
     elif name == "motif4":
         g = sg.workload_graph(3)
         res = {f"induced_{k}": v for k, v in oracle.motif4_induced(g).items()}
+    elif name == "fsm":
+        g = sg.workload_graph(4)
+        freq = oracle.fsm(g, 20, 1000)
+        res = {f"{shape}:{','.join(map(str, labels))}": v for (shape, labels), v in sorted(freq.items())}
     else:
         raise SystemExit(f"unknown workload {name}")
     return {"graph": {k: v for k, v in g.meta.items() if k != "abcd"},
@@ -44,7 +50,7 @@ def run(name):
 
 
 if __name__ == "__main__":
-    names = sys.argv[1:] or ["motif3", "cliques", "motif4"]
+    names = sys.argv[1:] or ["motif3", "cliques", "motif4", "fsm"]
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     data["_about"] = ("Expected counts written by tests/golden/make_golden.py from the oracle "
                       "only; counts are decimal strings (exact).")

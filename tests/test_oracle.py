@@ -321,3 +321,50 @@ def test_mni_matches_networkx_and_is_antimonotone():
         assert sub["wedge"] <= sub["edge"]
         assert sub["path3"] <= sub["wedge"] and sub["star3"] <= sub["wedge"]
         assert sub["triangle"] <= sub["wedge"]
+
+
+# ------------------------------------------------------------- FSM ---------
+
+def test_fsm_supports_match_bruteforce_mni():
+    """Every labeled pattern with 1..3 edges on small labeled graphs: the
+    per-vertex domain search agrees with brute-force MNI (all maps)."""
+    for seed, n, p, nl in [(31, 40, 0.12, 3), (32, 30, 0.2, 2), (33, 50, 0.08, 4)]:
+        g = sg.erdos_renyi(n, p, seed)
+        g.labels = sg.uniform_labels(g.n, nl, seed + 1)
+        sup = oracle.fsm_supports(g, nl)
+        for (shape, labels), s in sup.items():
+            d = oracle.mni_domains_bruteforce(g, oracle.fsm_pattern(shape, labels))
+            assert s == min(d), (shape, labels, s, d)
+
+
+def test_fsm_hub_and_corner_cases():
+    # a star centre with exactly one neighbour per label, a triangle and a
+    # path whose two ends would have to be the same vertex
+    g = sg.from_edges(7, [(0, 1), (0, 2), (0, 3), (1, 2), (3, 4), (4, 5), (5, 3), (5, 6)])
+    g.labels = np.array([0, 1, 1, 2, 0, 1, 2], dtype=np.int32)
+    sup = oracle.fsm_supports(g, 3)
+    for (shape, labels), s in sup.items():
+        d = oracle.mni_domains_bruteforce(g, oracle.fsm_pattern(shape, labels))
+        assert s == min(d), (shape, labels)
+    assert sup[("edge", (0, 1))] == min(2, 3)
+
+
+def test_fsm_antimonotone():
+    g = sg.chung_lu(300, 1200, 2.3, 40.0, 34)
+    g.labels = sg.zipf_labels(g.n, 4, 1.2, 35)
+    sup = oracle.fsm_supports(g, 4)
+    for (shape, labels), s in sup.items():
+        if shape == "wedge":
+            c, x, y = labels
+            assert s <= sup[("edge", tuple(sorted((c, x))))] and s <= sup[("edge", tuple(sorted((c, y))))]
+        if shape == "star":
+            c, x, y, z = labels
+            for a, b in ((x, y), (x, z), (y, z)):
+                assert s <= sup[("wedge", (c, min(a, b), max(a, b)))]
+        if shape == "triangle":
+            x, y, z = labels
+            assert s <= sup[("wedge", (x, min(y, z), max(y, z)))]
+        if shape == "path":
+            a, b, c, d = labels
+            assert s <= sup[("wedge", (b, min(a, c), max(a, c)))]
+            assert s <= sup[("wedge", (c, min(b, d), max(b, d)))]
