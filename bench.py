@@ -333,6 +333,88 @@ def run_ours(args):
     return 0
 
 
+# --------------------------------------------------------------- serving ---
+
+def run_serving(args):
+    """Poisson stream of count queries over a resident R-MAT graph: batched
+    continuous serving vs the same kernels one query at a time."""
+    import torch
+    import paper_2004_02369_b300 as pg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    scale = args.serve_scale
+    g = sg.workload_graph(5, scale_down=22 - scale)
+    G = pg.Graph.from_synth(g)
+    # unlabeled 5-cycles take minutes alone on power-law hubs: they are
+    # calibrated alone (alone_ms) and drawn only in their labeled form
+    qs = sg.serving_queries(args.serve_n, seed=sg.SEED_BASE + 55, labeled_only=("C5",))
+    types = sorted({q["name"] for q in qs})
+
+    # per-type service time alone (first call compiles / sizes scratch)
+    alone_ms = {}
+    for name in types:
+        q = next(x for x in qs if x["name"] == name)
+        plan = pg.Plan.from_dict(q)
+        pg.count(G, [plan])
+        t = time.perf_counter()
+        pg.count(G, [plan])
+        alone_ms[name] = (time.perf_counter() - t) * 1e3
+
+    def log(msg):
+        print(f"[serving {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+    log(f"graph n={g.n} m={g.m}; {len(qs)} queries; per-type alone ms {alone_ms}")
+
+    def drive(server, arrivals):
+        t0 = time.perf_counter()
+        tickets = []
+        for q, a in zip(qs, arrivals):
+            while time.perf_counter() - t0 < a:
+                time.sleep(min(2e-4, max(0.0, a - (time.perf_counter() - t0))))
+            tickets.append(server.submit(q))
+        server.drain(args.serve_timeout)
+        res = {r["ticket"]: r for r in server.poll(len(qs) + 10)}
+        out = [res[t] for t in tickets]
+        lat = np.array([r["t_done"] - r["t_submit"] for r in out]) * 1e3
+        span = max(r["t_done"] for r in out) - min(r["t_submit"] for r in out)
+        return out, {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "queries_per_s": len(out) / span,
+                     "batches": server.stats()["batches"]}
+
+    # serial capacity: closed loop, everything submitted at t = 0
+    srv = pg.Server(G, serial=True)
+    base, cal = drive(srv, np.zeros(len(qs)))
+    srv.close()
+    capacity = cal["queries_per_s"]
+    log(f"serial capacity {capacity:.1f} queries/s ({cal})")
+    want = [r["count"] for r in base]
+    runs = []
+    for f in args.serve_lambdas:
+        arrivals = sg.poisson_arrivals(len(qs), f * capacity, seed=sg.SEED_BASE + int(100 * f))
+        row = {"lambda_x_capacity": f, "rate_qps": f * capacity}
+        for mode, kw in (("serial", dict(serial=True)), ("batched", dict(n_streams=4, max_batch=32))):
+            srv = pg.Server(G, **kw)
+            out, st = drive(srv, arrivals)
+            srv.close()
+            log(f"lambda {f} {mode}: {st}")
+            if [r["count"] for r in out] != want:
+                raise SystemExit(f"serving counts differ from one-at-a-time ({mode}, lambda {f})")
+            row[mode] = st
+        runs.append(row)
+    line = {"metric": "serving p50/p99 latency and queries/s, batched vs one query at a time",
+            "unit": "ms, queries/s", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"serving_rmat_scale{scale}_ef16_labels8",
+                       "graph": {"n": g.n, "m": g.m, "max_degree": int(g.meta["max_degree"])},
+                       "queries": len(qs), "types": types, "labeled_fraction": 0.1,
+                       "labeled_only": ["C5"],
+                       "arrivals": "Poisson, rate = lambda x measured serial capacity",
+                       "batched": "4 streams, up to 32 queries per launch"},
+            "serial_capacity_qps": capacity, "alone_ms": alone_ms, "runs": runs,
+            "mix_equals_alone": True}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,6 +423,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kernel", type=int, default=0, help="PG_KERNEL_* (0 = auto)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    ap.add_argument("--workload", choices=["cliques", "serving"], default="cliques")
+    ap.add_argument("--serve-scale", type=int, default=16, help="R-MAT scale of the serving graph")
+    ap.add_argument("--serve-n", type=int, default=300, help="queries per arrival rate")
+    ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
+    ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")
     ap.add_argument("--only-kernel", action="store_true",
                     help="time the counting steps only (for profiler runs)")
     ap.add_argument("--traffic", type=float, default=None,
@@ -348,6 +435,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

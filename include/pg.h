@@ -293,6 +293,68 @@ typedef struct {
 int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *out, int64_t capacity,
            int64_t *n_frequent, void *stream);
 
+/*
+ * Serving: a request loop over a resident graph.  Queries are submitted at
+ * any time from any host thread; a worker thread admits waiting queries into
+ * batches whenever one of n_streams streams is free and the batch's scratch
+ * requirement fits that stream's preallocated share of memory_budget (a
+ * batch that does not fit is split; a query that does not fit alone fails
+ * with PG_ENOMEM in its result), counts each batch in one launch (the batch
+ * kernel over the shared prefix tree, cliques by the clique kernel), and
+ * publishes per-query results with submit / start / completion times.
+ * Batches on different streams overlap on the device, and queries arriving
+ * while others run are admitted as soon as a stream frees up.  Plans are
+ * compiled once per distinct pattern and kept.  The paper runs one mining
+ * program at a time (Section 5.1); this loop applies its processing model to
+ * a stream of patterns.
+ *   n_streams      concurrent batches (1..16); memory_budget: device bytes
+ *                  for scratch (0: 40% of free memory, at most 64 GiB);
+ *   max_batch      queries per batch (1..64); serial = 1: one query per
+ *                  launch and one launch at a time (the baseline).
+ * Times are seconds since pg_server_create (host steady clock); t_done is
+ * when the worker observed the batch's completion.
+ */
+typedef struct pg_server pg_server;
+typedef struct {
+    int32_t n_streams;
+    int32_t max_batch;
+    int64_t memory_budget;
+    int32_t serial;
+    int32_t pad;
+} pg_server_config;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;     /* PG_OK or the error that failed the query */
+    int32_t batch_size; /* queries in the launch that counted it */
+    uint64_t count_lo, count_hi; /* 128-bit count */
+    double t_submit, t_start, t_done;
+} pg_query_result;
+
+typedef struct {
+    int32_t n_streams;
+    int32_t pad;
+    int64_t batches, launched_queries, outstanding, cached_plans;
+    int64_t scratch_bytes_per_stream;
+    double now;
+} pg_server_stats;
+
+/* pg_server_create - start the worker on the current device.  The graph
+ * must outlive the server.  Errors: PG_EINVAL, PG_ENOMEM, PG_EDEVICE. */
+int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_server **out);
+/* pg_server_submit - enqueue one count query; *ticket identifies its result.
+ * Compiles the pattern on first sight (errors as pg_compile_pattern). */
+int pg_server_submit(pg_server *s, const pg_pattern_desc *q, uint64_t *ticket);
+/* pg_server_poll - move up to max_results finished results into out (host). */
+int pg_server_poll(pg_server *s, pg_query_result *out, int32_t max_results, int32_t *n_out);
+/* pg_server_drain - wait until every submitted query has a result, or
+ * PG_ETIMEOUT after timeout_s seconds. */
+int pg_server_drain(pg_server *s, double timeout_s);
+/* pg_server_get_stats - counters of the server (host struct out). */
+int pg_server_get_stats(pg_server *s, pg_server_stats *out);
+/* pg_server_free - stop the worker, wait for launches, release everything. */
+void pg_server_free(pg_server *s);
+
 /* pg_last_error - message of the last failed call on this host thread. */
 const char *pg_last_error(void);
 

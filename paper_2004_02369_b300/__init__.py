@@ -70,6 +70,13 @@ _lib.pg_free_plan.restype = None
 _lib.pg_count.argtypes = [_vp, _vp, _i32, _vp, _vp]
 _lib.pg_count_ex.argtypes = [_vp, _vp, _i32, _vp, _i32, _vp]
 _lib.pg_fsm.argtypes = [_vp, _i32, ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64), _vp]
+_lib.pg_server_create.argtypes = [_vp, _vp, ctypes.POINTER(_vp)]
+_lib.pg_server_submit.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]
+_lib.pg_server_poll.argtypes = [_vp, _vp, _i32, ctypes.POINTER(_i32)]
+_lib.pg_server_drain.argtypes = [_vp, ctypes.c_double]
+_lib.pg_server_get_stats.argtypes = [_vp, _vp]
+_lib.pg_server_free.argtypes = [_vp]
+_lib.pg_server_free.restype = None
 _lib.pg_count_cliques_noalloc.argtypes = [_vp, _i32, _i32, _vp, _vp]
 _lib.pg_compile_batch.argtypes = [_vp, _i32, _i32, ctypes.POINTER(_vp)]
 _lib.pg_batch_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]
@@ -318,6 +325,74 @@ def fsm(graph: Graph, threshold: int, max_edges: int = 3, stream=None) -> dict:
         r = arr[i]
         out[(FSM_SHAPE_NAMES[r.shape], tuple(r.labels[j] for j in range(width[r.shape])))] = int(r.support)
     return out
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("serial", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class QueryResult(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("count_lo", ctypes.c_uint64), ("count_hi", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("pad", ctypes.c_int32), ("batches", ctypes.c_int64),
+                ("launched_queries", ctypes.c_int64), ("outstanding", ctypes.c_int64),
+                ("cached_plans", ctypes.c_int64), ("scratch_bytes_per_stream", ctypes.c_int64),
+                ("now", ctypes.c_double)]
+
+
+class Server:
+    """Request loop over a resident graph (native worker thread, see pg.h)."""
+
+    def __init__(self, graph: Graph, n_streams: int = 4, max_batch: int = 32, memory_budget: int = 0,
+                 serial: bool = False):
+        self.graph = graph  # keep the graph alive
+        cfg = ServerConfig(n_streams, max_batch, memory_budget, 1 if serial else 0, 0)
+        h = _vp()
+        _check(_lib.pg_server_create(graph.handle, ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+
+    def submit(self, p: dict) -> int:
+        """Enqueue a count query (pattern dict as in Plan.from_dict); returns its ticket."""
+        e = np.ascontiguousarray(np.asarray(p["edges"], dtype=np.int32).reshape(-1))
+        a = np.ascontiguousarray(np.asarray(p.get("anti_edges", []), dtype=np.int32).reshape(-1))
+        lab = None if p.get("labels") is None else np.ascontiguousarray(p["labels"], dtype=np.int32)
+        av = None if p.get("anti_vertex") is None else np.ascontiguousarray(p["anti_vertex"], dtype=np.uint8)
+        d = _PatternDesc(int(p["k"]), e.size // 2, e.ctypes.data if e.size else None, a.size // 2,
+                         a.ctypes.data if a.size else None, None if lab is None else lab.ctypes.data,
+                         None if av is None else av.ctypes.data, 1 if p.get("vertex_induced") else 0)
+        t = ctypes.c_uint64()
+        _check(_lib.pg_server_submit(self._h, ctypes.byref(d), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, max_results: int = 4096) -> list[dict]:
+        arr = (QueryResult * max_results)()
+        n = _i32()
+        _check(_lib.pg_server_poll(self._h, arr, max_results, ctypes.byref(n)))
+        return [dict(ticket=int(r.ticket), status=int(r.status), count=_u128(r.count_lo, r.count_hi),
+                     t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done, batch_size=int(r.batch_size))
+                for r in arr[:n.value]]
+
+    def drain(self, timeout_s: float = 600.0):
+        _check(_lib.pg_server_drain(self._h, timeout_s))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_lib.pg_server_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_ if k != "pad"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.pg_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 def decode_counts(words) -> list[int]:

@@ -71,8 +71,7 @@ extern "C" int pg_load_graph(const int64_t *offsets, int64_t n, const int32_t *a
         }
         rc = pg_graph_build(g, d_off, d_adj, nnz, d_lab, s);
         if (rc) break;
-        if ((e = cudaMalloc(&g->queues, PG_MAX_QUEUES * sizeof(unsigned long long))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
-        if ((e = cudaMalloc(&g->tmp_counts, 2 * PG_MAX_QUEUES * sizeof(unsigned long long))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+        if ((rc = pg_exec_init(&g->exec0)) != PG_OK) break;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaStreamSynchronize"); break; }
     } while (0);
     if (rc) {
@@ -98,7 +97,7 @@ extern "C" int pg_graph_get_info(const pg_graph *g, pg_graph_info *out) {
     out->m = g->m;
     out->max_degree = g->max_deg;
     out->max_out_degree = g->max_out;
-    out->device_bytes = g->bytes_device + (int64_t)g->scratch_bytes;
+    out->device_bytes = g->bytes_device + (int64_t)g->ex->scratch_bytes;
     out->labeled = g->labeled;
     out->n_labels = g->n_labels;
     return PG_OK;
@@ -116,26 +115,39 @@ extern "C" void pg_free_graph(pg_graph *g) {
     if (g->adj) cudaFree(g->adj);
     if (g->rank) cudaFree(g->rank);
     if (g->hubbits) cudaFree(g->hubbits);
-    if (g->scratch) cudaFree(g->scratch);
-    if (g->queues) cudaFree(g->queues);
-    if (g->tmp_counts) cudaFree(g->tmp_counts);
+    pg_exec_release(&g->exec0);
     if (g->heavy) cudaFree(g->heavy);
     if (g->batch_cache) pg_batch_free(g->batch_cache);
     delete g;
 }
 
+int pg_exec_init(pg_exec *x) {
+    PG_CUDA(cudaMalloc(&x->queues, PG_MAX_QUEUES * sizeof(unsigned long long)));
+    PG_CUDA(cudaMalloc(&x->tmp_counts, 2 * PG_MAX_QUEUES * sizeof(unsigned long long)));
+    return PG_OK;
+}
+
+void pg_exec_release(pg_exec *x) {
+    if (x->scratch) cudaFree(x->scratch);
+    if (x->queues) cudaFree(x->queues);
+    if (x->tmp_counts) cudaFree(x->tmp_counts);
+    x->scratch = nullptr;
+    x->queues = x->tmp_counts = nullptr;
+    x->scratch_bytes = 0;
+}
+
 int pg_ensure_scratch(pg_graph *g, size_t bytes, cudaStream_t s) {
-    if (bytes <= g->scratch_bytes) return PG_OK;
-    if (g->scratch) {
+    if (bytes <= g->ex->scratch_bytes) return PG_OK;
+    if (g->ex->scratch) {
         // earlier launches on any stream may still read the old arena
         PG_CUDA(cudaDeviceSynchronize());
-        cudaFree(g->scratch);
-        g->scratch = nullptr;
-        g->scratch_bytes = 0;
+        cudaFree(g->ex->scratch);
+        g->ex->scratch = nullptr;
+        g->ex->scratch_bytes = 0;
     }
     (void)s;
-    PG_CUDA(cudaMalloc(&g->scratch, bytes));
-    g->scratch_bytes = bytes;
+    PG_CUDA(cudaMalloc(&g->ex->scratch, bytes));
+    g->ex->scratch_bytes = bytes;
     return PG_OK;
 }
 
@@ -304,11 +316,11 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
     PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * n_plans, s));
     if (kernel == PG_KERNEL_CLIQUE) {
         // one launch counts every size kmin..kmax; copy each plan's size out
-        PG_CUDA(cudaMemsetAsync(g->tmp_counts, 0, 2 * sizeof(uint64_t) * (kmax - kmin + 1), s));
-        rc = pg_launch_clique(g, kmin, kmax, g->tmp_counts, 0, s);
+        PG_CUDA(cudaMemsetAsync(g->ex->tmp_counts, 0, 2 * sizeof(uint64_t) * (kmax - kmin + 1), s));
+        rc = pg_launch_clique(g, kmin, kmax, g->ex->tmp_counts, 0, s);
         if (rc) return rc;
         for (int i = 0; i < n_plans; ++i)
-            PG_CUDA(cudaMemcpyAsync(counts_dev + 2 * i, g->tmp_counts + 2 * (plans[i]->h.pat.k - kmin),
+            PG_CUDA(cudaMemcpyAsync(counts_dev + 2 * i, g->ex->tmp_counts + 2 * (plans[i]->h.pat.k - kmin),
                                     2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         return PG_OK;
     }

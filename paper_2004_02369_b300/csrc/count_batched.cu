@@ -241,6 +241,8 @@ struct pg_batch {
     bool any_level[PGP_MAXK] = {};
     PgTrieNode *d_nodes = nullptr;
     PgTrieTerm *d_terms = nullptr;
+    void *d_image = nullptr; // all device arrays of the batch, contiguous
+    bool image_owned = false;
 };
 
 namespace {
@@ -350,6 +352,7 @@ int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out
         bb->out_n.push_back((int)bb->term_slot.size() - bb->out_first.back());
     }
     int rc = pg_batch_build_trie(bb);
+    if (!rc && !(flags & PG_BATCH_HOST_ONLY)) rc = pg_batch_upload(bb);
     if (rc) { pg_batch_free(bb); return rc; }
     *out = bb;
     return PG_OK;
@@ -446,31 +449,95 @@ int pg_batch_build_trie(pg_batch *b) {
         for (auto &tm : n.terms) b->terms.push_back(tm);
     }
     b->n_roots = (int)roots.size();
-    const size_t nb = b->nodes.size() * sizeof(PgTrieNode), tb = std::max<size_t>(1, b->terms.size()) * sizeof(PgTrieTerm);
-    auto up = [](void **dst, const void *src, size_t bytes) -> cudaError_t {
-        cudaError_t e = cudaMalloc(dst, bytes ? bytes : 16);
-        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-        return e;
+    return PG_OK;
+}
+
+namespace {
+// Device arrays of a batch, in one contiguous layout: nodes, terms, term
+// slots, term coefficients, output ranges / divisors, slot counts.
+struct BatchImage {
+    size_t off[8];
+    size_t bytes;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+BatchImage batch_image(const pg_batch *b) {
+    const size_t sz[8] = {b->nodes.size() * sizeof(PgTrieNode), b->terms.size() * sizeof(PgTrieTerm),
+                          b->term_slot.size() * sizeof(int), b->term_coef.size() * sizeof(long long),
+                          b->out_first.size() * sizeof(int), b->out_n.size() * sizeof(int),
+                          b->out_div.size() * sizeof(unsigned long long),
+                          2 * sizeof(unsigned long long) * (size_t)b->n_slots};
+    BatchImage im;
+    size_t o = 0;
+    for (int i = 0; i < 8; ++i) {
+        im.off[i] = o;
+        o += align16(std::max<size_t>(sz[i], 16));
+    }
+    im.bytes = o;
+    return im;
+}
+
+void batch_fill_host(const pg_batch *b, const BatchImage &im, unsigned char *h) {
+    auto put = [&](int i, const void *src, size_t bytes) {
+        if (bytes) std::memcpy(h + im.off[i], src, bytes);
     };
-    cudaError_t e;
-    if ((e = up((void **)&b->d_nodes, b->nodes.data(), nb)) != cudaSuccess ||
-        (e = up((void **)&b->d_terms, b->terms.data(), b->terms.size() * sizeof(PgTrieTerm))) != cudaSuccess ||
-        (e = up((void **)&b->d_term_slot, b->term_slot.data(), b->term_slot.size() * sizeof(int))) != cudaSuccess ||
-        (e = up((void **)&b->d_term_coef, b->term_coef.data(), b->term_coef.size() * sizeof(long long))) != cudaSuccess ||
-        (e = up((void **)&b->d_out_first, b->out_first.data(), b->out_first.size() * sizeof(int))) != cudaSuccess ||
-        (e = up((void **)&b->d_out_n, b->out_n.data(), b->out_n.size() * sizeof(int))) != cudaSuccess ||
-        (e = up((void **)&b->d_out_div, b->out_div.data(), b->out_div.size() * sizeof(unsigned long long))) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_slot_counts, 2 * sizeof(unsigned long long) * (size_t)b->n_slots)) != cudaSuccess)
+    put(0, b->nodes.data(), b->nodes.size() * sizeof(PgTrieNode));
+    put(1, b->terms.data(), b->terms.size() * sizeof(PgTrieTerm));
+    put(2, b->term_slot.data(), b->term_slot.size() * sizeof(int));
+    put(3, b->term_coef.data(), b->term_coef.size() * sizeof(long long));
+    put(4, b->out_first.data(), b->out_first.size() * sizeof(int));
+    put(5, b->out_n.data(), b->out_n.size() * sizeof(int));
+    put(6, b->out_div.data(), b->out_div.size() * sizeof(unsigned long long));
+}
+
+void batch_point(pg_batch *b, const BatchImage &im, unsigned char *d) {
+    b->d_nodes = (PgTrieNode *)(d + im.off[0]);
+    b->d_terms = (PgTrieTerm *)(d + im.off[1]);
+    b->d_term_slot = (int *)(d + im.off[2]);
+    b->d_term_coef = (long long *)(d + im.off[3]);
+    b->d_out_first = (int *)(d + im.off[4]);
+    b->d_out_n = (int *)(d + im.off[5]);
+    b->d_out_div = (unsigned long long *)(d + im.off[6]);
+    b->d_slot_counts = (unsigned long long *)(d + im.off[7]);
+}
+}  // namespace
+
+// Device copy owned by the batch (public batches, pg_count_ex's cache).
+int pg_batch_upload(pg_batch *b) {
+    const BatchImage im = batch_image(b);
+    std::vector<unsigned char> h(im.bytes, 0);
+    batch_fill_host(b, im, h.data());
+    void *d = nullptr;
+    PG_CUDA(cudaMalloc(&d, im.bytes));
+    cudaError_t e = cudaMemcpy(d, h.data(), im.bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
         return pg_cuda_error(e, "batch upload");
-    (void)tb;
+    }
+    b->d_image = d;
+    b->image_owned = true;
+    batch_point(b, im, (unsigned char *)d);
+    return PG_OK;
+}
+
+// Device copy staged into caller areas with an asynchronous copy on stream
+// s: `host` must be pinned and stay untouched until the copy is done; no
+// allocation.  PG_ENOMEM if the image is larger than the areas.
+int pg_batch_stage(pg_batch *b, void *dev_area, void *host_area, size_t area_bytes, cudaStream_t s) {
+    const BatchImage im = batch_image(b);
+    if (im.bytes > area_bytes) return pg_set_error(PG_ENOMEM, "batch image larger than the staging area");
+    batch_fill_host(b, im, (unsigned char *)host_area);
+    PG_CUDA(cudaMemcpyAsync(dev_area, host_area, im.bytes, cudaMemcpyHostToDevice, s));
+    b->d_image = dev_area;
+    b->image_owned = false;
+    batch_point(b, im, (unsigned char *)dev_area);
     return PG_OK;
 }
 
 void pg_batch_free(pg_batch *b) {
     if (!b) return;
-    for (void *p : {(void *)b->d_nodes, (void *)b->d_terms, (void *)b->d_term_slot, (void *)b->d_term_coef,
-                    (void *)b->d_out_first, (void *)b->d_out_n, (void *)b->d_out_div, (void *)b->d_slot_counts})
-        if (p) cudaFree(p);
+    if (b->image_owned && b->d_image) cudaFree(b->d_image);
     delete b;
 }
 
@@ -514,9 +581,9 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.terms = b->d_terms;
     a.n_roots = b->n_roots;
     a.n_slots = b->n_slots;
-    a.scratch = (int *)g->scratch;
+    a.scratch = (int *)g->ex->scratch;
     a.warp_stride = batch_layout(g, b, a.lvl_off);
-    a.queue = g->queues + queue_slot;
+    a.queue = g->ex->queues + queue_slot;
     a.n = (int)g->n;
     a.counts = b->d_slot_counts;
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
@@ -528,12 +595,12 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     if (b->clique_kmax) {
         if (g->max_out >= 65536) return pg_set_error(PG_EUNSUPPORTED, "clique kernel needs out-degrees below 65536");
         const int span = b->clique_kmax - b->clique_kmin + 1;
-        PG_CUDA(cudaMemsetAsync(g->tmp_counts, 0, 2 * sizeof(unsigned long long) * span, s));
-        int rc = pg_launch_clique(g, b->clique_kmin, b->clique_kmax, g->tmp_counts, queue_slot + 2, s);
+        PG_CUDA(cudaMemsetAsync(g->ex->tmp_counts, 0, 2 * sizeof(unsigned long long) * span, s));
+        int rc = pg_launch_clique(g, b->clique_kmin, b->clique_kmax, g->ex->tmp_counts, queue_slot + 2, s);
         if (rc) return rc;
         for (int p = 0; p < b->n_slots; ++p)
             if (b->clique_k[p])
-                PG_CUDA(cudaMemcpyAsync(b->d_slot_counts + 2 * p, g->tmp_counts + 2 * (b->clique_k[p] - b->clique_kmin),
+                PG_CUDA(cudaMemcpyAsync(b->d_slot_counts + 2 * p, g->ex->tmp_counts + 2 * (b->clique_k[p] - b->clique_kmin),
                                         2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
     }
     k_combine<<<(b->n_out + 63) / 64, 64, 0, s>>>(b->d_slot_counts, b->d_term_slot, b->d_term_coef, b->d_out_first,

@@ -426,8 +426,8 @@ size_t pg_clique_scratch_bytes(const pg_graph *g) {
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, int queue_slot,
                      cudaStream_t s) {
     if (queue_slot + 1 >= PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "queue slot out of range");
-    return launch(g, kmin, kmax, counts_dev, g->queues + queue_slot, g->scratch,
-                  (long long)(g->scratch_bytes / std::max<size_t>(pg_clique_slab_bytes(g), 1)), s);
+    return launch(g, kmin, kmax, counts_dev, g->ex->queues + queue_slot, g->ex->scratch,
+                  (long long)(g->ex->scratch_bytes / std::max<size_t>(pg_clique_slab_bytes(g), 1)), s);
 }
 
 // Same kernel on caller-supplied scratch: `queue` = two 64-bit counters

@@ -141,8 +141,8 @@ int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_
     a.orders = p->d_orders;
     a.n_orders = (int)p->h.orders.size();
     a.warp_stride = level_layout(g, p, a.lvl_off);
-    a.scratch = (int *)g->scratch;
-    a.queue = g->queues + queue_slot;
+    a.scratch = (int *)g->ex->scratch;
+    a.queue = g->ex->queues + queue_slot;
     a.n_tasks = n_tasks_of(g, p);
     a.persistent = persistent ? 1 : 0;
     a.counts = counts_dev;

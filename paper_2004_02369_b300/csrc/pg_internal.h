@@ -33,6 +33,20 @@ struct DevGraph {
 #define PG_MAX_HUBS 512
 
 #define PG_PAD 0x7fffffff
+
+#define PG_MAX_QUEUES 64
+
+// Per-launch-stream device state: the scratch arena (grown on demand), the
+// work-queue counters and small count buffers.  Launches that may overlap on
+// the device use different contexts.
+struct pg_exec {
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    unsigned long long *queues = nullptr;     // PG_MAX_QUEUES counters
+    unsigned long long *tmp_counts = nullptr; // 2 * PG_MAX_QUEUES words
+};
+int pg_exec_init(pg_exec *x);
+void pg_exec_release(pg_exec *x);
 #define PG_CLIQUE_LIGHT_D 64 // out-degree up to which one warp handles a clique start vertex
 
 struct pg_graph {
@@ -47,11 +61,11 @@ struct pg_graph {
     int32_t labeled = 0, n_labels = 0;
     int device = 0;
     int num_sms = 0;
-    // scratch arena (grown on demand) and per-launch work-queue counters
-    void *scratch = nullptr;
-    size_t scratch_bytes = 0;
-    unsigned long long *queues = nullptr; // PG_MAX_QUEUES counters
-    unsigned long long *tmp_counts = nullptr; // 2 * PG_MAX_QUEUES words
+    // execution context used by launches on this graph: the graph's own one,
+    // or (in server stream views) one per stream
+    pg_exec exec0;
+    pg_exec *ex = &exec0;
+    bool is_view = false;
     // vertices with out-degree > PG_CLIQUE_LIGHT_D, by out-degree descending
     int *heavy = nullptr;
     int64_t n_heavy = 0;
@@ -61,7 +75,6 @@ struct pg_graph {
     int64_t bytes_device = 0;
 };
 
-#define PG_MAX_QUEUES 64
 #define PG_STATIC_SCRATCH_BYTES (32u << 20) // fixed scratch of pg_count_cliques_noalloc
 
 struct pg_batch;
@@ -110,6 +123,9 @@ int pg_fsm_run(pg_graph *g, int max_edges, unsigned long long threshold, pg_fsm_
 // count_batched.cu: many plans, one launch over a shared prefix tree
 int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out);
 int pg_batch_build_trie(pg_batch *b);
+#define PG_BATCH_HOST_ONLY 0x100 // internal flag: build the tree only, stage later
+int pg_batch_upload(pg_batch *b);
+int pg_batch_stage(pg_batch *b, void *dev_area, void *host_area, size_t area_bytes, cudaStream_t s);
 void pg_batch_free(pg_batch *b);
 void pg_batch_stats(const pg_batch *b, int *nodes, int *programs, int *levels_total);
 int pg_batch_slots(const pg_batch *b);

@@ -1,0 +1,325 @@
+// Serving runtime: a request loop over a resident graph.
+//
+// Queries (patterns) arrive through pg_server_submit at any time; their
+// plans are compiled once and cached.  A worker thread admits waiting
+// queries into batches whenever one of the server's streams is free and the
+// batch's scratch requirement fits that stream's preallocated arena (device
+// memory admission), counts each batch in one launch of the batched kernel
+// (shared prefix tree, cliques through the clique kernel), and publishes the
+// results with their submit / start / completion times.  Batches on different
+// streams run concurrently on the device (continuous batching: queries that
+// arrive while others are on the GPU are admitted as soon as a stream frees
+// up).  With serial = 1 the same kernels run one query per launch, one
+// launch at a time -- the one-query-at-a-time baseline.
+//
+// Section 5.1 processing model (tasks = start vertices) applied to a stream
+// of patterns; the paper itself runs one mining program at a time.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "pg_internal.h"
+
+namespace {
+
+struct ServerQuery {
+    uint64_t ticket;
+    pg_plan *plan;
+    double t_submit;
+};
+
+struct Slot {
+    pg_exec ex;
+    pg_graph view;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void *d_area = nullptr, *h_area = nullptr;
+    size_t area_bytes = 0;
+    uint64_t *d_counts = nullptr, *h_counts = nullptr;
+    std::vector<ServerQuery> qs;
+    pg_batch *batch = nullptr;
+    double t_start = 0;
+    bool busy = false;
+};
+
+constexpr size_t kAreaBytes = 4u << 20;
+
+}  // namespace
+
+struct pg_server {
+    pg_graph *g = nullptr;
+    pg_server_config cfg{};
+    std::vector<Slot> slots;
+    std::mutex mu;
+    std::deque<ServerQuery> pending;
+    std::deque<pg_query_result> results;
+    std::mutex plan_mu;
+    std::unordered_map<std::string, pg_plan *> plans;
+    std::thread worker;
+    std::atomic<bool> stop{false};
+    std::atomic<int64_t> outstanding{0};
+    std::chrono::steady_clock::time_point t0;
+    int device = 0;
+    uint64_t next_ticket = 1;
+    std::atomic<int64_t> batches{0}, launched_queries{0};
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+std::string pattern_key(const pg_pattern_desc *d) {
+    std::string k = std::to_string(d->k) + "|" + std::to_string(d->vertex_induced) + "|";
+    auto pairs = [&](const int32_t *p, int n) {
+        std::vector<std::pair<int, int>> v;
+        for (int i = 0; i < n; ++i) v.push_back({std::min(p[2 * i], p[2 * i + 1]), std::max(p[2 * i], p[2 * i + 1])});
+        std::sort(v.begin(), v.end());
+        for (auto &e : v) k += std::to_string(e.first) + "-" + std::to_string(e.second) + ",";
+        k += "|";
+    };
+    pairs(d->edges, d->n_edges);
+    pairs(d->anti_edges, d->n_anti);
+    for (int u = 0; u < d->k; ++u) k += std::to_string(d->labels ? d->labels[u] : -1) + ",";
+    k += "|";
+    for (int u = 0; u < d->k; ++u) k += std::to_string(d->anti_vertex ? (int)d->anti_vertex[u] : 0);
+    return k;
+}
+
+void emit(pg_server *S, const ServerQuery &q, int status, const uint64_t *cnt, double t_start, double t_done, int bs) {
+    pg_query_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.ticket = q.ticket;
+    r.status = status;
+    r.count_lo = cnt ? cnt[0] : 0;
+    r.count_hi = cnt ? cnt[1] : 0;
+    r.t_submit = q.t_submit;
+    r.t_start = t_start;
+    r.t_done = t_done;
+    r.batch_size = bs;
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->results.push_back(r);
+}
+
+// Try to launch up to `take` queries on slot s; returns queries launched.
+int launch_batch(pg_server *S, Slot &s, std::vector<ServerQuery> qs) {
+    while (!qs.empty()) {
+        std::vector<pg_plan *> plans;
+        for (auto &q : qs) plans.push_back(q.plan);
+        pg_batch *b = nullptr;
+        int rc = pg_batch_build(plans.data(), (int)plans.size(), PG_BATCH_EXPAND_ANTI | PG_BATCH_HOST_ONLY, &b);
+        if (rc == PG_OK) {
+            const size_t need = pg_batch_scratch_bytes(&s.view, b);
+            if (need <= s.ex.scratch_bytes) {
+                rc = pg_batch_stage(b, s.d_area, s.h_area, s.area_bytes, s.stream);
+                if (rc == PG_OK) {
+                    s.t_start = S->now();
+                    rc = pg_launch_batched(&s.view, b, (unsigned long long *)s.d_counts, 0, s.stream);
+                }
+                if (rc == PG_OK) {
+                    cudaMemcpyAsync(s.h_counts, s.d_counts, 2 * sizeof(uint64_t) * qs.size(), cudaMemcpyDeviceToHost,
+                                    s.stream);
+                    cudaEventRecord(s.done, s.stream);
+                    s.batch = b;
+                    s.qs = qs;
+                    s.busy = true;
+                    S->batches++;
+                    S->launched_queries += (int64_t)qs.size();
+                    return (int)qs.size();
+                }
+            } else {
+                rc = PG_ENOMEM;
+            }
+            pg_batch_free(b);
+        }
+        if (qs.size() == 1) {
+            // the query alone does not fit (or fails): report it
+            emit(S, qs[0], rc, nullptr, S->now(), S->now(), 1);
+            S->outstanding--;
+            return 0;
+        }
+        // admit fewer: return the second half to the front of the queue
+        const size_t keep = qs.size() / 2;
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            for (size_t i = qs.size(); i-- > keep;) S->pending.push_front(qs[i]);
+        }
+        qs.resize(keep);
+    }
+    return 0;
+}
+
+void worker_loop(pg_server *S) {
+    cudaSetDevice(S->device);
+    const int max_batch = S->cfg.serial ? 1 : std::max(1, std::min(S->cfg.max_batch, (int)PG_MAX_QUEUES));
+    while (!S->stop.load()) {
+        bool progress = false;
+        for (Slot &s : S->slots) {
+            if (!s.busy || cudaEventQuery(s.done) != cudaSuccess) continue;
+            const double t = S->now();
+            for (size_t i = 0; i < s.qs.size(); ++i) emit(S, s.qs[i], PG_OK, s.h_counts + 2 * i, s.t_start, t, (int)s.qs.size());
+            S->outstanding -= (int64_t)s.qs.size();
+            pg_batch_free(s.batch);
+            s.batch = nullptr;
+            s.qs.clear();
+            s.busy = false;
+            progress = true;
+        }
+        for (Slot &s : S->slots) {
+            if (s.busy) continue;
+            std::vector<ServerQuery> take;
+            {
+                std::lock_guard<std::mutex> lock(S->mu);
+                while (!S->pending.empty() && (int)take.size() < max_batch) {
+                    take.push_back(S->pending.front());
+                    S->pending.pop_front();
+                }
+            }
+            if (take.empty()) break;
+            launch_batch(S, s, take);
+            progress = true;
+            if (S->cfg.serial) break;
+        }
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+}  // namespace
+
+extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_server **out) {
+    if (!g || !cfg || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    *out = nullptr;
+    pg_server *S = new (std::nothrow) pg_server();
+    if (!S) return pg_set_error(PG_ENOMEM, "host allocation failed");
+    S->g = g;
+    S->cfg = *cfg;
+    S->t0 = std::chrono::steady_clock::now();
+    const int n_streams = cfg->serial ? 1 : std::max(1, std::min(cfg->n_streams, 16));
+    int rc = PG_OK;
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e != cudaSuccess) {
+        delete S;
+        return pg_cuda_error(e, "cudaGetDevice");
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t budget = cfg->memory_budget > 0 ? (size_t)cfg->memory_budget : std::min<size_t>(free_b / 5 * 2, 64ull << 30);
+    const size_t per_stream = budget / n_streams;
+    S->slots.resize(n_streams);
+    for (Slot &s : S->slots) {
+        if ((rc = pg_exec_init(&s.ex)) != PG_OK) break;
+        if ((e = cudaMalloc(&s.ex.scratch, per_stream)) != cudaSuccess) { rc = pg_cuda_error(e, "server scratch"); break; }
+        s.ex.scratch_bytes = per_stream;
+        s.view = *g;
+        s.view.ex = &s.ex;
+        s.view.is_view = true;
+        s.view.batch_cache = nullptr;
+        s.view.batch_key.clear();
+        if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaMalloc(&s.d_area, kAreaBytes)) != cudaSuccess ||
+            (e = cudaMallocHost(&s.h_area, kAreaBytes)) != cudaSuccess ||
+            (e = cudaMalloc(&s.d_counts, 2 * sizeof(uint64_t) * PG_MAX_QUEUES)) != cudaSuccess ||
+            (e = cudaMallocHost(&s.h_counts, 2 * sizeof(uint64_t) * PG_MAX_QUEUES)) != cudaSuccess) {
+            rc = pg_cuda_error(e, "server stream setup");
+            break;
+        }
+        s.area_bytes = kAreaBytes;
+    }
+    if (rc) {
+        pg_server_free(S);
+        return rc;
+    }
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return PG_OK;
+}
+
+extern "C" int pg_server_submit(pg_server *S, const pg_pattern_desc *q, uint64_t *ticket) {
+    if (!S || !q || !ticket) return pg_set_error(PG_EINVAL, "NULL argument");
+    const double t = S->now();
+    pg_plan *plan = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(S->plan_mu);
+        const std::string key = pattern_key(q);
+        auto it = S->plans.find(key);
+        if (it != S->plans.end()) {
+            plan = it->second;
+        } else {
+            int rc = pg_compile_pattern(q, &plan);
+            if (rc) return rc;
+            if (plan->h.labeled && !S->g->labeled) {
+                pg_free_plan(plan);
+                return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+            }
+            S->plans[key] = plan;
+        }
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    *ticket = S->next_ticket++;
+    S->pending.push_back({*ticket, plan, t});
+    S->outstanding++;
+    return PG_OK;
+}
+
+extern "C" int pg_server_poll(pg_server *S, pg_query_result *out, int32_t max_results, int32_t *n_out) {
+    if (!S || !n_out || (max_results > 0 && !out)) return pg_set_error(PG_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(S->mu);
+    int n = 0;
+    while (n < max_results && !S->results.empty()) {
+        out[n++] = S->results.front();
+        S->results.pop_front();
+    }
+    *n_out = n;
+    return PG_OK;
+}
+
+extern "C" int pg_server_drain(pg_server *S, double timeout_s) {
+    if (!S) return pg_set_error(PG_EINVAL, "NULL argument");
+    const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (S->outstanding.load() > 0) {
+        if (std::chrono::steady_clock::now() > until) return pg_set_error(PG_ETIMEOUT, "queries still outstanding");
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    return PG_OK;
+}
+
+extern "C" int pg_server_get_stats(pg_server *S, pg_server_stats *out) {
+    if (!S || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_streams = (int32_t)S->slots.size();
+    out->batches = S->batches.load();
+    out->launched_queries = S->launched_queries.load();
+    out->outstanding = S->outstanding.load();
+    out->cached_plans = (int64_t)S->plans.size();
+    out->scratch_bytes_per_stream = S->slots.empty() ? 0 : (int64_t)S->slots[0].ex.scratch_bytes;
+    out->now = S->now();
+    return PG_OK;
+}
+
+extern "C" void pg_server_free(pg_server *S) {
+    if (!S) return;
+    S->stop = true;
+    if (S->worker.joinable()) S->worker.join();
+    for (Slot &s : S->slots) {
+        if (s.stream) cudaStreamSynchronize(s.stream);
+        if (s.batch) pg_batch_free(s.batch);
+        if (s.done) cudaEventDestroy(s.done);
+        if (s.stream) cudaStreamDestroy(s.stream);
+        if (s.d_area) cudaFree(s.d_area);
+        if (s.h_area) cudaFreeHost(s.h_area);
+        if (s.d_counts) cudaFree(s.d_counts);
+        if (s.h_counts) cudaFreeHost(s.h_counts);
+        pg_exec_release(&s.ex);
+    }
+    for (auto &kv : S->plans) pg_free_plan(kv.second);
+    delete S;
+}

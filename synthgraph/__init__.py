@@ -328,3 +328,46 @@ def motif4_patterns() -> list[dict]:
 def motif3_patterns() -> list[dict]:
     return [pattern(3, clique_edges(3), vertex_induced=True, name="induced_triangle"),
             pattern(3, chain_edges(3), vertex_induced=True, name="induced_wedge")]
+
+
+# ---------------------------------------------------------------------------
+# Serving query stream: count queries mixing 3-6 cliques, 4-5 cycles, the
+# 4-vertex chain, 3-5 vertex stars, tailed triangles (plain, with the tail
+# anti-adjacent to both other triangle vertices, and to one of them), with a
+# fraction of labeled variants (every pattern vertex labeled uniformly).
+# ---------------------------------------------------------------------------
+
+SERVING_TYPES = {
+    "K3": (3, clique_edges(3), []), "K4": (4, clique_edges(4), []),
+    "K5": (5, clique_edges(5), []), "K6": (6, clique_edges(6), []),
+    "C4": (4, cycle_edges(4), []), "C5": (5, cycle_edges(5), []),
+    "P4": (4, chain_edges(4), []),
+    "S3": (3, star_edges(3), []), "S4": (4, star_edges(4), []), "S5": (5, star_edges(5), []),
+    "TT": (4, TAILED_TRIANGLE, []), "TT_anti2": (4, TAILED_TRIANGLE, [(3, 1), (3, 2)]),
+    "TT_anti1": (4, TAILED_TRIANGLE, [(3, 1)]),
+}
+
+
+def serving_queries(n: int, seed: int, n_labels: int = 8, labeled_fraction: float = 0.1,
+                    types=None, labeled_only=()) -> list[dict]:
+    """n query patterns drawn uniformly over the types, a seeded fraction of
+    them (all of those whose type is in labeled_only) with every vertex
+    labeled uniformly over n_labels."""
+    rng = np.random.default_rng(seed)
+    names = list(types or SERVING_TYPES)
+    out = []
+    for _ in range(n):
+        name = names[int(rng.integers(len(names)))]
+        k, edges, anti = SERVING_TYPES[name]
+        labels = None
+        if rng.random() < labeled_fraction or name in labeled_only:
+            labels = [int(x) for x in rng.integers(0, n_labels, k)]
+        out.append(pattern(k, edges, anti_edges=anti, labels=labels,
+                           name=name + ("_lab" if labels else "")))
+    return out
+
+
+def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process with the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, n))
