@@ -73,6 +73,7 @@ struct Walker {
     unsigned *cbuf; // kMaxK level bitmaps of cws words
     unsigned *ring; // nslots candidate bitmaps
     int *items;     // kItems packed (slot << 16 | l)
+    unsigned *bsh;  // 32 re-indexed rows of compressed_row
     int cws, nslots;
     int m;          // queued items
     int used;       // ring slots in use
@@ -233,6 +234,76 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
     }
 }
 
+// Rows with at most 32 bits: re-index the sub-graph induced on R_i (the
+// common out-neighbours of v and list[i]) onto those bits, so that every
+// candidate set of the deeper levels is one 32-bit word.  Lane a holds
+// B_a = {b < a : p_b in R_{p_a}} for the a-th set bit p_a of R_i:
+//   4-cliques through (v, list[i]):  sum_a popc(B_a)
+//   5-cliques:  sum_a sum_{b in B_a} popc(B_a & B_b)
+//   6-cliques:  sum_a sum_{b in B_a} sum_{q in B_a & B_b} popc(B_a & B_b & B_q)
+// Returns false (nothing counted) when R_i has more than 32 bits.
+__device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, unsigned *bsh, int lane,
+                                               unsigned long long *cnt) {
+    const unsigned *Ri = t.rows + (size_t)i * t.ws;
+    const int nw = (i + 31) >> 5;
+    int c = 0;
+    for (int w = 0; w < nw; ++w) c += __popc(Ri[w]);
+    if (c > 32) return false;
+    if (c < 2) return true; // no edge inside R_i
+    // position p_a of the a-th bit, and the word prefix of bit counts
+    int pa = -1, prefix = 0;
+    for (int w = 0; w < nw; ++w) {
+        const unsigned x = Ri[w];
+        const int pc = __popc(x);
+        if (lane >= prefix && lane < prefix + pc) {
+            unsigned y = x;
+            for (int k = lane - prefix; k > 0; --k) y &= y - 1; // drop the lower set bits
+            pa = w * 32 + __ffs(y) - 1;
+        }
+        prefix += pc;
+    }
+    unsigned B = 0;
+    if (lane < c) {
+        const unsigned *Rp = t.rows + (size_t)pa * t.ws;
+        int pre = 0;
+        for (int w = 0; w <= ((pa - 1) >> 5) && pa > 0; ++w) {
+            const unsigned riw = Ri[w];
+            unsigned x = Rp[w] & riw;
+            while (x) {
+                const int b = __ffs(x) - 1;
+                x &= x - 1;
+                B |= 1u << (pre + __popc(riw & ((1u << b) - 1)));
+            }
+            pre += __popc(riw);
+        }
+    }
+    cnt[1] += __popc(B);
+    if (kmax >= 5) {
+        bsh[lane] = B;
+        __syncwarp();
+        unsigned long long s5 = 0, s6 = 0;
+        unsigned y = B;
+        while (y) {
+            const int b = __ffs(y) - 1;
+            y &= y - 1;
+            const unsigned z = B & bsh[b];
+            s5 += __popc(z);
+            if (kmax >= 6) {
+                unsigned zz = z;
+                while (zz) {
+                    const int q = __ffs(zz) - 1;
+                    zz &= zz - 1;
+                    s6 += __popc(z & bsh[q]);
+                }
+            }
+        }
+        cnt[2] += s5;
+        cnt[3] += s6;
+        __syncwarp();
+    }
+    return true;
+}
+
 // Pending products of the last level belong to size kmax: cnt[kmax - 3].
 __device__ __forceinline__ void drain(const Tile &t, Walker &wk, int kmax, int lane, unsigned long long *cnt) {
     if (wk.m == 0) {
@@ -265,6 +336,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
     wk.cbuf = smem + kCtl + a.region_words + (size_t)warp * a.warp_words;
     wk.ring = wk.cbuf + (size_t)kMaxK * a.cws;
     wk.items = (int *)(wk.ring + (size_t)a.nslots * a.cws);
+    wk.bsh = (unsigned *)(wk.items + kItems);
     wk.m = 0;
     wk.used = 0;
 
@@ -304,7 +376,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
                 r = __shfl_sync(PG_FULL, r, 0);
                 const int i = d - 1 - r; // longest rows first
                 if (i < 2) break;
-                walk<1>(ht, wk, ht.rows + (size_t)i * ht.ws, i, a.kmax, lane, cnt);
+                if (a.kmax > 6 || !compressed_row(ht, i, a.kmax, wk.bsh, lane, cnt))
+                    walk<1>(ht, wk, ht.rows + (size_t)i * ht.ws, i, a.kmax, lane, cnt);
             }
             drain(ht, wk, a.kmax, lane, cnt);
         }
@@ -338,7 +411,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
             __syncwarp();
             build_rows<false>(g, lt, d, lane, 32, cnt[0]);
             if (a.kmax >= 4) {
-                for (int i = d - 1; i >= 2; --i) walk<1>(lt, wk, lt.rows + (size_t)i * lt.ws, i, a.kmax, lane, cnt);
+                for (int i = d - 1; i >= 2; --i)
+                    if (a.kmax > 6 || !compressed_row(lt, i, a.kmax, wk.bsh, lane, cnt))
+                        walk<1>(lt, wk, lt.rows + (size_t)i * lt.ws, i, a.kmax, lane, cnt);
                 drain(lt, wk, a.kmax, lane, cnt);
             }
             __syncwarp();
@@ -366,7 +441,7 @@ Layout layout_for(const pg_graph *g) {
     a.hws = (int)(((D + 31) / 32) | 1);
     a.cws = std::max(a.hws, kLightWs);
     a.nslots = (int)std::min<long long>(32, std::max<long long>(2, 1024 / a.cws));
-    a.warp_words = (int)(((size_t)kMaxK * a.cws + (size_t)a.nslots * a.cws + kItems + 3) & ~3ull);
+    a.warp_words = (int)(((size_t)kMaxK * a.cws + (size_t)a.nslots * a.cws + kItems + 32 + 3) & ~3ull);
     const size_t heavy_words = (size_t)4 * a.dpad + 4 + (size_t)D * a.hws;
     const size_t light_words = (size_t)kWarps * kLightTile;
     const size_t warps_words = (size_t)kWarps * a.warp_words;
