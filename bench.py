@@ -26,6 +26,10 @@ sys.path.insert(0, ROOT)
 import synthgraph as sg  # noqa: E402
 
 WORKLOAD = "kclique_chunglu_n1M_m10M_g2.1"
+# ncu figures of k_count_clique on this workload (profiles/k_count_clique_chunglu_n1M_m10M.md),
+# valid only for the kernel source they were taken on
+NCU_CLIQUE = {"source_sha16": "9b62fc6937754486", "dram_bytes_per_launch": 88186880,
+              "l2_bytes_per_launch": 5773751136, "issue_active_frac": 0.693, "inst_executed_frac": 0.647}
 METRIC = "exact pattern matches/sec"
 UNIT = "matches/s"
 CLIQUE_SIZES = (4, 5)
@@ -309,10 +313,20 @@ def run_ours(args):
     hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     alg = algorithmic_bytes(g, G.rank(), min(CLIQUE_SIZES))
     achieved = alg / (ms_step / 1e3) / 1e9
+    import hashlib
+    src = os.path.join(ROOT, "paper_2004_02369_b300", "csrc", "count_clique.cu")
+    sha16 = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ncu_valid = sha16 == NCU_CLIQUE["source_sha16"]
+    traffic = args.traffic if args.traffic is not None else (NCU_CLIQUE["dram_bytes_per_launch"] if ncu_valid else None)
     roofline = {"bound": "hbm", "kernel": "k_count_clique", "achieved": achieved, "peak": hbm_peak,
                 "unit": "GB/s", "frac": achieved / hbm_peak,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg, "traffic": args.traffic}
+                "algorithmic_bytes_per_launch": alg, "traffic": traffic,
+                "ncu": ({"l2_bytes_per_launch": NCU_CLIQUE["l2_bytes_per_launch"],
+                         "issue_active_frac": NCU_CLIQUE["issue_active_frac"],
+                         "inst_executed_frac_of_peak": NCU_CLIQUE["inst_executed_frac"],
+                         "note": "graph is L2-resident; the kernel is instruction-issue bound"}
+                        if ncu_valid else None)}
 
     cpu_rate, _, cpu_secs = cpu_oracle_rate(g, 1)
     cfg = workload_config(g)
@@ -329,6 +343,113 @@ def run_ours(args):
                                        f"{cpu_secs:.1f} s"},
             "plain_one_pattern_per_launch": plain,
             "wall_s_timed": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- other workloads ---
+
+def _events_ms(fn, stream, reps=1):
+    import torch
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record(stream)
+    for _ in range(reps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def run_motif3(args):
+    """Induced triangles and wedges on ER G(2000, 0.005): launch-latency
+    bound, so microseconds per two-pattern batch, with and without CUDA-graph
+    replay of the captured batch launch."""
+    import torch
+    import paper_2004_02369_b300 as pg
+    torch.cuda.set_device(0)
+    g = sg.workload_graph(1)
+    G = pg.Graph.from_synth(g)
+    plans = [pg.Plan.from_dict(p) for p in sg.motif3_patterns()]
+    batch = pg.Batch(plans)
+    out = torch.zeros(4, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(5):
+            pg.count_batch(G, batch, out, stream=side)
+        reps = 200
+        eager_us = 1e3 * _events_ms(lambda: pg.count_batch(G, batch, out, stream=side), side, reps)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            pg.count_batch(G, batch, out, stream=side)
+        graph.replay()
+        graph_us = 1e3 * _events_ms(graph.replay, side, reps)
+    torch.cuda.synchronize()
+    counts = pg.decode_counts(out)
+    line = {"metric": "microseconds per batch of induced 3-motifs", "value": graph_us, "unit": "us",
+            "higher_is_better": False, "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "motif3_er_n2000_p0.005", "m": g.m,
+                       "patterns": ["induced_triangle", "induced_wedge"]},
+            "eager_us": eager_us, "cuda_graph_us": graph_us,
+            "counts": {"induced_triangle": counts[0], "induced_wedge": counts[1]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_motif4(args):
+    """The six induced 4-motifs of R-MAT scale 20 in one fused launch."""
+    import torch
+    import paper_2004_02369_b300 as pg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for sd in ([4, 0] if not args.motif4_small else [4]):
+        g = sg.workload_graph(3, scale_down=sd)
+        G = pg.Graph.from_synth(g)
+        plans = [pg.Plan.from_dict(p) for p in sg.motif4_patterns()]
+        out = torch.zeros(12, dtype=torch.int64, device="cuda")
+        b = pg.Batch(plans)
+        pg.count_batch(G, b, out)
+        fused = _events_ms(lambda: pg.count_batch(G, b, out), stream)
+        counts = pg.decode_counts(out)
+        row = {"n": g.n, "m": g.m, "fused_batched_ms": fused,
+               "counts": dict(zip([p["name"] for p in sg.motif4_patterns()], counts)),
+               "matches_per_s": sum(counts) / (fused / 1e3)}
+        if sd > 0:
+            sep = 0.0
+            o = torch.zeros(2, dtype=torch.int64, device="cuda")
+            for pl in plans:
+                sep += _events_ms(lambda: pg.count_async(G, [pl], o, kernel=pg.KERNEL_GENERIC), stream)
+            row["six_separate_launches_ms"] = sep
+        res[f"rmat_scale{20 - sd}"] = row
+    full = res.get("rmat_scale20") or res["rmat_scale16"]
+    line = {"metric": "exact pattern matches/sec", "value": full["matches_per_s"], "unit": "matches/s",
+            "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "motif4_induced_rmat_scale20_ef16"}, "results": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fsm(args):
+    """Frequent labeled patterns (1..3 edges, MNI >= 1000) on Chung-Lu 500K."""
+    import torch
+    import paper_2004_02369_b300 as pg
+    torch.cuda.set_device(0)
+    g = sg.workload_graph(4)
+    G = pg.Graph.from_synth(g)
+    pg.fsm(G, threshold=1000)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    freq = pg.fsm(G, threshold=1000)
+    dt = time.perf_counter() - t
+    by_shape = {}
+    for (shape, _), v in freq.items():
+        by_shape[shape] = by_shape.get(shape, 0) + 1
+    line = {"metric": "FSM wall seconds (all labeled patterns <= 3 edges, MNI >= 1000)", "value": dt,
+            "unit": "s", "higher_is_better": False, "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "fsm_chunglu_n500K_m5M_g2.3_zipf20", "threshold": 1000},
+            "frequent": len(freq), "frequent_by_shape": by_shape}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -423,7 +544,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kernel", type=int, default=0, help="PG_KERNEL_* (0 = auto)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
-    ap.add_argument("--workload", choices=["cliques", "serving"], default="cliques")
+    ap.add_argument("--workload", choices=["cliques", "serving", "motif3", "motif4", "fsm"], default="cliques")
+    ap.add_argument("--motif4-small", action="store_true", help="skip the full-size motif run")
     ap.add_argument("--serve-scale", type=int, default=16, help="R-MAT scale of the serving graph")
     ap.add_argument("--serve-n", type=int, default=300, help="queries per arrival rate")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
@@ -437,6 +559,12 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "motif3":
+        return run_motif3(args)
+    if args.workload == "motif4":
+        return run_motif4(args)
+    if args.workload == "fsm":
+        return run_fsm(args)
     return run_ours(args)
 
 
