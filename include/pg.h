@@ -55,7 +55,15 @@ typedef struct pg_batch pg_batch; /* several plans merged for one launch (opaque
  *   anti_edges   n_anti pairs (u, v): m(u) and m(v) must not be adjacent.
  *   labels       k labels, -1 = any label; NULL = unlabeled pattern.
  *   anti_vertex  k flags (1 = anti-vertex: never matched, only its anti-edges
- *                constrain the match); NULL = none.
+ *                constrain the match); NULL = none.  For an anti-vertex a
+ *                with regular neighbours N(a) (the vertices it has
+ *                anti-edges to) a match is valid only if no data vertex lies
+ *                in adj(m(u)) for every u in N(a) apart from the images of
+ *                the pattern neighbours of N(a) (Section 3.1.2).  An
+ *                anti-vertex has anti-edges only, to regular vertices only,
+ *                and no label (PG_EINVAL otherwise).  Anti-vertex patterns
+ *                run on PG_KERNEL_GENERIC (batches refuse them with
+ *                PG_EUNSUPPORTED).
  *   vertex_induced  1: every non-adjacent pair of regular vertices becomes
  *                an anti-edge (the Theorem of Section 3.1.3).
  * All arrays are host memory, read during pg_compile_pattern only.
@@ -193,6 +201,37 @@ int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *c
                 int32_t kernel, void *stream);
 
 /*
+ * pg_match - list the distinct matches of one plan's pattern (Section 3.2,
+ * match(G, p, f): the callback f becomes an output array).
+ *   out_dev   int32[capacity * k], device, caller-owned: row r holds one
+ *             match, column u the ORIGINAL id of the data vertex matched to
+ *             pattern vertex u (-1 in anti-vertex columns).  One row per
+ *             match (one representative per automorphism class, the one the
+ *             symmetry-breaking partial order of Section 4.1 keeps); row
+ *             order is unspecified.
+ *   capacity  rows available in out_dev (0 with out_dev NULL only counts).
+ *   n_total   host uint64: the number of matches, whatever the capacity.
+ * Synchronous (returns after *n_total is on the host).  If n_total exceeds
+ * capacity the first `capacity` rows are valid, distinct matches and the call
+ * returns PG_ETRUNC.  Errors: PG_EINVAL (NULL argument, labeled pattern on
+ * an unlabeled graph), PG_ETRUNC, PG_ENOMEM, PG_EDEVICE.
+ */
+int pg_match(pg_graph *g, pg_plan *p, int32_t *out_dev, uint64_t capacity, uint64_t *n_total,
+             void *stream);
+
+/*
+ * pg_match_range - pg_match restricted to the matches whose start vertex (the
+ * data vertex of the first matching-order position, Section 5.1 task) has
+ * degree rank in [rank_begin, rank_end), 0 <= rank_begin <= rank_end <= n.
+ * Disjoint ranges list disjoint sets of matches whose union over a partition
+ * of [0, n) is the full listing, so a result larger than one buffer can be
+ * paged range by range.  Same output and errors as pg_match, plus PG_EINVAL
+ * for a range outside [0, n].
+ */
+int pg_match_range(pg_graph *g, pg_plan *p, int64_t rank_begin, int64_t rank_end, int32_t *out_dev,
+                   uint64_t capacity, uint64_t *n_total, void *stream);
+
+/*
  * pg_count_cliques_noalloc - k-clique counts for every k in kmin..kmax
  * (3 <= kmin <= kmax <= 8), computed by the same kernel as PG_KERNEL_CLIQUE,
  * without allocating any device memory.  The paper has no counterpart: this
@@ -304,7 +343,9 @@ int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *o
  * publishes per-query results with submit / start / completion times.
  * Batches on different streams overlap on the device, and queries arriving
  * while others run are admitted as soon as a stream frees up.  Plans are
- * compiled once per distinct pattern and kept.  The paper runs one mining
+ * compiled once per distinct pattern and kept.  An anti-vertex query is
+ * launched alone on the plan interpreter (PG_KERNEL_GENERIC), since batches
+ * do not take anti-vertex plans.  The paper runs one mining
  * program at a time (Section 5.1); this loop applies its processing model to
  * a stream of patterns.
  *   n_streams      concurrent batches (1..16); memory_budget: device bytes

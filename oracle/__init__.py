@@ -18,6 +18,7 @@ adds the few closed forms that are easier to read in Python:
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 import subprocess
 from math import comb
@@ -63,6 +64,8 @@ def lib():
         u64p = ctypes.POINTER(ctypes.c_uint64)
         L.or_pattern_aut.argtypes = [ctypes.POINTER(_Pattern), u64p]
         L.or_count_maps.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), ctypes.c_int, u64p]
+        L.or_list_maps.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), ctypes.c_void_p,
+                                   ctypes.c_uint64, u64p]
         L.or_mni_bruteforce.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), u64p]
         L.or_triangles.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int]
         L.or_triangles.restype = ctypes.c_uint64
@@ -135,6 +138,61 @@ def count(g, p: dict, threads: int = 0) -> int:
     if maps % aut:
         raise AssertionError(f"maps {maps} not divisible by |Aut| {aut}")
     return maps // aut
+
+
+def automorphism_perms(p: dict) -> np.ndarray:
+    """Every permutation s of the pattern vertices (row: s[u] for u = 0..k-1)
+    that keeps edges, anti-edges, labels and anti-vertex status: brute force
+    over all k! permutations (Section 2.1)."""
+    k = p["k"]
+    rel = [[0] * k for _ in range(k)]
+    for (u, w) in p["edges"]:
+        rel[u][w] = rel[w][u] = 1
+    for (u, w) in p.get("anti_edges", ()):
+        rel[u][w] = rel[w][u] = 2
+    lab = p.get("labels") or [-1] * k
+    av = p.get("anti_vertex") or [0] * k
+    out = [s for s in itertools.permutations(range(k))
+           if all(lab[u] == lab[s[u]] and av[u] == av[s[u]] for u in range(k))
+           and all(rel[u][w] == rel[s[u]][s[w]] for u in range(k) for w in range(k))]
+    return np.array(out, dtype=np.int64)
+
+
+def list_maps(g, p: dict) -> np.ndarray:
+    """Every valid map as a row (column u = data vertex of pattern vertex u,
+    -1 at anti-vertices); rows = count_maps(g, p)."""
+    n = count_maps(g, p)
+    out = np.zeros((max(n, 1), p["k"]), dtype=np.int32)
+    gr = _GraphRef(g)
+    got = ctypes.c_uint64()
+    _check(lib().or_list_maps(ctypes.byref(gr.s), ctypes.byref(_pattern_struct(p)), out.ctypes.data,
+                              n, ctypes.byref(got)))
+    assert int(got.value) == n
+    return out[:n]
+
+
+def canonical_matches(rows: np.ndarray, p: dict) -> np.ndarray:
+    """The class of map m under Aut(p) is {m o s}; its representative here is
+    the lexicographically smallest row m[s] over s in Aut(p)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    best = rows.copy()
+    if rows.shape[0] == 0:
+        return best
+    for s in automorphism_perms(p):
+        cand = rows[:, s]
+        diff = cand != best
+        first = np.argmax(diff, axis=1)
+        r = np.arange(rows.shape[0])
+        less = diff.any(axis=1) & (cand[r, first] < best[r, first])
+        best[less] = cand[less]
+    return best
+
+
+def match_keys(g, p: dict) -> np.ndarray:
+    """The distinct matches of p in g (Section 2.1): one canonical row per
+    class of valid maps under Aut(p), sorted; len = count(g, p)."""
+    keys = canonical_matches(list_maps(g, p), p)
+    return np.unique(keys, axis=0) if keys.shape[0] else keys
 
 
 def mni_domains_bruteforce(g, p: dict) -> list[int]:

@@ -14,6 +14,10 @@
  *                    every edge, every anti-edge, every label and every
  *                    anti-vertex constraint.  Backtracking by neighbour
  *                    expansion (patterns are connected), no partial order.
+ *  or_list_maps      the maps counted by or_count_maps themselves, one row of
+ *                    k images per map (-1 at anti-vertices), for listing
+ *                    (Section 3.2, match()): matches are the classes of maps
+ *                    under Aut, formed by the caller.
  *  or_pattern_aut    |Aut| of a pattern by brute force over all k!
  *                    permutations (edges, anti-edges, labels and anti-vertex
  *                    status preserved), restricted to the regular vertices.
@@ -262,6 +266,53 @@ int or_count_maps(const or_graph *g, const or_pattern *p, int nthreads, uint64_t
         total += bt(&c, 1);
     }
     *maps_out = total;
+    return OR_OK;
+}
+
+/* ---------------------------- list maps ----------------------------------- */
+
+typedef struct {
+    bt_ctx c;
+    int32_t *out;
+    uint64_t capacity, n;
+} list_ctx;
+
+static void bt_list(list_ctx *L, int pos) {
+    bt_ctx *c = &L->c;
+    if (pos == c->o.nreg) {
+        if (!anti_vertices_ok(c)) return;
+        if (L->n < L->capacity) {
+            int32_t *row = L->out + L->n * (uint64_t)c->p->k;
+            for (int u = 0; u < c->p->k; ++u) row[u] = c->p->anti_vertex[u] ? -1 : (int32_t)c->phi[u];
+        }
+        L->n++;
+        return;
+    }
+    int u = c->o.order[pos];
+    int64_t par = c->phi[c->o.order[c->o.parent[pos]]];
+    for (int64_t e = c->g->off[par]; e < c->g->off[par + 1]; ++e) {
+        int64_t x = c->g->adj[e];
+        if (!compatible(c, pos, x)) continue;
+        c->phi[u] = x;
+        bt_list(L, pos + 1);
+    }
+}
+
+/* Every valid map as a row of k data vertices (phi(u) in column u, -1 for
+ * anti-vertices), at most `capacity` rows written; *n_out = number of maps.
+ * Single-threaded: meant for small graphs. */
+int or_list_maps(const or_graph *g, const or_pattern *p, int32_t *out, uint64_t capacity, uint64_t *n_out) {
+    if (validate_pattern(p)) return OR_EINVAL;
+    list_ctx L;
+    if (make_order(p, &L.c.o)) return OR_EINVAL;
+    L.c.g = g; L.c.p = p;
+    L.out = out; L.capacity = capacity; L.n = 0;
+    for (int64_t v = 0; v < g->n; ++v) {
+        if (!compatible(&L.c, 0, v)) continue;
+        L.c.phi[L.c.o.order[0]] = v;
+        bt_list(&L, 1);
+    }
+    *n_out = L.n;
     return OR_OK;
 }
 

@@ -83,6 +83,8 @@ _lib.pg_batch_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i3
 _lib.pg_count_batch.argtypes = [_vp, _vp, _vp, _vp]
 _lib.pg_free_batch.argtypes = [_vp]
 _lib.pg_free_batch.restype = None
+_lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
+_lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_last_error.restype = ctypes.c_char_p
 
 
@@ -287,6 +289,46 @@ def count_async(graph: Graph, plans, out, kernel: int = KERNEL_AUTO, stream=None
         raise ValueError("out must be a CUDA tensor with 2*len(plans) 64-bit elements")
     _check(_lib.pg_count_ex(graph.handle, _plan_array(plans), len(plans), out.data_ptr(),
                             kernel, _stream_ptr(stream)))
+
+
+def match(graph: Graph, plan: Plan, out=None, rank_range=None, stream=None):
+    """List the distinct matches of ``plan``'s pattern.
+
+    Returns ``(rows, n_total)``: ``rows`` is a torch CUDA int32 tensor of
+    shape (min(n_total, capacity), k), column u the original id of the data
+    vertex matched to pattern vertex u (-1 at anti-vertices).  ``out`` is an
+    optional caller-owned int32 CUDA tensor of shape (capacity, k); without
+    it the matches are counted first (pg_match with capacity 0) and a tensor
+    of exactly that size is allocated.  ``rank_range`` = (begin, end) lists
+    only the matches whose start vertex has degree rank in [begin, end).
+    A result larger than ``out`` keeps the first rows and raises nothing;
+    compare ``n_total`` with the capacity.
+    """
+    import torch
+    k = plan.pattern["k"]
+    n = graph.info().n
+    lo, hi = (0, n) if rank_range is None else (int(rank_range[0]), int(rank_range[1]))
+    total = ctypes.c_uint64()
+    sp = _stream_ptr(stream)
+
+    def call(ptr, cap):
+        return _lib.pg_match_range(graph.handle, plan.handle, lo, hi, ptr, cap, ctypes.byref(total), sp)
+
+    if out is None:
+        rc = call(None, 0)
+        if rc not in (PG_OK, PG_ETRUNC):
+            _check(rc)
+        out = torch.empty((max(int(total.value), 1), k), dtype=torch.int32, device="cuda")
+        if int(total.value) == 0:
+            return out[:0], 0
+    if not out.is_cuda or out.dtype != torch.int32 or out.dim() != 2 or out.shape[1] != k or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int32 CUDA tensor of shape (capacity, k)")
+    cap = out.shape[0]
+    rc = call(out.data_ptr(), cap)
+    if rc not in (PG_OK, PG_ETRUNC):
+        _check(rc)
+    n_total = int(total.value)
+    return out[:min(n_total, cap)], n_total
 
 
 def count_cliques_noalloc(graph: Graph, kmin: int, kmax: int, out, stream=None):

@@ -114,6 +114,7 @@ extern "C" void pg_free_graph(pg_graph *g) {
     if (g->vinfo) cudaFree(g->vinfo);
     if (g->adj) cudaFree(g->adj);
     if (g->rank) cudaFree(g->rank);
+    if (g->orig) cudaFree(g->orig);
     if (g->hubbits) cudaFree(g->hubbits);
     pg_exec_release(&g->exec0);
     if (g->heavy) cudaFree(g->heavy);
@@ -188,7 +189,9 @@ extern "C" int pg_compile_pattern(const pg_pattern_desc *d, pg_plan **out) {
     }
     static std::atomic<uint64_t> next_serial{1};
     pl->serial = next_serial++;
-    pl->kernel_auto = (pl->h.is_clique && pl->h.pat.k >= 3) ? PG_KERNEL_CLIQUE : PG_KERNEL_BATCHED;
+    pl->kernel_auto = (pl->h.is_clique && pl->h.pat.k >= 3) ? PG_KERNEL_CLIQUE
+                      : pl->h.anti_vertices                  ? PG_KERNEL_GENERIC
+                                                             : PG_KERNEL_BATCHED;
     *out = pl;
     return PG_OK;
 }
@@ -250,14 +253,18 @@ extern "C" int pg_plan_describe(const pg_plan *pl, char *buf, int64_t size) {
 extern "C" void pg_free_plan(pg_plan *pl) {
     if (!pl) return;
     if (pl->d_orders) cudaFree(pl->d_orders);
+    if (pl->d_list_orders) cudaFree(pl->d_list_orders);
     delete pl;
 }
 
 int pg_plan_upload(pg_plan *pl) {
     if (pl->d_orders || pl->h.orders.empty()) return PG_OK;
     const size_t bytes = pl->h.orders.size() * sizeof(PgOrder);
+    const size_t lbytes = pl->h.list_orders.size() * sizeof(PgOrder);
     PG_CUDA(cudaMalloc(&pl->d_orders, bytes));
     PG_CUDA(cudaMemcpy(pl->d_orders, pl->h.orders.data(), bytes, cudaMemcpyHostToDevice));
+    PG_CUDA(cudaMalloc(&pl->d_list_orders, lbytes));
+    PG_CUDA(cudaMemcpy(pl->d_list_orders, pl->h.list_orders.data(), lbytes, cudaMemcpyHostToDevice));
     return PG_OK;
 }
 
@@ -270,18 +277,22 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
     if (n_plans > PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "at most 64 plans per call");
     if (n_plans == 0) return PG_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    bool all_clique = true;
+    bool all_clique = true, any_anti_vertex = false;
     int kmin = PG_MAX_PATTERN + 1, kmax = 0;
     for (int i = 0; i < n_plans; ++i) {
         if (!plans[i]) return pg_set_error(PG_EINVAL, "NULL plan");
         const PgPlanHost &h = plans[i]->h;
         if (h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
         all_clique &= h.is_clique && h.pat.k >= 3;
+        any_anti_vertex |= h.anti_vertices;
         kmin = std::min(kmin, h.pat.k);
         kmax = std::max(kmax, h.pat.k);
     }
     if (all_clique && g->max_out >= 65536) all_clique = false;
-    if (kernel == PG_KERNEL_AUTO) kernel = all_clique ? PG_KERNEL_CLIQUE : PG_KERNEL_BATCHED;
+    if (kernel == PG_KERNEL_AUTO)
+        kernel = all_clique ? PG_KERNEL_CLIQUE : any_anti_vertex ? PG_KERNEL_GENERIC : PG_KERNEL_BATCHED;
+    if (any_anti_vertex && kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN)
+        return pg_set_error(PG_EUNSUPPORTED, "anti-vertex patterns run on the plan interpreter (PG_KERNEL_GENERIC)");
     if (kernel == PG_KERNEL_CLIQUE && !all_clique)
         return pg_set_error(PG_EINVAL, "PG_KERNEL_CLIQUE needs unlabeled k-clique patterns, k >= 3");
     if (kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN && kernel != PG_KERNEL_CLIQUE &&
@@ -374,6 +385,38 @@ extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uin
     PG_CUDA(cudaMemcpyAsync(counts_out, c.p, 2 * sizeof(uint64_t) * n_plans, cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
     return PG_OK;
+}
+
+// ---------------------------------------------------------------- match ----
+
+extern "C" int pg_match_range(pg_graph *g, pg_plan *pl, int64_t rank_begin, int64_t rank_end, int32_t *out_dev,
+                              uint64_t capacity, uint64_t *n_total, void *stream) {
+    if (!g || !pl || !n_total || (capacity > 0 && !out_dev)) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (rank_begin < 0 || rank_end < rank_begin || rank_end > g->n)
+        return pg_set_error(PG_EINVAL, "start-vertex rank range out of bounds");
+    if (pl->h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+    if (capacity > (uint64_t)INT64_MAX / (uint64_t)pl->h.pat.k) return pg_set_error(PG_EINVAL, "capacity too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = pg_plan_upload(pl);
+    if (rc) return rc;
+    rc = pg_ensure_scratch(g, pg_match_scratch_bytes(g, pl), s);
+    if (rc) return rc;
+    unsigned long long *counter = g->ex->tmp_counts;
+    rc = pg_launch_match(g, pl, rank_begin, rank_end, out_dev, capacity, counter, s);
+    if (rc) return rc;
+    unsigned long long total = 0;
+    PG_CUDA(cudaMemcpyAsync(&total, counter, sizeof(total), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    *n_total = total;
+    if (total > capacity)
+        return pg_set_error(PG_ETRUNC, "more matches than capacity: the first `capacity` rows were written");
+    return PG_OK;
+}
+
+extern "C" int pg_match(pg_graph *g, pg_plan *pl, int32_t *out_dev, uint64_t capacity, uint64_t *n_total,
+                        void *stream) {
+    if (!g) return pg_set_error(PG_EINVAL, "NULL argument");
+    return pg_match_range(g, pl, 0, g->n, out_dev, capacity, n_total, stream);
 }
 
 extern "C" int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *out, int64_t capacity,

@@ -276,6 +276,9 @@ std::vector<int> canonical(const PgPattern &q) {
 // merged and counted once by their own (edge-induced) plans.
 int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out) {
     if (n_plans < 1 || n_plans > kMaxSlots) return pg_set_error(PG_EINVAL, "a batch holds 1..64 plans");
+    for (int i = 0; i < n_plans; ++i)
+        if (plans[i]->h.anti_vertices)
+            return pg_set_error(PG_EUNSUPPORTED, "anti-vertex patterns run on the plan interpreter (PG_KERNEL_GENERIC)");
     pg_batch *bb = new (std::nothrow) pg_batch();
     if (!bb) return pg_set_error(PG_ENOMEM, "host allocation failed");
     std::map<std::vector<int>, int> slot_of;

@@ -17,7 +17,9 @@
 // elements, check membership in the other lists by binary search, compact
 // with __ballot_sync/__popc) into a per-warp scratch buffer.  The last level
 // is counted, by inclusion-exclusion over its difference lists when that
-// touches fewer elements than filtering the driver list.
+// touches fewer elements than filtering the driver list.  Levels that carry
+// anti-vertex checks (Section 4.3) are filtered candidate by candidate; a
+// checked last level is enumerated instead of counted.
 #include "level_ops.cuh"
 
 namespace {
@@ -45,19 +47,24 @@ __device__ unsigned __int128 run_task(const GenericArgs &a, int v, const PgOrder
     const int L = ord.n_levels;
     const int4 v0 = __ldg(&g.vinfo[v]);
     if (ord.lv[0].label >= 0 && v0.w != ord.lv[0].label) return 0;
-    if (L == 1) return 1;
     int m[PGP_MAXK];
     int sz[PGP_MAXK], idx[PGP_MAXK];
     m[0] = v;
+    if (ord.lv[0].n_anti && !checks_ok(g, ord, 0, m, lane)) return 0;
+    if (L == 1) return 1;
     unsigned __int128 total = 0;
     int l = 1;
     for (;;) {
-        if (l == L - 1) {
-            const unsigned long long c = count_last(g, ord.lv[l], m, lane);
-            total += choose_u128(c, ord.lv[l].group);
+        const PgLevel &lv = ord.lv[l];
+        if (l == L - 1 && !lv.n_anti) {
+            const unsigned long long c = count_last(g, lv, m, lane);
+            total += choose_u128(c, lv.group);
         } else {
-            sz[l] = fill_level(g, ord.lv[l], m, wbuf + a.lvl_off[l], lane);
+            int *buf = wbuf + a.lvl_off[l];
+            sz[l] = fill_level(g, lv, m, buf, lane);
+            if (lv.n_anti) sz[l] = filter_anti(g, ord, l, m, buf, sz[l], lane);
             idx[l] = 0;
+            if (l == L - 1) total += (unsigned)sz[l]; // checked vertices are never grouped
         }
         // advance to the next unexplored candidate
         while (l >= 1 && (l == L - 1 || idx[l] >= sz[l])) --l;
@@ -96,23 +103,31 @@ int generic_grid(const pg_graph *g) {
     return per_sm * g->num_sms;
 }
 
-// Per-warp buffer layout: level l (1 <= l < n_levels - 1) gets max out-degree
-// ints when its candidates lie in the start's out-neighbourhood, else max
-// degree ints (each rounded to 32).
-long long level_layout(const pg_graph *g, const pg_plan *p, long long *off) {
+}  // namespace
+
+// Per-warp buffer layout: every materialised level l >= 1 (all but a counted
+// last level) gets max out-degree ints when its candidates lie in a bound
+// vertex's out-neighbourhood, else max degree ints (each rounded to 32).
+long long pg_level_layout(const pg_graph *g, const std::vector<PgOrder> &orders, bool listing, long long *off) {
     const long long cap_out = (g->max_out + 31) & ~31ll, cap_all = (g->max_deg + 31) & ~31ll;
     long long total = 0;
     for (int l = 0; l < PGP_MAXK; ++l) {
         off[l] = total;
         bool any = false, all_out = true;
-        for (auto &o : p->h.orders)
-            if (l >= 1 && l < o.n_levels - 1) {
+        for (auto &o : orders)
+            if (l >= 1 && (l < o.n_levels - 1 || (l == o.n_levels - 1 && (listing || o.lv[l].n_anti)))) {
                 any = true;
                 all_out &= o.lv[l].out_bounded != 0;
             }
         if (any) total += all_out ? cap_out : cap_all;
     }
     return total;
+}
+
+namespace {
+
+long long level_layout(const pg_graph *g, const pg_plan *p, long long *off) {
+    return pg_level_layout(g, p->h.orders, false, off);
 }
 
 unsigned long long n_tasks_of(const pg_graph *g, const pg_plan *p) {

@@ -60,13 +60,14 @@ __global__ void k_degree_keys(const int64_t *off, int64_t n, unsigned long long 
     keys[v] = ((0xffffffffull - deg) << 32) | (unsigned long long)v;
 }
 
-// rank[orig] = r ; pdeg[r] = padded degree ; udeg[r] = degree
-__global__ void k_rank(const unsigned long long *sorted, const int64_t *off, int64_t n, int *rank,
+// rank[orig] = r ; orig_of[r] = orig ; pdeg[r] = padded degree ; udeg[r] = degree
+__global__ void k_rank(const unsigned long long *sorted, const int64_t *off, int64_t n, int *rank, int *orig_of,
                        int64_t *pdeg, int64_t *udeg) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int v = (int)(sorted[r] & 0xffffffffull);
     rank[v] = (int)r;
+    orig_of[r] = v;
     const int64_t d = off[v + 1] - off[v];
     udeg[r] = d;
     pdeg[r] = (d + 3) & ~3ll;
@@ -194,6 +195,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     PG_CUDA(cudaMalloc(&ustart.p, nn * sizeof(int64_t)));
     PG_CUDA(cudaMalloc(&pstart.p, nn * sizeof(int64_t)));
     PG_CUDA(cudaMalloc(&g->rank, nn * sizeof(int)));
+    PG_CUDA(cudaMalloc(&g->orig, nn * sizeof(int)));
     PG_CUDA(cudaMalloc(&g->vinfo, nn * sizeof(int4)));
     PG_CUDA(cudaMalloc(&maxes_b.p, 3 * sizeof(int)));
     int *maxes = (int *)maxes_b.p;
@@ -219,7 +221,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, need, (unsigned long long *)vkeys.p,
                                            (unsigned long long *)vkeys2.p, (int64_t)n, 0, 64, s));
     const unsigned long long *sorted = (const unsigned long long *)vkeys2.p;
-    k_rank<<<grid_for(n, kBlock), kBlock, 0, s>>>(sorted, d_off, n, g->rank, (int64_t *)pdeg.p,
+    k_rank<<<grid_for(n, kBlock), kBlock, 0, s>>>(sorted, d_off, n, g->rank, g->orig, (int64_t *)pdeg.p,
                                                   (int64_t *)udeg.p);
     need = tmp_bytes;
     PG_CUDA(cub::DeviceScan::ExclusiveSum(tmp.p, need, (int64_t *)pdeg.p, (int64_t *)pstart.p, (int64_t)n, s));
@@ -297,7 +299,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
         PG_CUDA(cudaGetLastError());
         PG_CUDA(cudaStreamSynchronize(s));
     }
-    g->bytes_device = (int64_t)(nn * (sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int)) +
+    g->bytes_device = (int64_t)(nn * (2 * sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int)) +
                       (int64_t)g->n_hubs * g->hub_stride * 4 + g->n_heavy * 4;
     return PG_OK;
 }

@@ -155,6 +155,58 @@ static __device__ __noinline__ unsigned long long count_last(const DevGraph &g, 
     return (unsigned long long)total;
 }
 
+// Anti-vertex check C on the bound images m (Section 3.1.2): true iff no
+// data vertex lies in every adj(m[int_src]) other than the images
+// m[excl_src].  The warp walks the shortest list and stops at the first
+// witness.
+static __device__ __noinline__ bool anti_ok(const DevGraph &g, const PgAntiCheck &C, const int *m, int lane) {
+    Slice s[PGP_MAXK];
+    int drv = 0;
+    for (int i = 0; i < C.n_int; ++i) {
+        const int w = m[C.int_src[i]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        s[i] = Slice{adj_of(g, vi), vi.y, w};
+        if (s[i].len < s[drv].len) drv = i;
+    }
+    const Slice d = s[drv];
+    for (int base = 0; base < d.len; base += 32) {
+        const int idx = base + lane;
+        bool hit = idx < d.len;
+        if (hit) {
+            const int x = __ldg(d.p + idx);
+            for (int i = 0; i < C.n_int && hit; ++i)
+                if (i != drv) hit = in_slice(g, s[i], x);
+            for (int i = 0; i < C.n_excl && hit; ++i) hit = x != m[C.excl_src[i]];
+        }
+        if (__any_sync(PG_FULL, hit)) return false;
+    }
+    return true;
+}
+
+// Every anti-vertex check attached to level l passes for the images m.
+__device__ __forceinline__ bool checks_ok(const DevGraph &g, const PgOrder &ord, int l, const int *m, int lane) {
+    bool ok = true;
+    for (int c = 0; c < ord.n_checks && ok; ++c)
+        if (ord.chk[c].level == l) ok = anti_ok(g, ord.chk[c], m, lane);
+    return ok;
+}
+
+// Keep the candidates buf[0, n) of level l that pass its anti-vertex checks
+// (m[l] takes each candidate in turn); returns how many are kept, in order.
+static __device__ __noinline__ int filter_anti(const DevGraph &g, const PgOrder &ord, int l, int *m, int *buf, int n,
+                                               int lane) {
+    int kept = 0;
+    for (int i = 0; i < n; ++i) {
+        const int x = buf[i];
+        m[l] = x;
+        if (checks_ok(g, ord, l, m, lane)) {
+            if (lane == 0) buf[kept] = x; // kept <= i: never a slot still to be read
+            ++kept;
+        }
+    }
+    __syncwarp();
+    return kept;
+}
 
 // A set given by a level spec is a plain bounded slice of one adjacency list
 // (minus excluded images) when it has one intersected list, no differences

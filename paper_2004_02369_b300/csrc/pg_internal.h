@@ -54,6 +54,7 @@ struct pg_graph {
     int4 *vinfo = nullptr;
     int *adj = nullptr;
     int *rank = nullptr; // original id -> rank
+    int *orig = nullptr; // rank -> original id
     unsigned *hubbits = nullptr;
     int64_t n = 0, m = 0, adj_entries = 0;
     int64_t max_deg = 0, max_out = 0;
@@ -83,6 +84,7 @@ struct pg_plan {
     PgPlanHost h;
     uint64_t serial = 0;         // unique per compiled plan (batch cache key)
     PgOrder *d_orders = nullptr; // device copy of h.orders
+    PgOrder *d_list_orders = nullptr; // device copy of h.list_orders
     int kernel_auto = PG_KERNEL_GENERIC;
 };
 
@@ -109,6 +111,14 @@ int pg_plan_upload(pg_plan *p);
 int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev,
                       int queue_slot, bool persistent, cudaStream_t s);
 size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persistent);
+// per-warp level buffers of a level program (offsets per level, total ints)
+long long pg_level_layout(const pg_graph *g, const std::vector<PgOrder> &orders, bool listing, long long *off);
+
+// match_list.cu: listing of the matches whose start vertex has rank in
+// [rank_begin, rank_end); rows of k original ids (-1 at anti-vertices)
+int pg_launch_match(pg_graph *g, const pg_plan *p, int64_t rank_begin, int64_t rank_end, int32_t *out,
+                    unsigned long long capacity, unsigned long long *n_total_dev, cudaStream_t s);
+size_t pg_match_scratch_bytes(const pg_graph *g, const pg_plan *p);
 
 // count_clique.cu: sizes kmin..kmax in one launch, counts_dev[2*(k-kmin)]
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,

@@ -103,10 +103,15 @@ bool is_chain_group(const PgPattern &p, const Closure &c, const std::vector<int>
     return true;
 }
 
-std::vector<std::vector<int>> noncore_groups(const PgPattern &p, const Closure &c, uint32_t noncore) {
+std::vector<std::vector<int>> noncore_groups(const PgPattern &p, const Closure &c, uint32_t noncore,
+                                             uint32_t singles = 0) {
     std::vector<std::vector<int>> classes, groups;
     for (int u = 0; u < p.k; ++u) {
         if (!(noncore >> u & 1)) continue;
+        if (singles >> u & 1) {
+            groups.push_back({u});
+            continue;
+        }
         bool placed = false;
         for (auto &g : classes)
             if (twins(p, g[0], u)) {
@@ -166,6 +171,167 @@ int core_scan_cost(const PgPattern &p, const Closure &cl, uint32_t core_mask) {
     return cost;
 }
 
+// Anti-vertex a: its regular neighbours, and those plus their pattern
+// neighbours (every regular vertex its check reads).
+struct AntiSpec {
+    uint32_t nbrs, reads;
+};
+
+// computeMatchingOrders (Section 4.1) and the lowering of each order into a
+// level program.  groups: the non-core groups; counted: index of the group
+// counted from its set's cardinality (-1: every vertex enumerated); partner:
+// index of a single-vertex group counted jointly with it (-1: none).
+int lower_orders(const PgPattern &p, const Closure &cl, uint32_t best, const std::vector<std::vector<int>> &groups,
+                 int counted, int partner, const std::vector<AntiSpec> &avs, std::vector<PgOrder> &orders,
+                 std::string &err) {
+    const int k = p.k;
+    std::vector<int> core;
+    for (int u = 0; u < k; ++u)
+        if (best >> u & 1) core.push_back(u);
+    const int c = (int)core.size();
+    std::vector<int> seq = core;
+    std::sort(seq.begin(), seq.end());
+    do {
+        int pos[PGP_MAXK];
+        for (int i = 0; i < k; ++i) pos[i] = -1;
+        for (int i = 0; i < c; ++i) pos[seq[i]] = i;
+        bool ok = true;
+        for (int a : core)
+            for (int b : core)
+                if (cl.less[a][b] && pos[a] > pos[b]) ok = false;
+        if (!ok) continue;
+        if (orders.size() >= PGP_MAX_ORDERS) { err = "too many matching orders"; return PG_EINVAL; }
+
+        // Exploration order: start from the highest sequence position (the
+        // task's start vertex, Section 5.2 high-to-low), then repeatedly the
+        // highest-position core vertex adjacent to one already bound.
+        int lvl_of[PGP_MAXK];
+        for (int i = 0; i < k; ++i) lvl_of[i] = -1;
+        std::vector<int> bound_order;
+        bound_order.push_back(seq[c - 1]);
+        lvl_of[seq[c - 1]] = 0;
+        while ((int)bound_order.size() < c) {
+            int pick = -1;
+            for (int i = c - 1; i >= 0 && pick < 0; --i) {
+                int u = seq[i];
+                if (lvl_of[u] >= 0) continue;
+                for (int x : bound_order)
+                    if (p.rel[u][x] == 1) { pick = u; break; }
+            }
+            lvl_of[pick] = (int)bound_order.size();
+            bound_order.push_back(pick);
+        }
+        // non-core: enumerated groups first (chain order), counted group last;
+        // a single counted vertex is paired with another single non-core
+        // vertex placed right before it (joint counting of the last two)
+        std::vector<int> nc_order;
+        for (int i = 0; i < (int)groups.size(); ++i)
+            if (i != counted && i != partner)
+                for (int u : groups[i]) nc_order.push_back(u);
+        if (partner >= 0) nc_order.push_back(groups[partner][0]);
+        for (int u : nc_order) {
+            lvl_of[u] = (int)bound_order.size();
+            bound_order.push_back(u);
+        }
+        int counted_first = -1;
+        if (counted >= 0) {
+            counted_first = groups[counted][0];
+            lvl_of[counted_first] = (int)bound_order.size();
+            bound_order.push_back(counted_first);
+        }
+
+        PgOrder ord;
+        std::memset(&ord, 0, sizeof(ord));
+        ord.n_levels = (int)bound_order.size();
+        ord.n_core = c;
+        for (int l = 0; l < ord.n_levels; ++l) {
+            const int u = bound_order[l];
+            PgLevel &L = ord.lv[l];
+            L.pattern_vertex = (int8_t)u;
+            L.is_core = (int8_t)((best >> u) & 1);
+            L.label = p.label[u];
+            L.group = (int8_t)((u == counted_first) ? (int)groups[counted].size() : 1);
+            L.joint = (int8_t)(u == counted_first && partner >= 0);
+            if (l == 0) continue;
+            const bool core_level = L.is_core;
+            int lo_core = -1, hi_core = -1; // tightest core bounds (by position)
+            for (int j = 0; j < l; ++j) {
+                const int x = bound_order[j];
+                if (p.rel[u][x] == 1) L.int_src[L.n_int++] = (int8_t)j;
+                if (p.rel[u][x] == 2) L.diff_src[L.n_diff++] = (int8_t)j;
+                const bool x_core = (best >> x) & 1;
+                bool below, above; // m(x) < m(u) / m(x) > m(u) required
+                if (core_level && x_core) {
+                    below = pos[x] < pos[u];
+                    above = pos[x] > pos[u];
+                } else {
+                    below = cl.less[x][u];
+                    above = cl.less[u][x];
+                }
+                if (x_core && (below || above)) {
+                    if (below && (lo_core < 0 || pos[x] > pos[bound_order[lo_core]])) lo_core = j;
+                    if (above && (hi_core < 0 || pos[x] < pos[bound_order[hi_core]])) hi_core = j;
+                } else {
+                    if (below) L.lo_src[L.n_lo++] = (int8_t)j;
+                    if (above) L.hi_src[L.n_hi++] = (int8_t)j;
+                }
+            }
+            if (lo_core >= 0) L.lo_src[L.n_lo++] = (int8_t)lo_core;
+            if (hi_core >= 0) L.hi_src[L.n_hi++] = (int8_t)hi_core;
+            // candidates adjacent to a bound vertex x and ranked below it lie
+            // in N+(x): at most max out-degree of them
+            {
+                bool bounded = false;
+                for (int i = 0; i < L.n_int && !bounded; ++i) {
+                    const int x = bound_order[L.int_src[i]];
+                    const bool x_core = (best >> x) & 1;
+                    if (cl.less[u][x]) bounded = true;
+                    if (x_core && hi_core >= 0 && pos[bound_order[hi_core]] <= pos[x]) bounded = true;
+                    if (core_level && x_core && pos[x] > pos[u]) bounded = true;
+                }
+                L.out_bounded = (int8_t)bounded;
+            }
+            // injectivity: exclude every earlier image not already ruled out
+            for (int j = 0; j < l; ++j) {
+                const int x = bound_order[j];
+                const bool x_core = (best >> x) & 1;
+                bool out_of_set = false;
+                for (int i = 0; i < L.n_int && !out_of_set; ++i) {
+                    int y = bound_order[L.int_src[i]];
+                    if (y == x || p.rel[x][y] == 2) out_of_set = true; // m(x) not in adj(m(y))
+                }
+                for (int i = 0; i < L.n_diff && !out_of_set; ++i)
+                    if (p.rel[x][bound_order[L.diff_src[i]]] == 1) out_of_set = true;
+                for (int i = 0; i < L.n_lo && !out_of_set; ++i) {
+                    int y = bound_order[L.lo_src[i]];
+                    if (y == x || (x_core && ((best >> y) & 1) && pos[x] <= pos[y])) out_of_set = true;
+                }
+                for (int i = 0; i < L.n_hi && !out_of_set; ++i) {
+                    int y = bound_order[L.hi_src[i]];
+                    if (y == x || (x_core && ((best >> y) & 1) && pos[x] >= pos[y])) out_of_set = true;
+                }
+                if (!out_of_set && L.label >= 0 && p.label[x] >= 0 && p.label[x] != L.label) out_of_set = true;
+                if (!out_of_set) L.excl_src[L.n_excl++] = (int8_t)j;
+            }
+        }
+        // anti-vertex checks, each at the level binding the last vertex it reads
+        for (const AntiSpec &a : avs) {
+            PgAntiCheck &C = ord.chk[ord.n_checks++];
+            int at = 0;
+            for (int u = 0; u < p.k; ++u)
+                if (a.reads >> u & 1) at = std::max(at, lvl_of[u]);
+            C.level = (int8_t)at;
+            for (int u = 0; u < p.k; ++u) {
+                if (a.nbrs >> u & 1) C.int_src[C.n_int++] = (int8_t)lvl_of[u];
+                else if (a.reads >> u & 1) C.excl_src[C.n_excl++] = (int8_t)lvl_of[u];
+            }
+            ord.lv[at].n_anti++;
+        }
+        orders.push_back(ord);
+    } while (std::next_permutation(seq.begin(), seq.end()));
+    return PG_OK;
+}
+
 }  // namespace
 
 int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, std::string &err) {
@@ -194,7 +360,12 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
         }
     if (!reg) { err = "pattern has no regular vertex"; return PG_EINVAL; }
     if (!connected_by_edges(p, reg)) { err = "regular pattern vertices must be connected by edges"; return PG_EINVAL; }
-    if (reg != (1u << k) - 1) { err = "anti-vertices are not supported by this build"; return PG_EUNSUPPORTED; }
+    for (int u = 0; u < k; ++u)
+        if (p.anti_vertex[u]) {
+            if (p.label[u] >= 0) { err = "anti-vertices carry no label"; return PG_EINVAL; }
+            for (int w = 0; w < k; ++w)
+                if (p.anti_vertex[w] && p.rel[u][w]) { err = "anti-vertices may not be related to each other"; return PG_EINVAL; }
+        }
 
     // Theorem of Section 3.1.3: vertex-induced == anti-edges on all non-adjacent pairs.
     if (vertex_induced)
@@ -282,159 +453,60 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
     out.core_mask = best;
     const uint32_t noncore = reg & ~best;
 
-    // non-core groups; the largest is counted, the rest enumerated
-    std::vector<std::vector<int>> groups = noncore_groups(p, cl, noncore);
+    // anti-vertices: the regular vertices each check reads (Section 4.3,
+    // "Checking Anti-Vertices"): its neighbours, and their pattern neighbours
+    // whose images are excluded as witnesses
+    std::vector<AntiSpec> avs;
+    uint32_t involved = 0;
+    for (int a = 0; a < k; ++a) {
+        if (!p.anti_vertex[a]) continue;
+        AntiSpec sp{0, 0};
+        for (int u = 0; u < k; ++u)
+            if (p.rel[a][u] == 2 && (reg >> u & 1)) sp.nbrs |= 1u << u;
+        sp.reads = sp.nbrs;
+        for (int u = 0; u < k; ++u)
+            if (sp.nbrs >> u & 1)
+                for (int w = 0; w < k; ++w)
+                    if (p.rel[u][w] == 1 && (reg >> w & 1)) sp.reads |= 1u << w;
+        involved |= sp.reads;
+        avs.push_back(sp);
+    }
+    out.anti_vertices = !avs.empty();
+
+    // non-core groups; the largest is counted (an uninvolved one on ties),
+    // the rest enumerated.  Vertices an anti-vertex check reads are single.
+    std::vector<std::vector<int>> groups = noncore_groups(p, cl, noncore, involved);
     int counted = -1;
-    for (int i = 0; i < (int)groups.size(); ++i)
-        if (counted < 0 || groups[i].size() > groups[counted].size()) counted = i;
+    for (int i = 0; i < (int)groups.size(); ++i) {
+        if (counted < 0 || groups[i].size() > groups[counted].size()) { counted = i; continue; }
+        if (groups[i].size() == groups[counted].size() && (involved >> groups[counted][0] & 1) &&
+            !(involved >> groups[i][0] & 1))
+            counted = i;
+    }
     out.counted_group = counted < 0 ? 1 : (int)groups[counted].size();
     // joint partner: another single-vertex group (fewest regular neighbours,
-    // i.e. the set most expensive to enumerate)
+    // i.e. the set most expensive to enumerate); neither may be read by an
+    // anti-vertex check
     int partner = -1;
-    if (counted >= 0 && groups[counted].size() == 1) {
+    if (counted >= 0 && groups[counted].size() == 1 && !(involved >> groups[counted][0] & 1)) {
         auto nbrs = [&](int u) {
             int c = 0;
             for (int w = 0; w < k; ++w) c += p.rel[u][w] == 1;
             return c;
         };
         for (int i = 0; i < (int)groups.size(); ++i)
-            if (i != counted && groups[i].size() == 1 &&
+            if (i != counted && groups[i].size() == 1 && !(involved >> groups[i][0] & 1) &&
                 (partner < 0 || nbrs(groups[i][0]) < nbrs(groups[partner][0])))
                 partner = i;
     }
-
-    // ---- computeMatchingOrders (Section 4.1) ----------------------------
-    std::vector<int> core;
+    int rc = lower_orders(p, cl, best, groups, counted, partner, avs, out.orders, err);
+    if (rc) return rc;
+    // listing program: every non-core vertex enumerated on its own level
+    std::vector<std::vector<int>> singles;
     for (int u = 0; u < k; ++u)
-        if (best >> u & 1) core.push_back(u);
-    const int c = (int)core.size();
-    std::vector<int> seq = core;
-    std::sort(seq.begin(), seq.end());
-    do {
-        int pos[PGP_MAXK];
-        for (int i = 0; i < k; ++i) pos[i] = -1;
-        for (int i = 0; i < c; ++i) pos[seq[i]] = i;
-        bool ok = true;
-        for (int a : core)
-            for (int b : core)
-                if (cl.less[a][b] && pos[a] > pos[b]) ok = false;
-        if (!ok) continue;
-        if (out.orders.size() >= PGP_MAX_ORDERS) { err = "too many matching orders"; return PG_EINVAL; }
-
-        // Exploration order: start from the highest sequence position (the
-        // task's start vertex, Section 5.2 high-to-low), then repeatedly the
-        // highest-position core vertex adjacent to one already bound.
-        int lvl_of[PGP_MAXK];
-        for (int i = 0; i < k; ++i) lvl_of[i] = -1;
-        std::vector<int> bound_order;
-        bound_order.push_back(seq[c - 1]);
-        lvl_of[seq[c - 1]] = 0;
-        while ((int)bound_order.size() < c) {
-            int pick = -1;
-            for (int i = c - 1; i >= 0 && pick < 0; --i) {
-                int u = seq[i];
-                if (lvl_of[u] >= 0) continue;
-                for (int x : bound_order)
-                    if (p.rel[u][x] == 1) { pick = u; break; }
-            }
-            lvl_of[pick] = (int)bound_order.size();
-            bound_order.push_back(pick);
-        }
-        // non-core: enumerated groups first (chain order), counted group last;
-        // a single counted vertex is paired with another single non-core
-        // vertex placed right before it (joint counting of the last two)
-        std::vector<int> nc_order;
-        for (int i = 0; i < (int)groups.size(); ++i)
-            if (i != counted && i != partner)
-                for (int u : groups[i]) nc_order.push_back(u);
-        if (partner >= 0) nc_order.push_back(groups[partner][0]);
-        for (int u : nc_order) {
-            lvl_of[u] = (int)bound_order.size();
-            bound_order.push_back(u);
-        }
-        int counted_first = -1;
-        if (counted >= 0) {
-            counted_first = groups[counted][0];
-            lvl_of[counted_first] = (int)bound_order.size();
-            bound_order.push_back(counted_first);
-        }
-
-        PgOrder ord;
-        std::memset(&ord, 0, sizeof(ord));
-        ord.n_levels = (int)bound_order.size();
-        ord.n_core = c;
-        for (int l = 0; l < ord.n_levels; ++l) {
-            const int u = bound_order[l];
-            PgLevel &L = ord.lv[l];
-            L.pattern_vertex = (int8_t)u;
-            L.is_core = (int8_t)((best >> u) & 1);
-            L.label = p.label[u];
-            L.group = (int8_t)((u == counted_first) ? out.counted_group : 1);
-            L.joint = (int8_t)(u == counted_first && partner >= 0);
-            if (l == 0) continue;
-            const bool core_level = L.is_core;
-            int lo_core = -1, hi_core = -1; // tightest core bounds (by position)
-            for (int j = 0; j < l; ++j) {
-                const int x = bound_order[j];
-                if (p.rel[u][x] == 1) L.int_src[L.n_int++] = (int8_t)j;
-                if (p.rel[u][x] == 2) L.diff_src[L.n_diff++] = (int8_t)j;
-                const bool x_core = (best >> x) & 1;
-                bool below, above; // m(x) < m(u) / m(x) > m(u) required
-                if (core_level && x_core) {
-                    below = pos[x] < pos[u];
-                    above = pos[x] > pos[u];
-                } else {
-                    below = cl.less[x][u];
-                    above = cl.less[u][x];
-                }
-                if (x_core && (below || above)) {
-                    if (below && (lo_core < 0 || pos[x] > pos[bound_order[lo_core]])) lo_core = j;
-                    if (above && (hi_core < 0 || pos[x] < pos[bound_order[hi_core]])) hi_core = j;
-                } else {
-                    if (below) L.lo_src[L.n_lo++] = (int8_t)j;
-                    if (above) L.hi_src[L.n_hi++] = (int8_t)j;
-                }
-            }
-            if (lo_core >= 0) L.lo_src[L.n_lo++] = (int8_t)lo_core;
-            if (hi_core >= 0) L.hi_src[L.n_hi++] = (int8_t)hi_core;
-            // candidates adjacent to a bound vertex x and ranked below it lie
-            // in N+(x): at most max out-degree of them
-            {
-                bool bounded = false;
-                for (int i = 0; i < L.n_int && !bounded; ++i) {
-                    const int x = bound_order[L.int_src[i]];
-                    const bool x_core = (best >> x) & 1;
-                    if (cl.less[u][x]) bounded = true;
-                    if (x_core && hi_core >= 0 && pos[bound_order[hi_core]] <= pos[x]) bounded = true;
-                    if (core_level && x_core && pos[x] > pos[u]) bounded = true;
-                }
-                L.out_bounded = (int8_t)bounded;
-            }
-            // injectivity: exclude every earlier image not already ruled out
-            for (int j = 0; j < l; ++j) {
-                const int x = bound_order[j];
-                const bool x_core = (best >> x) & 1;
-                bool out_of_set = false;
-                for (int i = 0; i < L.n_int && !out_of_set; ++i) {
-                    int y = bound_order[L.int_src[i]];
-                    if (y == x || p.rel[x][y] == 2) out_of_set = true; // m(x) not in adj(m(y))
-                }
-                for (int i = 0; i < L.n_diff && !out_of_set; ++i)
-                    if (p.rel[x][bound_order[L.diff_src[i]]] == 1) out_of_set = true;
-                for (int i = 0; i < L.n_lo && !out_of_set; ++i) {
-                    int y = bound_order[L.lo_src[i]];
-                    if (y == x || (x_core && ((best >> y) & 1) && pos[x] <= pos[y])) out_of_set = true;
-                }
-                for (int i = 0; i < L.n_hi && !out_of_set; ++i) {
-                    int y = bound_order[L.hi_src[i]];
-                    if (y == x || (x_core && ((best >> y) & 1) && pos[x] >= pos[y])) out_of_set = true;
-                }
-                if (!out_of_set && L.label >= 0 && p.label[x] >= 0 && p.label[x] != L.label) out_of_set = true;
-                if (!out_of_set) L.excl_src[L.n_excl++] = (int8_t)j;
-            }
-        }
-        out.orders.push_back(ord);
-    } while (std::next_permutation(seq.begin(), seq.end()));
+        if (noncore >> u & 1) singles.push_back({u});
+    rc = lower_orders(p, cl, best, singles, -1, -1, avs, out.list_orders, err);
+    if (rc) return rc;
 
     // k-clique: complete on all vertices, unlabeled (vertex-induced or not)
     bool clique = !out.labeled;

@@ -15,6 +15,15 @@
 //
 // where m[j] is the data vertex bound at level j.
 //
+// An anti-vertex check (Section 3.1.2, Section 4.3 "Checking Anti-Vertices")
+// runs at the level that binds the last of the vertices it reads: a
+// candidate x of that level survives iff
+//
+//   ( /\ adj(m[int_src]) ) \ { m[excl_src] }  is empty,
+//
+// int_src being the anti-vertex's neighbours and excl_src the pattern
+// neighbours of those neighbours (their images are not witnesses).
+//
 // A last level marked `joint` belongs to a single non-core vertex y whose
 // only ties to the previous level's single non-core vertex x are the
 // partial order and injectivity (non-core vertices share no edge or
@@ -37,6 +46,7 @@ struct PgLevel {
     int8_t out_bounded;    // candidates lie in N+(start): at most max out-degree
     int8_t joint;          // last level only: counted jointly with the previous
                            // level (two single non-core vertices, see plan.cpp)
+    int8_t n_anti;         // anti-vertex checks attached to this level
     int8_t int_src[PGP_MAXK];
     int8_t diff_src[PGP_MAXK];
     int8_t lo_src[PGP_MAXK];
@@ -45,10 +55,20 @@ struct PgLevel {
     int32_t label; // -1: any
 };
 
+struct PgAntiCheck {
+    int8_t level; // checked when this level binds its candidate
+    int8_t n_int, n_excl, pad;
+    int8_t int_src[PGP_MAXK];
+    int8_t excl_src[PGP_MAXK];
+};
+
 struct PgOrder {
     int32_t n_levels;
     int32_t n_core;
     PgLevel lv[PGP_MAXK];
+    int32_t n_checks;
+    int32_t pad;
+    PgAntiCheck chk[PGP_MAXK];
 };
 
 #ifdef __cplusplus
@@ -71,7 +91,9 @@ struct PgPlanHost {
     int counted_group = 1;
     bool is_clique = false;               // k-clique (edge- or vertex-induced), unlabeled
     bool labeled = false;
-    std::vector<PgOrder> orders;
+    bool anti_vertices = false;           // pattern has anti-vertices (checks in the orders)
+    std::vector<PgOrder> orders;          // counting program: last level counted
+    std::vector<PgOrder> list_orders;     // listing program: every vertex its own level
     double compile_ms = 0.0;
 };
 

@@ -109,8 +109,43 @@ void emit(pg_server *S, const ServerQuery &q, int status, const uint64_t *cnt, d
     S->results.push_back(r);
 }
 
+// An anti-vertex query runs alone on the plan interpreter (batches refuse
+// anti-vertex plans); returns 1 if launched.
+int launch_alone(pg_server *S, Slot &s, const ServerQuery &q) {
+    int rc = pg_plan_upload(q.plan);
+    if (rc == PG_OK && pg_generic_scratch_bytes(&s.view, q.plan, true) > s.ex.scratch_bytes) rc = PG_ENOMEM;
+    if (rc == PG_OK && cudaMemsetAsync(s.d_counts, 0, 2 * sizeof(uint64_t), s.stream) != cudaSuccess) rc = PG_EDEVICE;
+    if (rc == PG_OK) {
+        s.t_start = S->now();
+        rc = pg_launch_generic(&s.view, q.plan, (unsigned long long *)s.d_counts, 0, true, s.stream);
+    }
+    if (rc != PG_OK) {
+        emit(S, q, rc, nullptr, S->now(), S->now(), 1);
+        S->outstanding--;
+        return 0;
+    }
+    cudaMemcpyAsync(s.h_counts, s.d_counts, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.stream);
+    cudaEventRecord(s.done, s.stream);
+    s.batch = nullptr;
+    s.qs = {q};
+    s.busy = true;
+    S->batches++;
+    S->launched_queries += 1;
+    return 1;
+}
+
 // Try to launch up to `take` queries on slot s; returns queries launched.
 int launch_batch(pg_server *S, Slot &s, std::vector<ServerQuery> qs) {
+    for (size_t i = 0; i < qs.size(); ++i) {
+        if (!qs[i].plan->h.anti_vertices) continue;
+        // the first anti-vertex query goes alone; the rest return to the queue front
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            for (size_t j = qs.size(); j-- > 0;)
+                if (j != i) S->pending.push_front(qs[j]);
+        }
+        return launch_alone(S, s, qs[i]);
+    }
     while (!qs.empty()) {
         std::vector<pg_plan *> plans;
         for (auto &q : qs) plans.push_back(q.plan);

@@ -37,12 +37,13 @@ def lib():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _lib.pe_count.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
-                                  ctypes.POINTER(_Desc), ctypes.c_void_p, ctypes.c_void_p]
+                                  ctypes.POINTER(_Desc), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
     return _lib
 
 
-def count(g, p: dict):
-    """(count, info) of pattern p on synthgraph graph g by interpreting the plan."""
+def count(g, p: dict, listing: bool = False):
+    """(count, info) of pattern p on synthgraph graph g by interpreting the
+    plan's counting program (or, with listing=True, its listing program)."""
     off = np.ascontiguousarray(g.offsets, dtype=np.int64)
     adj = np.ascontiguousarray(g.adj, dtype=np.int32)
     lab = None if g.labels is None else np.ascontiguousarray(g.labels, dtype=np.int32)
@@ -57,7 +58,7 @@ def count(g, p: dict):
     info = np.zeros(4, dtype=np.int32)
     rc = lib().pe_count(off.ctypes.data, g.n, adj.ctypes.data if adj.size else None,
                         None if lab is None else lab.ctypes.data, ctypes.byref(d),
-                        out.ctypes.data, info.ctypes.data)
+                        1 if listing else 0, out.ctypes.data, info.ctypes.data)
     if rc:
         raise RuntimeError(f"plan compile error {rc}")
     return (int(out[1]) << 64) | int(out[0]), info

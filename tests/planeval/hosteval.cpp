@@ -78,9 +78,37 @@ unsigned __int128 choose(uint64_t s, int k) {
     return r;
 }
 
+// Anti-vertex check: no data vertex lies in every adj(m[int_src]) other than
+// the images m[excl_src].
+bool anti_ok(const RankedGraph &g, const PgAntiCheck &C, const int *m) {
+    const int a = m[C.int_src[0]];
+    for (int64_t e = g.off[a]; e < g.off[a + 1]; ++e) {
+        const int x = g.adj[e];
+        bool in = true;
+        for (int i = 1; i < C.n_int && in; ++i) in = has(g, m[C.int_src[i]], x);
+        for (int i = 0; i < C.n_excl && in; ++i) in = x != m[C.excl_src[i]];
+        if (in) return false;
+    }
+    return true;
+}
+
+bool checks_ok(const RankedGraph &g, const PgOrder &o, int l, const int *m) {
+    for (int c = 0; c < o.n_checks; ++c)
+        if (o.chk[c].level == l && !anti_ok(g, o.chk[c], m)) return false;
+    return true;
+}
+
 unsigned __int128 walk(const RankedGraph &g, const PgOrder &o, int l, int *m) {
     const PgLevel &L = o.lv[l];
     std::vector<int> s = level_set(g, L, m);
+    if (L.n_anti) {
+        std::vector<int> kept;
+        for (int x : s) {
+            m[l] = x;
+            if (checks_ok(g, o, l, m)) kept.push_back(x);
+        }
+        s.swap(kept);
+    }
     if (l == o.n_levels - 1) return choose(s.size(), L.group);
     unsigned __int128 t = 0;
     for (int x : s) {
@@ -92,8 +120,10 @@ unsigned __int128 walk(const RankedGraph &g, const PgOrder &o, int l, int *m) {
 
 }  // namespace
 
+// Counts p on the graph by walking the compiled counting program (use_list =
+// 0) or the listing program (use_list = 1, every vertex enumerated).
 extern "C" int pe_count(const int64_t *off, int64_t n, const int32_t *adj, const int32_t *labels,
-                        const pg_pattern_desc *d, uint64_t *out2, int32_t *info) {
+                        const pg_pattern_desc *d, int32_t use_list, uint64_t *out2, int32_t *info) {
     PgPattern p;
     p.k = d->k;
     for (int i = 0; i < d->n_edges; ++i) {
@@ -115,11 +145,12 @@ extern "C" int pe_count(const int64_t *off, int64_t n, const int32_t *adj, const
     RankedGraph g = rank_graph(off, n, adj, labels);
     unsigned __int128 total = 0;
     int m[PGP_MAXK];
-    for (const PgOrder &o : h.orders) {
+    for (const PgOrder &o : use_list ? h.list_orders : h.orders) {
         for (int v = 0; v < g.n; ++v) {
             if (o.lv[0].label >= 0 && g.label[v] != o.lv[0].label) continue;
-            if (o.n_levels == 1) { total += 1; continue; }
             m[0] = v;
+            if (!checks_ok(g, o, 0, m)) continue;
+            if (o.n_levels == 1) { total += 1; continue; }
             total += walk(g, o, 1, m);
         }
     }

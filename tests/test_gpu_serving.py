@@ -55,6 +55,30 @@ def test_mix_equals_alone(pg, graph):
         assert r["t_submit"] <= r["t_start"] <= r["t_done"]
 
 
+def test_anti_vertex_queries_in_mix(pg, graph):
+    """Anti-vertex queries (run alone on the plan interpreter) interleaved
+    with batched ones: every count equals the oracle's / its count alone."""
+    g, G = graph
+    av = [sg.pattern(4, sg.clique_edges(3), anti_edges=[(3, 0), (3, 1), (3, 2)], anti_vertex=[0, 0, 0, 1]),
+          sg.pattern(3, [(0, 1)], anti_edges=[(2, 0), (2, 1)], anti_vertex=[0, 0, 1])]
+    qs = sg.serving_queries(30, seed=11, labeled_fraction=0.2)
+    mix = []
+    for i, q in enumerate(qs):
+        mix.append(q)
+        if i % 5 == 0:
+            mix.append(av[(i // 5) % 2])
+    got, _ = _serve(pg, G, mix, n_streams=4, max_batch=16)
+    assert all(r["status"] == 0 for r in got)
+    want = {0: oracle.count(g, av[0], threads=8), 1: oracle.count(g, av[1], threads=8)}
+    alone = _alone(pg, G, [q for q in mix if not q.get("anti_vertex")])
+    it = iter(alone)
+    for q, r in zip(mix, got):
+        if q.get("anti_vertex"):
+            assert r["count"] == want[av.index(q)]
+        else:
+            assert r["count"] == next(it)
+
+
 def test_serial_mode_equals_alone(pg, graph):
     g, G = graph
     qs = sg.serving_queries(20, seed=8, labeled_fraction=0.3)

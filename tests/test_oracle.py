@@ -233,6 +233,65 @@ def test_anti_vertex_p_e():
         assert oracle.count(g, p) == expect
 
 
+# ------------------------------------------------------------- listing -----
+
+LISTING_PATTERNS = [
+    sg.pattern(2, [(0, 1)]),
+    sg.pattern(3, sg.clique_edges(3)),
+    sg.pattern(3, sg.chain_edges(3)),
+    sg.pattern(4, sg.cycle_edges(4)),
+    sg.pattern(4, sg.TAILED_TRIANGLE, anti_edges=[(3, 1)]),
+    sg.pattern(4, sg.star_edges(4), vertex_induced=True),
+    sg.pattern(4, sg.clique_edges(3), anti_edges=[(3, 0), (3, 2)], anti_vertex=[0, 0, 0, 1]),
+]
+
+
+def test_automorphism_perms_agree_with_c():
+    """The Python permutation list and the C |Aut| are written separately."""
+    for p in LISTING_PATTERNS + [sg.pattern(5, sg.star_edges(5)), sg.pattern(5, sg.clique_edges(5)),
+                                 sg.pattern(3, sg.chain_edges(3), labels=[1, -1, 1])]:
+        perms = oracle.automorphism_perms(p)
+        av = p.get("anti_vertex") or [0] * p["k"]
+        restricted = {tuple(s[u] if not av[u] else -1 for u in range(p["k"])) for s in perms.tolist()}
+        assert len(restricted) == oracle.automorphisms(p), p
+
+
+def test_match_keys_one_per_match():
+    """|distinct matches| = maps / |Aut| for every listed pattern."""
+    for g in small_graphs()[:4]:
+        for p in LISTING_PATTERNS:
+            keys = oracle.match_keys(g, p)
+            assert keys.shape[0] == oracle.count(g, p), p
+            assert len({tuple(r) for r in keys.tolist()}) == keys.shape[0]
+
+
+def test_match_keys_brute_force_sets():
+    """Edges, triangles, p_e and a labeled edge listed by plain loops."""
+    for g in small_graphs()[:4]:
+        G = to_nx(g)
+        edges = {(min(a, b), max(a, b)) for a, b in G.edges()}
+        got = {tuple(r) for r in oracle.match_keys(g, LISTING_PATTERNS[0]).tolist()}
+        assert got == edges
+        tris = {t for t in itertools.combinations(range(g.n), 3)
+                if G.has_edge(t[0], t[1]) and G.has_edge(t[0], t[2]) and G.has_edge(t[1], t[2])}
+        got = {tuple(r) for r in oracle.match_keys(g, LISTING_PATTERNS[1]).tolist()}
+        assert got == tris
+        # p_e: the class of (a, b, c) under the swap of u1, u3 is keyed (min(a,c), b, max(a,c))
+        pe = set()
+        for a, c in edges:
+            common = set(G[a]) & set(G[c])
+            if len(common) == 1:
+                pe.add((a, common.pop(), c, -1))
+        got = {tuple(r) for r in oracle.match_keys(g, LISTING_PATTERNS[6]).tolist()}
+        assert got == pe
+    g = small_graphs()[0]
+    g.labels = sg.uniform_labels(g.n, 3, 77)
+    G = to_nx(g)
+    p = sg.pattern(2, [(0, 1)], labels=[1, -1])  # no symmetry: one match per (a, b)
+    want = {(a, b) for a in range(g.n) for b in G[a] if g.labels[a] == 1}
+    assert {tuple(r) for r in oracle.match_keys(g, p).tolist()} == want
+
+
 # ------------------------------------------------------------- cliques -----
 
 def test_kcliques_complete_graph():

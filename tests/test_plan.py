@@ -68,6 +68,24 @@ ALL_PATTERNS = ([sg.pattern(k, sg.clique_edges(k)) for k in range(1, 6)]
                    sg.pattern(5, [(0, 1), (1, 2), (2, 0), (2, 3), (3, 4)], vertex_induced=True),
                    sg.pattern(6, sg.star_edges(4) + [(3, 4), (3, 5)])])
 
+# Anti-vertex patterns (Section 3.1.2): triangles in no 4-clique, the paper's
+# p_e (friend pairs with one mutual friend), edges with no common neighbour,
+# wedges whose ends share no other neighbour, a star leaf of degree one, a
+# 4-cycle with no vertex adjacent to all four, two anti-vertices on a path,
+# a vertex-induced wedge with one, an isolated vertex.
+ANTI_VERTEX_PATTERNS = [
+    sg.pattern(4, sg.clique_edges(3), anti_edges=[(3, 0), (3, 1), (3, 2)], anti_vertex=[0, 0, 0, 1]),
+    sg.pattern(4, sg.clique_edges(3), anti_edges=[(3, 0), (3, 2)], anti_vertex=[0, 0, 0, 1]),
+    sg.pattern(3, [(0, 1)], anti_edges=[(2, 0), (2, 1)], anti_vertex=[0, 0, 1]),
+    sg.pattern(4, [(0, 1), (1, 2)], anti_edges=[(3, 0), (3, 2)], anti_vertex=[0, 0, 0, 1]),
+    sg.pattern(5, sg.star_edges(4), anti_edges=[(4, 1)], anti_vertex=[0, 0, 0, 0, 1]),
+    sg.pattern(5, sg.cycle_edges(4), anti_edges=[(4, 0), (4, 1), (4, 2), (4, 3)], anti_vertex=[0, 0, 0, 0, 1]),
+    sg.pattern(5, sg.chain_edges(3), anti_edges=[(3, 0), (3, 1), (4, 1), (4, 2)], anti_vertex=[0, 0, 0, 1, 1]),
+    sg.pattern(4, [(0, 1), (1, 2)], anti_edges=[(3, 0), (3, 2)], anti_vertex=[0, 0, 0, 1], vertex_induced=True),
+    sg.pattern(2, [], anti_edges=[(0, 1)], anti_vertex=[0, 1]),
+    sg.pattern(5, sg.TAILED_TRIANGLE, anti_edges=[(4, 3)], anti_vertex=[0, 0, 0, 0, 1]),
+]
+
 
 def test_compile_latency_under_half_ms():
     """Section 4.1: plans are computed from the pattern alone, typically < 0.5 ms."""
@@ -100,6 +118,33 @@ def test_plan_interpretation_matches_oracle(gi):
         assert got == oracle.count(g, p), (p, gi)
 
 
+@pytest.mark.parametrize("gi", range(5))
+def test_listing_program_matches_oracle(gi):
+    """The listing program (every vertex on its own level) finds each match once."""
+    g = _graphs()[gi]
+    for p in ALL_PATTERNS + ANTI_VERTEX_PATTERNS:
+        got, _ = planeval.count(g, p, listing=True)
+        assert got == oracle.count(g, p), (p, gi)
+
+
+@pytest.mark.parametrize("gi", range(5))
+def test_anti_vertex_plans_match_oracle(gi):
+    g = _graphs()[gi]
+    for p in ANTI_VERTEX_PATTERNS:
+        got, _ = planeval.count(g, p)
+        assert got == oracle.count(g, p), (p, gi)
+
+
+def test_anti_vertex_symmetry_breaking_paper_example():
+    """Section 4.3: in p_e the anti-vertex splits the triangle's symmetry; only
+    the two vertices it is anti-adjacent to stay interchangeable."""
+    pg = _pg()
+    info = pg.Plan.from_dict(ANTI_VERTEX_PATTERNS[1]).info()
+    assert info.automorphisms == 2
+    po = sorted((info.po[2 * i], info.po[2 * i + 1]) for i in range(info.n_po))
+    assert po == [(0, 2)]
+
+
 def test_labeled_plans_match_oracle():
     g = _graphs()[3]
     rng = np.random.default_rng(3)
@@ -124,3 +169,7 @@ def test_invalid_patterns_rejected():
         pg.Plan(3, [(0, 1), (1, 2)], anti_edges=[(0, 1)])
     with pytest.raises(pg.PgError):
         pg.Plan(2, [(0, 0)])
+    with pytest.raises(pg.PgError):  # anti-vertex with a true edge
+        pg.Plan(3, [(0, 1), (1, 2)], anti_vertex=[0, 0, 1])
+    with pytest.raises(pg.PgError):  # labeled anti-vertex
+        pg.Plan(3, [(0, 1)], anti_edges=[(2, 0)], anti_vertex=[0, 0, 1], labels=[-1, -1, 2])
