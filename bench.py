@@ -219,6 +219,10 @@ def run_ours(args):
     def step():
         pg.count_async(G, plans, counts, kernel=args.kernel, stream=stream)
 
+    # launch parameters chosen by measurement on this graph (the autotuned
+    # persistent variant); the search is not part of the timed steps
+    tune = pg.autotune(G, plans, stream=stream) if args.autotune and args.kernel == 0 else None
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -331,6 +335,7 @@ def run_ours(args):
     cpu_rate, _, cpu_secs = cpu_oracle_rate(g, 1)
     cfg = workload_config(g)
     cfg.update({"kernel": {0: "auto (persistent bitmap clique kernel)", 3: "clique"}.get(args.kernel, str(args.kernel)),
+                "autotune": tune,
                 "l2": "256 MiB buffer written between timed steps (not timed)",
                 "counts": {p.name: c for p, c in zip(plans, got)}})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -413,7 +418,16 @@ def run_motif4(args):
         pg.count_batch(G, b, out)
         fused = _events_ms(lambda: pg.count_batch(G, b, out), stream)
         counts = pg.decode_counts(out)
-        row = {"n": g.n, "m": g.m, "fused_batched_ms": fused,
+        tune = None
+        if args.autotune:
+            tune = pg.autotune(G, plans, sample_stride=8 if sd > 0 else 64)
+            tuned = _events_ms(lambda: pg.count_batch(G, b, out), stream)
+            if pg.decode_counts(out) != counts:
+                raise SystemExit("counts changed under tuned launch parameters")
+            tune["full_launch_ms_default"] = fused
+            tune["full_launch_ms_tuned"] = tuned
+            fused = tuned  # the parameters now in effect
+        row = {"n": g.n, "m": g.m, "fused_batched_ms": fused, "autotune": tune,
                "counts": dict(zip([p["name"] for p in sg.motif4_patterns()], counts)),
                "matches_per_s": sum(counts) / (fused / 1e3)}
         if sd > 0:
@@ -544,6 +558,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kernel", type=int, default=0, help="PG_KERNEL_* (0 = auto)")
     ap.add_argument("--no-compare-plain", dest="compare_plain", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch parameters")
     ap.add_argument("--workload", choices=["cliques", "serving", "motif3", "motif4", "fsm"], default="cliques")
     ap.add_argument("--motif4-small", action="store_true", help="skip the full-size motif run")
     ap.add_argument("--serve-scale", type=int, default=16, help="R-MAT scale of the serving graph")

@@ -297,6 +297,70 @@ int pg_count_batch(pg_graph *g, const pg_batch *b, uint64_t *counts_dev, void *s
 void pg_free_batch(pg_batch *b);
 
 /*
+ * Launch parameters of the persistent kernels, held per graph.  The paper
+ * fixes its runtime's task granularity by hand (Section 5.5); this library
+ * exposes the equivalent knobs and tunes them on the graph at hand.
+ *   clique_chunk          start vertices a warp takes per work-queue grab in
+ *                         the k-clique kernel (1..64; default 4).
+ *   clique_blocks_per_sm  CTAs per SM of the k-clique kernel (0 = as many as
+ *                         fit; larger values are clamped to that).
+ *   clique_heavy_min      start vertices with out-degree above this get a
+ *                         whole CTA, the rest one warp (8..64; default 64).
+ *   batched_warps         warps per CTA of the batched kernel (2, 4 or 8;
+ *                         default 4).
+ *   batched_chunk         start vertices per work-queue grab (1..64; default 1).
+ *   batched_blocks_per_sm CTAs per SM (0 = as many as fit).
+ *   hub_min_degree        vertices of at least this degree get a membership
+ *   hub_max               bitmap row, at most hub_max of them (highest degree
+ *                         first; defaults 1024 and 512; hub_max 0 = none).
+ */
+typedef struct {
+    int32_t clique_chunk;
+    int32_t clique_blocks_per_sm;
+    int32_t clique_heavy_min;
+    int32_t batched_warps;
+    int32_t batched_chunk;
+    int32_t batched_blocks_per_sm;
+    int32_t hub_min_degree;
+    int32_t hub_max;
+} pg_tuning;
+
+/* Outcome of pg_autotune. */
+typedef struct {
+    pg_tuning chosen;     /* now in effect on the graph */
+    double default_ms;    /* timed launch with the parameters in effect before */
+    double tuned_ms;      /* timed launch with `chosen` (same sample) */
+    double wall_ms;       /* host time of the whole search */
+    int32_t trials;       /* configurations timed */
+    int32_t kernel;       /* PG_KERNEL_* family tuned (CLIQUE or BATCHED) */
+    int32_t sample_stride;
+    int32_t pad;
+} pg_tune_report;
+
+/* pg_get_tuning / pg_set_tuning - read or replace a graph's launch
+ * parameters.  Setting rebuilds the hub bitmaps or the heavy-vertex list when
+ * their knobs change (synchronous).  Counts never depend on these values.
+ * Errors: PG_EINVAL (value out of range), PG_ENOMEM, PG_EDEVICE. */
+int pg_get_tuning(const pg_graph *g, pg_tuning *out);
+int pg_set_tuning(pg_graph *g, const pg_tuning *t, void *stream);
+
+/*
+ * pg_autotune - choose the launch parameters for counting `plans` on `g` by
+ * measurement, and keep them on the graph.  The kernel family is the one
+ * PG_KERNEL_AUTO picks for these plans (k-clique or batched; other families
+ * have nothing to tune and return PG_EUNSUPPORTED).  Coordinate descent over
+ * the family's knobs: each value is timed with CUDA events on `stream` (one
+ * untimed launch, then the best of two), the best kept before the next knob.
+ * sample_stride >= 1 times only every sample_stride-th start vertex (in rank
+ * order), so a workload whose full launch takes seconds is tuned in
+ * proportionally less time; 1 times the full launch.  Synchronous; report
+ * (host) may be NULL.  Errors: PG_EINVAL, PG_EUNSUPPORTED, PG_ENOMEM,
+ * PG_EDEVICE.
+ */
+int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, int32_t sample_stride,
+                pg_tune_report *report, void *stream);
+
+/*
  * pg_fsm - labeled frequent subgraph mining with MNI support (Section 2.1
  * FSM and minimum node image support; Section 3.2 "FSM" program with label
  * discovery; Section 5.5 domains).  Finds every connected labeled pattern

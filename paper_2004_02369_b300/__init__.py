@@ -85,6 +85,9 @@ _lib.pg_free_batch.argtypes = [_vp]
 _lib.pg_free_batch.restype = None
 _lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
+_lib.pg_get_tuning.argtypes = [_vp, _vp]
+_lib.pg_set_tuning.argtypes = [_vp, _vp, _vp]
+_lib.pg_autotune.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
 _lib.pg_last_error.restype = ctypes.c_char_p
 
 
@@ -338,6 +341,51 @@ def count_cliques_noalloc(graph: Graph, kmin: int, kmax: int, out, stream=None):
     if out.numel() < 2 * (kmax - kmin + 1) or not out.is_cuda:
         raise ValueError("out must be a CUDA tensor with 2*(kmax-kmin+1) 64-bit elements")
     _check(_lib.pg_count_cliques_noalloc(graph.handle, kmin, kmax, out.data_ptr(), _stream_ptr(stream)))
+
+
+class Tuning(ctypes.Structure):
+    """Launch parameters of the persistent kernels (pg_tuning in pg.h)."""
+    _fields_ = [("clique_chunk", ctypes.c_int32), ("clique_blocks_per_sm", ctypes.c_int32),
+                ("clique_heavy_min", ctypes.c_int32), ("batched_warps", ctypes.c_int32),
+                ("batched_chunk", ctypes.c_int32), ("batched_blocks_per_sm", ctypes.c_int32),
+                ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("chosen", Tuning), ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
+                ("wall_ms", ctypes.c_double), ("trials", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("sample_stride", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def get_tuning(graph: Graph) -> dict:
+    t = Tuning()
+    _check(_lib.pg_get_tuning(graph.handle, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def set_tuning(graph: Graph, stream=None, **values):
+    """Change some launch parameters of ``graph`` (others keep their value)."""
+    t = Tuning()
+    _check(_lib.pg_get_tuning(graph.handle, ctypes.byref(t)))
+    for k, v in values.items():
+        if k not in dict(Tuning._fields_):
+            raise KeyError(k)
+        setattr(t, k, int(v))
+    _check(_lib.pg_set_tuning(graph.handle, ctypes.byref(t), _stream_ptr(stream)))
+
+
+def autotune(graph: Graph, plans, sample_stride: int = 1, stream=None) -> dict:
+    """Measure and keep the best launch parameters for counting ``plans``."""
+    plans = list(plans)
+    r = TuneReport()
+    _check(_lib.pg_autotune(graph.handle, _plan_array(plans), len(plans), sample_stride, ctypes.byref(r),
+                            _stream_ptr(stream)))
+    return {"chosen": r.chosen.as_dict(), "default_ms": r.default_ms, "tuned_ms": r.tuned_ms,
+            "wall_ms": r.wall_ms, "trials": int(r.trials), "kernel": int(r.kernel),
+            "sample_stride": int(r.sample_stride)}
 
 
 class FsmPattern(ctypes.Structure):

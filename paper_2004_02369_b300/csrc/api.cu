@@ -97,7 +97,7 @@ extern "C" int pg_graph_get_info(const pg_graph *g, pg_graph_info *out) {
     out->m = g->m;
     out->max_degree = g->max_deg;
     out->max_out_degree = g->max_out;
-    out->device_bytes = g->bytes_device + (int64_t)g->ex->scratch_bytes;
+    out->device_bytes = pg_graph_bytes(g) + (int64_t)g->ex->scratch_bytes;
     out->labeled = g->labeled;
     out->n_labels = g->n_labels;
     return PG_OK;

@@ -43,8 +43,6 @@ struct PgTrieTerm {
 
 namespace {
 
-constexpr int kWarps = 4;
-constexpr int kBlock = kWarps * 32;
 constexpr int kMaxSlots = PG_MAX_QUEUES;
 
 struct BatchArgs {
@@ -58,6 +56,9 @@ struct BatchArgs {
     long long lvl_off[PGP_MAXK];
     unsigned long long *queue;
     int n;
+    int chunk;                  // start vertices per queue grab
+    int stride;                 // every stride-th start vertex (timing samples)
+    long long n_tasks;          // ceil(n / stride)
     unsigned long long *counts; // 2 words per slot
 };
 
@@ -79,8 +80,9 @@ __device__ void count_terms(const BatchArgs &a, const PgTrieNode &C, const int *
         }
 }
 
-__global__ void __launch_bounds__(kBlock) k_count_batched(BatchArgs a) {
-    __shared__ unsigned long long s_acc[kWarps][2 * kMaxSlots];
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_count_batched(BatchArgs a) {
+    __shared__ unsigned long long s_acc[W][2 * kMaxSlots];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -90,11 +92,17 @@ __global__ void __launch_bounds__(kBlock) k_count_batched(BatchArgs a) {
     __syncwarp();
     const DevGraph &g = a.g;
     int m[PGP_MAXK], node[PGP_MAXK], sz[PGP_MAXK], ci[PGP_MAXK], ch[PGP_MAXK];
+    long long task = 0, task_end = 0;
     for (;;) {
-        int v = 0;
-        if (lane == 0) v = (int)atomicAdd(a.queue, 1ull);
-        v = __shfl_sync(PG_FULL, v, 0);
-        if (v >= a.n) break;
+        if (task >= task_end) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(a.queue, (unsigned long long)a.chunk);
+            task = (long long)__shfl_sync(PG_FULL, t, 0);
+            if (task >= a.n_tasks) break;
+            task_end = min(task + a.chunk, a.n_tasks);
+        }
+        const int v = (int)(task * a.stride);
+        ++task;
         const int label = g.labeled ? __ldg(&g.vinfo[v].w) : 0;
         for (int r = 0; r < a.n_roots; ++r) {
             const PgTrieNode &R = a.nodes[r];
@@ -176,10 +184,19 @@ __global__ void k_combine(const unsigned long long *slot_counts, const int *term
     out[2 * i + 1] = (unsigned long long)(acc >> 64);
 }
 
+int batched_warps(const pg_graph *g) {
+    const int w = g->tune.batched_warps;
+    return (w == 2 || w == 8) ? w : 4;
+}
+
 int batched_grid(const pg_graph *g) {
+    const int w = batched_warps(g);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched, kBlock, 0);
+    if (w == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched<2>, 64, 0);
+    else if (w == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched<4>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched<8>, 256, 0);
     if (per_sm < 1) per_sm = 1;
+    if (g->tune.batched_blocks_per_sm > 0) per_sm = std::min(per_sm, g->tune.batched_blocks_per_sm);
     return per_sm * g->num_sms;
 }
 
@@ -567,7 +584,7 @@ long long batch_layout(const pg_graph *g, const pg_batch *b, long long *off) {
 
 size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b) {
     long long off[PGP_MAXK];
-    size_t bytes = (size_t)batched_grid(g) * kWarps * (size_t)batch_layout(g, b, off) * sizeof(int);
+    size_t bytes = (size_t)batched_grid(g) * batched_warps(g) * (size_t)batch_layout(g, b, off) * sizeof(int);
     if (b->clique_kmax) bytes = std::max(bytes, pg_clique_scratch_bytes(g));
     return bytes;
 }
@@ -588,11 +605,17 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.warp_stride = batch_layout(g, b, a.lvl_off);
     a.queue = g->ex->queues + queue_slot;
     a.n = (int)g->n;
+    a.chunk = std::max(1, g->tune.batched_chunk);
+    a.stride = std::max(1, g->sample_stride);
+    a.n_tasks = (g->n + a.stride - 1) / a.stride;
     a.counts = b->d_slot_counts;
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
     if (b->n_roots > 0) {
         PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
-        k_count_batched<<<batched_grid(g), kBlock, 0, s>>>(a);
+        const int w = batched_warps(g), grid = batched_grid(g);
+        if (w == 2) k_count_batched<2><<<grid, 64, 0, s>>>(a);
+        else if (w == 4) k_count_batched<4><<<grid, 128, 0, s>>>(a);
+        else k_count_batched<8><<<grid, 256, 0, s>>>(a);
         PG_CUDA(cudaGetLastError());
     }
     if (b->clique_kmax) {

@@ -55,6 +55,11 @@ struct CliqueArgs {
     long long slab_words;
     unsigned long long *queue; // [0] light cursor, [1] heavy cursor
     unsigned long long *counts;
+    int chunk;                 // light start vertices per queue grab
+    int heavy_min;             // light vertices have out-degree <= heavy_min (<= kLightD)
+    int stride;                // every stride-th start vertex (timing samples)
+    long long n_light_tasks;   // ceil(n / stride)
+    long long n_heavy_tasks;   // ceil(n_heavy / stride)
 };
 
 // Sub-graph tile of one start vertex: list = N+(v) (d entries), rows[i] =
@@ -357,7 +362,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long h = atomicAdd(a.queue + 1, 1ull);
-            ctl[0] = h < (unsigned long long)a.n_heavy ? a.heavy[h] : -1;
+            ctl[0] = h < (unsigned long long)a.n_heavy_tasks ? a.heavy[h * (unsigned long long)a.stride] : -1;
             ctl[1] = 0; // rows traversed
         }
         __syncthreads();
@@ -397,15 +402,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
     }
     for (;;) {
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, 4ull);
+        if (lane == 0) base = atomicAdd(a.queue, (unsigned long long)a.chunk);
         base = __shfl_sync(PG_FULL, base, 0);
-        if (base >= (unsigned long long)a.n) break;
-        for (int q = 0; q < 4; ++q) {
-            const int v = (int)base + q;
-            if (v >= a.n) break;
+        if (base >= (unsigned long long)a.n_light_tasks) break;
+        for (int q = 0; q < a.chunk; ++q) {
+            const unsigned long long t = base + (unsigned long long)q;
+            if (t >= (unsigned long long)a.n_light_tasks) break;
+            const int v = (int)(t * (unsigned long long)a.stride);
             const int4 vi = __ldg(&g.vinfo[v]);
             const int d = vi.z;
-            if (d < a.kmin - 1 || d > kLightD) continue;
+            if (d < a.kmin - 1 || d > a.heavy_min) continue;
             const int *nv = adj_of(g, vi);
             for (int i = lane; i < d; i += 32) lt.list[i] = __ldg(nv + i);
             __syncwarp();
@@ -461,6 +467,7 @@ int clique_grid(const pg_graph *g, size_t smem) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_clique, kBlock, smem);
     if (per_sm < 1) per_sm = 1;
+    if (g->tune.clique_blocks_per_sm > 0) per_sm = std::min(per_sm, g->tune.clique_blocks_per_sm);
     return per_sm * g->num_sms;
 }
 
@@ -480,6 +487,11 @@ int launch(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, unsi
     a.slabs = a.slab_words ? (unsigned *)slabs : nullptr;
     a.queue = queue;
     a.counts = counts_dev;
+    a.chunk = g->tune.clique_chunk;
+    a.heavy_min = g->heavy_min_built; // the threshold the heavy list was built with
+    a.stride = std::max(1, g->sample_stride);
+    a.n_light_tasks = (g->n + a.stride - 1) / a.stride;
+    a.n_heavy_tasks = (g->n_heavy + a.stride - 1) / a.stride;
     long long blocks = clique_grid(g, L.smem_bytes);
     if (a.slab_words && blocks > max_slabs) blocks = max_slabs;
     if (blocks < 1) return pg_set_error(PG_EINVAL, "scratch holds no slab for a single block");

@@ -116,13 +116,13 @@ __global__ void k_finish(int *adj, const int64_t *pstart, const int64_t *udeg, c
     atomicMax(maxes + 2, lab);
 }
 
-// heavy clique start vertices: out-degree > PG_CLIQUE_LIGHT_D, keyed by
+// heavy clique start vertices: out-degree > heavy_min, keyed by
 // (out-degree descending, rank ascending); others get the largest key
-__global__ void k_heavy_keys(const int4 *vinfo, int64_t n, unsigned long long *keys, unsigned *count) {
+__global__ void k_heavy_keys(const int4 *vinfo, int64_t n, int heavy_min, unsigned long long *keys, unsigned *count) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int dplus = vinfo[r].z;
-    if (dplus > PG_CLIQUE_LIGHT_D) {
+    if (dplus > heavy_min) {
         keys[r] = ((0xffffffffull - (unsigned long long)dplus) << 32) | (unsigned long long)r;
         atomicAdd(count, 1u);
     } else {
@@ -264,42 +264,86 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     g->max_out = hm[1];
     g->n_labels = d_labels ? hm[2] + 1 : 0;
 
-    // hub bitmaps for the highest-degree ranks
-    if (n > 0) {
-        std::vector<int4> head(std::min<int64_t>(n, PG_MAX_HUBS));
+    int rc = pg_graph_build_hubs(g, g->tune.hub_min_degree, g->tune.hub_max, s);
+    if (rc) return rc;
+    rc = pg_graph_build_heavy(g, g->tune.clique_heavy_min, s);
+    if (rc) return rc;
+    g->bytes_device = (int64_t)(nn * (2 * sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int));
+    return PG_OK;
+}
+
+int64_t pg_graph_bytes(const pg_graph *g) {
+    return g->bytes_device + (int64_t)g->n_hubs * g->hub_stride * 4 + g->n_heavy * 4;
+}
+
+// Hub bitmaps for the highest-degree ranks: ranks 0..h-1 of degree >=
+// min_degree, h <= max_hubs, at most 2 GiB.  Replaces earlier rows.
+int pg_graph_build_hubs(pg_graph *g, int min_degree, int max_hubs, cudaStream_t s) {
+    const int64_t n = g->n;
+    if (g->hubbits) {
+        PG_CUDA(cudaDeviceSynchronize()); // launches may still read the old rows
+        cudaFree(g->hubbits);
+        g->hubbits = nullptr;
+    }
+    g->n_hubs = 0;
+    g->hub_stride = (int)((n + 31) / 32);
+    if (n > 0 && max_hubs > 0) {
+        std::vector<int4> head(std::min<int64_t>(n, max_hubs));
         PG_CUDA(cudaMemcpyAsync(head.data(), g->vinfo, head.size() * sizeof(int4), cudaMemcpyDeviceToHost, s));
         PG_CUDA(cudaStreamSynchronize(s));
         int h = 0;
-        while (h < (int)head.size() && head[h].y >= PG_HUB_MIN_DEGREE) ++h;
-        const int stride = (int)((n + 31) / 32);
+        while (h < (int)head.size() && head[h].y >= min_degree) ++h;
+        const int stride = g->hub_stride;
         while (h > 0 && (int64_t)h * stride * 4 > (2ll << 30)) --h; // at most 2 GiB
-        g->n_hubs = h;
-        g->hub_stride = stride;
         if (h > 0) {
             PG_CUDA(cudaMalloc(&g->hubbits, (size_t)h * stride * sizeof(unsigned)));
             PG_CUDA(cudaMemsetAsync(g->hubbits, 0, (size_t)h * stride * sizeof(unsigned), s));
             k_hub_bits<<<grid_for((int64_t)h * 32, kBlock), kBlock, 0, s>>>(g->vinfo, g->adj, h, stride, g->hubbits);
             PG_CUDA(cudaGetLastError());
+            PG_CUDA(cudaStreamSynchronize(s));
         }
+        g->n_hubs = h;
     }
+    g->d.hubbits = g->hubbits;
+    g->d.n_hubs = g->n_hubs;
+    g->d.hub_stride = g->hub_stride;
+    return PG_OK;
+}
 
-    // heavy clique start vertices (reuse the vertex key buffers)
-    if (n > 0) {
-        PG_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
-        k_heavy_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(g->vinfo, n, (unsigned long long *)vkeys.p, err);
-        need = tmp_bytes;
-        PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, need, (unsigned long long *)vkeys.p,
-                                               (unsigned long long *)vkeys2.p, (int64_t)n, 0, 64, s));
-        unsigned nh = 0;
-        PG_CUDA(cudaMemcpyAsync(&nh, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        PG_CUDA(cudaStreamSynchronize(s));
-        g->n_heavy = nh;
-        PG_CUDA(cudaMalloc(&g->heavy, (nh > 0 ? nh : 1) * sizeof(int)));
-        if (nh > 0) k_heavy_ids<<<grid_for(nh, kBlock), kBlock, 0, s>>>((unsigned long long *)vkeys2.p, nh, g->heavy);
-        PG_CUDA(cudaGetLastError());
-        PG_CUDA(cudaStreamSynchronize(s));
+// Heavy clique start vertices: out-degree > heavy_min, by out-degree
+// descending (rank ascending on ties).  Replaces the earlier list.
+int pg_graph_build_heavy(pg_graph *g, int heavy_min, cudaStream_t s) {
+    const int64_t n = g->n;
+    if (g->heavy) {
+        PG_CUDA(cudaDeviceSynchronize());
+        cudaFree(g->heavy);
+        g->heavy = nullptr;
     }
-    g->bytes_device = (int64_t)(nn * (2 * sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int)) +
-                      (int64_t)g->n_hubs * g->hub_stride * 4 + g->n_heavy * 4;
+    g->n_heavy = 0;
+    const int64_t nn = n > 0 ? n : 1;
+    PG_CUDA(cudaMalloc(&g->heavy, nn * sizeof(int)));
+    if (n == 0) return PG_OK;
+    DevBuf k1, k2, cnt, tmp;
+    PG_CUDA(cudaMalloc(&k1.p, nn * sizeof(unsigned long long)));
+    PG_CUDA(cudaMalloc(&k2.p, nn * sizeof(unsigned long long)));
+    PG_CUDA(cudaMalloc(&cnt.p, sizeof(unsigned)));
+    size_t tmp_bytes = 0;
+    PG_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, (unsigned long long *)k1.p,
+                                           (unsigned long long *)k2.p, (int64_t)n, 0, 64, s));
+    PG_CUDA(cudaMalloc(&tmp.p, tmp_bytes + 16));
+    PG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), s));
+    k_heavy_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(g->vinfo, n, heavy_min, (unsigned long long *)k1.p,
+                                                        (unsigned *)cnt.p);
+    PG_CUDA(cudaGetLastError());
+    PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, tmp_bytes, (unsigned long long *)k1.p,
+                                           (unsigned long long *)k2.p, (int64_t)n, 0, 64, s));
+    unsigned nh = 0;
+    PG_CUDA(cudaMemcpyAsync(&nh, cnt.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    g->n_heavy = nh;
+    g->heavy_min_built = heavy_min;
+    if (nh > 0) k_heavy_ids<<<grid_for(nh, kBlock), kBlock, 0, s>>>((unsigned long long *)k2.p, nh, g->heavy);
+    PG_CUDA(cudaGetLastError());
+    PG_CUDA(cudaStreamSynchronize(s));
     return PG_OK;
 }

@@ -49,6 +49,20 @@ int pg_exec_init(pg_exec *x);
 void pg_exec_release(pg_exec *x);
 #define PG_CLIQUE_LIGHT_D 64 // out-degree up to which one warp handles a clique start vertex
 
+// Defaults of the launch parameters (pg_tuning in pg.h).
+inline pg_tuning pg_default_tuning() {
+    pg_tuning t;
+    t.clique_chunk = 4;
+    t.clique_blocks_per_sm = 0;
+    t.clique_heavy_min = PG_CLIQUE_LIGHT_D;
+    t.batched_warps = 4;
+    t.batched_chunk = 1;
+    t.batched_blocks_per_sm = 0;
+    t.hub_min_degree = PG_HUB_MIN_DEGREE;
+    t.hub_max = PG_MAX_HUBS;
+    return t;
+}
+
 struct pg_graph {
     DevGraph d{};
     int4 *vinfo = nullptr;
@@ -67,13 +81,19 @@ struct pg_graph {
     pg_exec exec0;
     pg_exec *ex = &exec0;
     bool is_view = false;
-    // vertices with out-degree > PG_CLIQUE_LIGHT_D, by out-degree descending
+    // vertices with out-degree > heavy_min_built, by out-degree descending
     int *heavy = nullptr;
     int64_t n_heavy = 0;
+    int heavy_min_built = PG_CLIQUE_LIGHT_D; // out-degree threshold of the heavy list
+    int servers = 0;                         // running servers holding views of this graph
     // last batch built by pg_count_ex for a plan list (keyed by plan serials)
     pg_batch *batch_cache = nullptr;
     std::vector<uint64_t> batch_key;
-    int64_t bytes_device = 0;
+    int64_t bytes_device = 0;  // vinfo, adj, rank maps (hubs and heavy list: pg_graph_bytes)
+    pg_tuning tune = pg_default_tuning();
+    // launches take every sample_stride-th start vertex (timing samples of
+    // pg_autotune only; 1 otherwise)
+    int sample_stride = 1;
 };
 
 #define PG_STATIC_SCRATCH_BYTES (32u << 20) // fixed scratch of pg_count_cliques_noalloc
@@ -101,6 +121,9 @@ int pg_cuda_error(cudaError_t e, const char *what);
 // graph.cu
 int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int64_t nnz,
                    const int32_t *d_labels, cudaStream_t s);
+int pg_graph_build_hubs(pg_graph *g, int min_degree, int max_hubs, cudaStream_t s);
+int pg_graph_build_heavy(pg_graph *g, int heavy_min, cudaStream_t s);
+int64_t pg_graph_bytes(const pg_graph *g);
 
 // scratch management (api.cu)
 int pg_ensure_scratch(pg_graph *g, size_t bytes, cudaStream_t s);

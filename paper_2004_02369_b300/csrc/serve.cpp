@@ -235,6 +235,7 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
     pg_server *S = new (std::nothrow) pg_server();
     if (!S) return pg_set_error(PG_ENOMEM, "host allocation failed");
     S->g = g;
+    g->servers++; // views copy the graph's hub and heavy pointers: no retuning meanwhile
     S->cfg = *cfg;
     S->t0 = std::chrono::steady_clock::now();
     const int n_streams = cfg->serial ? 1 : std::max(1, std::min(cfg->n_streams, 16));
@@ -356,5 +357,6 @@ extern "C" void pg_server_free(pg_server *S) {
         pg_exec_release(&s.ex);
     }
     for (auto &kv : S->plans) pg_free_plan(kv.second);
+    if (S->g) S->g->servers--;
     delete S;
 }
