@@ -313,6 +313,11 @@ void pg_free_batch(pg_batch *b);
  *   hub_min_degree        vertices of at least this degree get a membership
  *   hub_max               bitmap row, at most hub_max of them (highest degree
  *                         first; defaults 1024 and 512; hub_max 0 = none).
+ *   batched_split_grain   a start vertex of degree d > grain becomes
+ *                         ceil(d / grain) batched-kernel tasks (at most 1024)
+ *                         that share its first-level candidates, so that hub
+ *                         start vertices do not serialise on one warp
+ *                         (0 = no split; default 512).
  */
 typedef struct {
     int32_t clique_chunk;
@@ -323,13 +328,18 @@ typedef struct {
     int32_t batched_blocks_per_sm;
     int32_t hub_min_degree;
     int32_t hub_max;
+    int32_t batched_split_grain;
+    int32_t pad;
 } pg_tuning;
 
 /* Outcome of pg_autotune. */
 typedef struct {
     pg_tuning chosen;     /* now in effect on the graph */
     double default_ms;    /* timed launch with the parameters in effect before */
-    double tuned_ms;      /* timed launch with `chosen` (same sample) */
+    double tuned_ms;      /* best timed launch of the search (same sample) */
+    double full_default_ms; /* sample_stride > 1 and a different choice: full */
+    double full_tuned_ms;   /* launches with the old and the chosen parameters; the
+                               chosen ones are kept only if faster (else -1) */
     double wall_ms;       /* host time of the whole search */
     int32_t trials;       /* configurations timed */
     int32_t kernel;       /* PG_KERNEL_* family tuned (CLIQUE or BATCHED) */
@@ -351,9 +361,11 @@ int pg_set_tuning(pg_graph *g, const pg_tuning *t, void *stream);
  * have nothing to tune and return PG_EUNSUPPORTED).  Coordinate descent over
  * the family's knobs: each value is timed with CUDA events on `stream` (one
  * untimed launch, then the best of two), the best kept before the next knob.
- * sample_stride >= 1 times only every sample_stride-th start vertex (in rank
+ * sample_stride >= 1 times only every sample_stride-th task (in rank
  * order), so a workload whose full launch takes seconds is tuned in
- * proportionally less time; 1 times the full launch.  Synchronous; report
+ * proportionally less time; 1 times the full launch.  A choice made on a
+ * sample is then timed against the previous parameters on the full launch
+ * and kept only if faster.  Synchronous; report
  * (host) may be NULL.  Errors: PG_EINVAL, PG_EUNSUPPORTED, PG_ENOMEM,
  * PG_EDEVICE.
  */

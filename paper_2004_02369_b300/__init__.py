@@ -348,14 +348,16 @@ class Tuning(ctypes.Structure):
     _fields_ = [("clique_chunk", ctypes.c_int32), ("clique_blocks_per_sm", ctypes.c_int32),
                 ("clique_heavy_min", ctypes.c_int32), ("batched_warps", ctypes.c_int32),
                 ("batched_chunk", ctypes.c_int32), ("batched_blocks_per_sm", ctypes.c_int32),
-                ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32)]
+                ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32),
+                ("batched_split_grain", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "pad"}
 
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("chosen", Tuning), ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
+                ("full_default_ms", ctypes.c_double), ("full_tuned_ms", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("trials", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("sample_stride", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
@@ -384,6 +386,7 @@ def autotune(graph: Graph, plans, sample_stride: int = 1, stream=None) -> dict:
     _check(_lib.pg_autotune(graph.handle, _plan_array(plans), len(plans), sample_stride, ctypes.byref(r),
                             _stream_ptr(stream)))
     return {"chosen": r.chosen.as_dict(), "default_ms": r.default_ms, "tuned_ms": r.tuned_ms,
+            "full_default_ms": r.full_default_ms, "full_tuned_ms": r.full_tuned_ms,
             "wall_ms": r.wall_ms, "trials": int(r.trials), "kernel": int(r.kernel),
             "sample_stride": int(r.sample_stride)}
 

@@ -118,6 +118,7 @@ extern "C" void pg_free_graph(pg_graph *g) {
     if (g->hubbits) cudaFree(g->hubbits);
     pg_exec_release(&g->exec0);
     if (g->heavy) cudaFree(g->heavy);
+    if (g->split_prefix) cudaFree(g->split_prefix);
     if (g->batch_cache) pg_batch_free(g->batch_cache);
     delete g;
 }

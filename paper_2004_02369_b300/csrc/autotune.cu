@@ -12,6 +12,7 @@
 // sample of start vertices.  Counts never depend on the values.
 #include <chrono>
 #include <cmath>
+#include <cstring>
 
 #include "pg_internal.h"
 
@@ -41,6 +42,8 @@ int check_tuning(const pg_tuning &t) {
     if (t.batched_chunk < 1 || t.batched_chunk > 64) return pg_set_error(PG_EINVAL, "batched_chunk must be 1..64");
     if (t.hub_min_degree < 1 || t.hub_max < 0 || t.hub_max > 65536)
         return pg_set_error(PG_EINVAL, "hub_min_degree must be >= 1 and hub_max 0..65536");
+    if (t.batched_split_grain != 0 && t.batched_split_grain < 16)
+        return pg_set_error(PG_EINVAL, "batched_split_grain must be 0 or >= 16");
     return PG_OK;
 }
 
@@ -53,6 +56,10 @@ int apply(pg_graph *g, const pg_tuning &t, cudaStream_t s) {
     }
     if (t.clique_heavy_min != g->heavy_min_built) {
         rc = pg_graph_build_heavy(g, t.clique_heavy_min, s);
+        if (rc) return rc;
+    }
+    if (t.batched_split_grain != g->split_grain_built) {
+        rc = pg_graph_build_split(g, t.batched_split_grain, s);
         if (rc) return rc;
     }
     g->tune = t;
@@ -124,6 +131,7 @@ extern "C" int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         {&pg_tuning::clique_blocks_per_sm, {1, 2, 0}},
     };
     if (kernel == PG_KERNEL_BATCHED) {
+        knobs.push_back({&pg_tuning::batched_split_grain, {0, 128, 512, 2048}});
         knobs.push_back({&pg_tuning::batched_warps, {2, 4, 8}});
         knobs.push_back({&pg_tuning::batched_chunk, {1, 2, 4, 8}});
         knobs.push_back({&pg_tuning::batched_blocks_per_sm, {1, 2, 4, 0}});
@@ -168,6 +176,18 @@ extern "C" int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         }
     } while (0);
     g->sample_stride = 1;
+    // a choice made on a sample is kept only if the full launch agrees
+    double full_start = -1, full_best = -1;
+    if (!rc && sample_stride > 1 && std::memcmp(&best, &start, sizeof(best)) != 0) {
+        do {
+            if ((rc = apply(g, start, s)) != PG_OK) break;
+            if ((rc = time_count(g, plans, n_plans, kernel, (uint64_t *)dc.p, s, ev, &full_start)) != PG_OK) break;
+            if ((rc = apply(g, best, s)) != PG_OK) break;
+            if ((rc = time_count(g, plans, n_plans, kernel, (uint64_t *)dc.p, s, ev, &full_best)) != PG_OK) break;
+            trials += 2;
+            if (full_best >= full_start) best = start;
+        } while (0);
+    }
     const int rc2 = apply(g, rc ? start : best, s);
     if (rc) return rc;
     if (rc2) return rc2;
@@ -175,6 +195,8 @@ extern "C" int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         report->chosen = best;
         report->default_ms = base_ms;
         report->tuned_ms = best_ms;
+        report->full_default_ms = full_start;
+        report->full_tuned_ms = full_best;
         report->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         report->trials = trials;
         report->kernel = kernel;

@@ -56,9 +56,15 @@ struct BatchArgs {
     long long lvl_off[PGP_MAXK];
     unsigned long long *queue;
     int n;
-    int chunk;                  // start vertices per queue grab
-    int stride;                 // every stride-th start vertex (timing samples)
-    long long n_tasks;          // ceil(n / stride)
+    int chunk;                  // tasks per queue grab
+    int stride;                 // every stride-th task (timing samples)
+    long long n_tasks;          // ceil((n_split_tasks + n - n_split) / stride)
+    // Ranks 0..n_split-1 (the highest degrees) are split: rank r owns tasks
+    // split_prefix[r] .. split_prefix[r+1]-1, task j of S walking the level-1
+    // candidates with index = j (mod S).  Later ranks are one task each.
+    const long long *split_prefix;
+    int n_split;
+    long long n_split_tasks;
     unsigned long long *counts; // 2 words per slot
 };
 
@@ -101,13 +107,26 @@ __global__ void __launch_bounds__(W * 32) k_count_batched(BatchArgs a) {
             if (task >= a.n_tasks) break;
             task_end = min(task + a.chunk, a.n_tasks);
         }
-        const int v = (int)(task * a.stride);
+        const long long tg = task * a.stride;
         ++task;
+        int v, part = 0, parts = 1;
+        if (tg < a.n_split_tasks) {
+            int lo = 0, hi = a.n_split; // last r with split_prefix[r] <= tg
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(a.split_prefix + mid) <= tg) lo = mid; else hi = mid;
+            }
+            v = lo;
+            part = (int)(tg - __ldg(a.split_prefix + lo));
+            parts = (int)(__ldg(a.split_prefix + lo + 1) - __ldg(a.split_prefix + lo));
+        } else {
+            v = a.n_split + (int)(tg - a.n_split_tasks);
+        }
         const int label = g.labeled ? __ldg(&g.vinfo[v].w) : 0;
         for (int r = 0; r < a.n_roots; ++r) {
             const PgTrieNode &R = a.nodes[r];
             if (R.spec.label >= 0 && R.spec.label != label) continue;
-            if (lane == 0)
+            if (lane == 0 && part == 0)
                 for (int t = 0; t < R.n_terms; ++t) add_slot(acc, a.terms[R.first_term + t].slot, 1);
             if (R.n_children == 0) continue;
             int l = 0;
@@ -120,7 +139,7 @@ __global__ void __launch_bounds__(W * 32) k_count_batched(BatchArgs a) {
                 const PgTrieNode &N = a.nodes[node[l]];
                 if (ch[l] >= N.n_children) {
                     ch[l] = 0;
-                    if (++ci[l] >= sz[l]) {
+                    if ((ci[l] += (l == 1 ? parts : 1)) >= sz[l]) {
                         if (l == 0) break;
                         --l;
                         ++ch[l];
@@ -130,8 +149,9 @@ __global__ void __launch_bounds__(W * 32) k_count_batched(BatchArgs a) {
                 if (l > 0) m[l] = wbuf[a.lvl_off[l] + ci[l]];
                 const int child = N.first_child + ch[l];
                 const PgTrieNode &C = a.nodes[child];
-                if (C.n_terms) count_terms(a, C, m, lane, acc);
-                for (int j = 0; j < C.n_joint; ++j) {
+                // what depends on the start vertex alone is counted by part 0
+                if (C.n_terms && (l > 0 || part == 0)) count_terms(a, C, m, lane, acc);
+                for (int j = 0; j < C.n_joint && (l > 0 || part == 0); ++j) {
                     const PgTrieNode &J = a.nodes[C.first_child + C.n_children + j];
                     const unsigned long long c =
                         count_joint(g, C.spec, J.spec, l + 1, m, wbuf + a.lvl_off[l + 1], wbuf + a.lvl_off[l + 2], lane);
@@ -140,11 +160,12 @@ __global__ void __launch_bounds__(W * 32) k_count_batched(BatchArgs a) {
                 }
                 if (C.n_children) {
                     const int s = fill_level(g, C.spec, m, wbuf + a.lvl_off[l + 1], lane);
-                    if (s > 0) {
+                    const int first = l == 0 ? part : 0; // a part's first level-1 candidate
+                    if (s > first) {
                         ++l;
                         node[l] = child;
                         sz[l] = s;
-                        ci[l] = 0;
+                        ci[l] = first;
                         ch[l] = 0;
                         continue;
                     }
@@ -607,7 +628,10 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.n = (int)g->n;
     a.chunk = std::max(1, g->tune.batched_chunk);
     a.stride = std::max(1, g->sample_stride);
-    a.n_tasks = (g->n + a.stride - 1) / a.stride;
+    a.split_prefix = g->split_prefix;
+    a.n_split = g->n_split;
+    a.n_split_tasks = g->n_split_tasks;
+    a.n_tasks = (g->n_split_tasks + (g->n - g->n_split) + a.stride - 1) / a.stride;
     a.counts = b->d_slot_counts;
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
     if (b->n_roots > 0) {

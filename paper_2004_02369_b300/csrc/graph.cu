@@ -268,12 +268,60 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     if (rc) return rc;
     rc = pg_graph_build_heavy(g, g->tune.clique_heavy_min, s);
     if (rc) return rc;
+    rc = pg_graph_build_split(g, g->tune.batched_split_grain, s);
+    if (rc) return rc;
     g->bytes_device = (int64_t)(nn * (2 * sizeof(int) + sizeof(int4)) + g->adj_entries * sizeof(int));
     return PG_OK;
 }
 
 int64_t pg_graph_bytes(const pg_graph *g) {
-    return g->bytes_device + (int64_t)g->n_hubs * g->hub_stride * 4 + g->n_heavy * 4;
+    return g->bytes_device + (int64_t)g->n_hubs * g->hub_stride * 4 + g->n_heavy * 4 +
+           (g->split_prefix ? (int64_t)(g->n_split + 1) * 8 : 0);
+}
+
+// Task split of the batched kernel: ranks r < n_split (degree > grain) own
+// ceil(degree / grain) tasks each (at most 1024), laid out by the prefix
+// array split_prefix[0..n_split].  Degrees fall with rank, so n_split is
+// found by binary search over single vinfo reads.
+int pg_graph_build_split(pg_graph *g, int grain, cudaStream_t s) {
+    if (g->split_prefix) {
+        PG_CUDA(cudaDeviceSynchronize());
+        cudaFree(g->split_prefix);
+        g->split_prefix = nullptr;
+    }
+    g->n_split = 0;
+    g->n_split_tasks = 0;
+    g->split_grain_built = grain;
+    if (grain <= 0 || g->n == 0) return PG_OK;
+    auto degree = [&](int64_t r, int *d) -> int {
+        int4 vi;
+        PG_CUDA(cudaMemcpyAsync(&vi, g->vinfo + r, sizeof(int4), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaStreamSynchronize(s));
+        *d = vi.y;
+        return PG_OK;
+    };
+    int64_t lo = 0, hi = g->n; // first rank with degree <= grain
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        int d = 0;
+        int rc = degree(mid, &d);
+        if (rc) return rc;
+        if (d > grain) lo = mid + 1; else hi = mid;
+    }
+    const int64_t h = lo;
+    if (h == 0) return PG_OK;
+    std::vector<int4> head(h);
+    PG_CUDA(cudaMemcpyAsync(head.data(), g->vinfo, h * sizeof(int4), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    std::vector<long long> prefix(h + 1, 0);
+    for (int64_t r = 0; r < h; ++r)
+        prefix[r + 1] = prefix[r] + std::min<long long>(1024, ((long long)head[r].y + grain - 1) / grain);
+    PG_CUDA(cudaMalloc(&g->split_prefix, (h + 1) * sizeof(long long)));
+    PG_CUDA(cudaMemcpyAsync(g->split_prefix, prefix.data(), (h + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    g->n_split = (int)h;
+    g->n_split_tasks = prefix[h];
+    return PG_OK;
 }
 
 // Hub bitmaps for the highest-degree ranks: ranks 0..h-1 of degree >=

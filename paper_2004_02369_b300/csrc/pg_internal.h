@@ -60,6 +60,7 @@ inline pg_tuning pg_default_tuning() {
     t.batched_blocks_per_sm = 0;
     t.hub_min_degree = PG_HUB_MIN_DEGREE;
     t.hub_max = PG_MAX_HUBS;
+    t.batched_split_grain = 512;
     return t;
 }
 
@@ -85,6 +86,11 @@ struct pg_graph {
     int *heavy = nullptr;
     int64_t n_heavy = 0;
     int heavy_min_built = PG_CLIQUE_LIGHT_D; // out-degree threshold of the heavy list
+    // batched-kernel task split of the highest-degree ranks (see count_batched.cu)
+    long long *split_prefix = nullptr;
+    int n_split = 0;
+    long long n_split_tasks = 0;
+    int split_grain_built = 0;
     int servers = 0;                         // running servers holding views of this graph
     // last batch built by pg_count_ex for a plan list (keyed by plan serials)
     pg_batch *batch_cache = nullptr;
@@ -123,6 +129,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
                    const int32_t *d_labels, cudaStream_t s);
 int pg_graph_build_hubs(pg_graph *g, int min_degree, int max_hubs, cudaStream_t s);
 int pg_graph_build_heavy(pg_graph *g, int heavy_min, cudaStream_t s);
+int pg_graph_build_split(pg_graph *g, int grain, cudaStream_t s);
 int64_t pg_graph_bytes(const pg_graph *g);
 
 // scratch management (api.cu)

@@ -38,7 +38,7 @@ def motif_case(pg):
 
 CLIQUE_VALUES = {"clique_heavy_min": [8, 16, 33, 64], "clique_chunk": [1, 3, 16, 64],
                  "clique_blocks_per_sm": [1, 2, 0]}
-BATCHED_VALUES = {"batched_warps": [2, 8, 4], "batched_chunk": [1, 5, 64], "batched_blocks_per_sm": [1, 3, 0],
+BATCHED_VALUES = {"batched_split_grain": [16, 100, 0, 512], "batched_warps": [2, 8, 4], "batched_chunk": [1, 5, 64], "batched_blocks_per_sm": [1, 3, 0],
                   "hub_min_degree": [1, 300, 1 << 30, 1024], "hub_max": [0, 7, 2048, 512]}
 
 
@@ -82,18 +82,22 @@ def test_autotune_batched_sampled(pg, motif_case):
     g, pats, want = motif_case
     G = pg.Graph.from_synth(g)
     plans = [pg.Plan.from_dict(p) for p in pats]
+    default = pg.get_tuning(G)
     rep = pg.autotune(G, plans, sample_stride=7)
     assert rep["kernel"] == pg.KERNEL_BATCHED and rep["sample_stride"] == 7
     assert rep["tuned_ms"] <= rep["default_ms"]
     assert rep["chosen"]["batched_warps"] in (2, 4, 8)
     assert pg.get_tuning(G) == rep["chosen"]
+    if rep["full_tuned_ms"] >= 0:  # a sampled choice is kept only if the full launch is faster
+        assert rep["full_tuned_ms"] < rep["full_default_ms"] or rep["chosen"] == default
     assert pg.count(G, plans) == want  # full counts after a sampled search
 
 
 def test_tuning_validation(pg):
     g = sg.erdos_renyi(100, 0.05, 304)
     G = pg.Graph.from_synth(g)
-    for bad in [dict(batched_warps=3), dict(clique_chunk=0), dict(clique_heavy_min=65), dict(hub_max=-1)]:
+    for bad in [dict(batched_warps=3), dict(clique_chunk=0), dict(clique_heavy_min=65), dict(hub_max=-1),
+                dict(batched_split_grain=8)]:
         with pytest.raises(pg.PgError) as e:
             pg.set_tuning(G, **bad)
         assert e.value.code == pg.PG_EINVAL
