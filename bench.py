@@ -28,8 +28,8 @@ import synthgraph as sg  # noqa: E402
 WORKLOAD = "kclique_chunglu_n1M_m10M_g2.1"
 # ncu figures of k_count_clique on this workload (profiles/k_count_clique_chunglu_n1M_m10M.md),
 # valid only for the kernel source they were taken on
-NCU_CLIQUE = {"source_sha16": "9b62fc6937754486", "dram_bytes_per_launch": 88186880,
-              "l2_bytes_per_launch": 5773751136, "issue_active_frac": 0.693, "inst_executed_frac": 0.647}
+NCU_CLIQUE = {"source_sha16": "9aa03cc35376c69d", "dram_bytes_per_launch": 89225984,
+              "l2_bytes_per_launch": 5841528672, "issue_active_frac": 0.691, "inst_executed_frac": 0.690}
 METRIC = "exact pattern matches/sec"
 UNIT = "matches/s"
 CLIQUE_SIZES = (4, 5)
