@@ -201,6 +201,25 @@ int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *c
                 int32_t kernel, void *stream);
 
 /*
+ * pg_count_until - count one plan's matches until `target` of them are found
+ * (existence queries, Section 3.2.3, with early termination, Section 5.4).
+ * Warps add their counts to a device total after every task; the first that
+ * sees the total reach `target` raises a device stop flag, which the others
+ * poll between tasks and between first-level candidates, so exploration ends
+ * soon after the target is met.
+ *   target     >= 1 (1 = "does a match exist?").
+ *   count_out  host uint64[2], (low, high): the number of matches found
+ *              before exploration stopped.  Exact when *reached is 0 (the
+ *              whole graph was explored); otherwise a partial count >= target.
+ *   reached    host: 1 if at least `target` matches exist, else 0.
+ * Runs on the plan interpreter (PG_KERNEL_GENERIC).  Synchronous.  Errors:
+ * PG_EINVAL (target 0, NULL argument, labeled pattern on an unlabeled
+ * graph), PG_ENOMEM, PG_EDEVICE.
+ */
+int pg_count_until(pg_graph *g, pg_plan *p, uint64_t target, uint64_t *count_out, int32_t *reached,
+                   void *stream);
+
+/*
  * pg_match - list the distinct matches of one plan's pattern (Section 3.2,
  * match(G, p, f): the callback f becomes an output array).
  *   out_dev   int32[capacity * k], device, caller-owned: row r holds one
@@ -318,6 +337,9 @@ void pg_free_batch(pg_batch *b);
  *                         that share its first-level candidates, so that hub
  *                         start vertices do not serialise on one warp
  *                         (0 = no split; default 512).
+ *   batched_regcap        1: the batched kernel variant limited to 64
+ *                         registers per thread (more resident warps, some
+ *                         spilling); 0: the compiler's choice (default).
  */
 typedef struct {
     int32_t clique_chunk;
@@ -329,7 +351,7 @@ typedef struct {
     int32_t hub_min_degree;
     int32_t hub_max;
     int32_t batched_split_grain;
-    int32_t pad;
+    int32_t batched_regcap;
 } pg_tuning;
 
 /* Outcome of pg_autotune. */

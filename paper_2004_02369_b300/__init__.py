@@ -12,6 +12,7 @@ CUDA tensor on the caller's stream.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -83,6 +84,7 @@ _lib.pg_batch_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i3
 _lib.pg_count_batch.argtypes = [_vp, _vp, _vp, _vp]
 _lib.pg_free_batch.argtypes = [_vp]
 _lib.pg_free_batch.restype = None
+_lib.pg_count_until.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.POINTER(_i32), _vp]
 _lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_get_tuning.argtypes = [_vp, _vp]
@@ -294,6 +296,32 @@ def count_async(graph: Graph, plans, out, kernel: int = KERNEL_AUTO, stream=None
                             kernel, _stream_ptr(stream)))
 
 
+def count_until(graph: Graph, plan: Plan, target: int, stream=None):
+    """(count, reached): count matches until ``target`` are found.  The count
+    is exact when reached is False, else a partial count >= target."""
+    out = np.zeros(2, dtype=np.uint64)
+    reached = _i32()
+    _check(_lib.pg_count_until(graph.handle, plan.handle, int(target), out.ctypes.data, ctypes.byref(reached),
+                               _stream_ptr(stream)))
+    return _u128(out[0], out[1]), bool(reached.value)
+
+
+def exists(graph: Graph, plan: Plan, stream=None) -> bool:
+    """Whether the graph has at least one match (stops at the first)."""
+    return count_until(graph, plan, 1, stream)[1]
+
+
+def clustering_coefficient_above(graph: Graph, bound: float, stream=None):
+    """Whether the global clustering coefficient 3T / W exceeds ``bound``
+    (Section 3.2.3): W = connected triples = matches of the 3-vertex star,
+    counted exactly first; triangles are then counted only until 3T > bound W.
+    Returns (answer, triangles counted, W)."""
+    wedges = count(graph, [Plan(3, [(0, 1), (0, 2)])], stream)[0]
+    need = max(1, math.floor(bound * wedges / 3) + 1)  # smallest T with 3T > bound * W
+    tri, reached = count_until(graph, Plan(3, [(0, 1), (1, 2), (0, 2)]), need, stream)
+    return reached and 3 * tri > bound * wedges, tri, wedges
+
+
 def match(graph: Graph, plan: Plan, out=None, rank_range=None, stream=None):
     """List the distinct matches of ``plan``'s pattern.
 
@@ -349,10 +377,10 @@ class Tuning(ctypes.Structure):
                 ("clique_heavy_min", ctypes.c_int32), ("batched_warps", ctypes.c_int32),
                 ("batched_chunk", ctypes.c_int32), ("batched_blocks_per_sm", ctypes.c_int32),
                 ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32),
-                ("batched_split_grain", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("batched_split_grain", ctypes.c_int32), ("batched_regcap", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "pad"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class TuneReport(ctypes.Structure):

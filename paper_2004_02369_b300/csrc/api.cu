@@ -388,6 +388,33 @@ extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uin
     return PG_OK;
 }
 
+// ------------------------------------------------------------ existence ----
+
+extern "C" int pg_count_until(pg_graph *g, pg_plan *pl, uint64_t target, uint64_t *count_out, int32_t *reached,
+                              void *stream) {
+    if (!g || !pl || !count_out || !reached) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (target < 1) return pg_set_error(PG_EINVAL, "target must be >= 1");
+    if (pl->h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = pg_plan_upload(pl);
+    if (rc) return rc;
+    rc = pg_ensure_scratch(g, pg_generic_scratch_bytes(g, pl, true), s);
+    if (rc) return rc;
+    unsigned long long *counts = g->ex->tmp_counts;          // (low, high)
+    unsigned long long *stop = g->ex->queues + PG_MAX_QUEUES - 1;
+    PG_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
+    PG_CUDA(cudaMemsetAsync(stop, 0, sizeof(unsigned long long), s));
+    rc = pg_launch_generic(g, pl, counts, 0, true, s, target, stop);
+    if (rc) return rc;
+    unsigned long long host[2];
+    PG_CUDA(cudaMemcpyAsync(host, counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    count_out[0] = host[0];
+    count_out[1] = host[1];
+    *reached = (host[1] != 0 || host[0] >= target) ? 1 : 0;
+    return PG_OK;
+}
+
 // ---------------------------------------------------------------- match ----
 
 extern "C" int pg_match_range(pg_graph *g, pg_plan *pl, int64_t rank_begin, int64_t rank_end, int32_t *out_dev,

@@ -86,8 +86,11 @@ __device__ void count_terms(const BatchArgs &a, const PgTrieNode &C, const int *
         }
 }
 
-template <int W>
-__global__ void __launch_bounds__(W * 32) k_count_batched(BatchArgs a) {
+// W warps per CTA; CAP = 1 limits the kernel to 64 registers per thread
+// (32 / W CTAs per SM: more resident warps to hide the latency of the
+// binary searches, at the price of some spilling).
+template <int W, int CAP>
+__global__ void __launch_bounds__(W * 32, CAP ? 32 / W : 0) k_count_batched(BatchArgs a) {
     __shared__ unsigned long long s_acc[W][2 * kMaxSlots];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -210,12 +213,23 @@ int batched_warps(const pg_graph *g) {
     return (w == 2 || w == 8) ? w : 4;
 }
 
+template <int CAP>
+void batched_kernel(int w, void **fn) {
+    *fn = w == 2 ? (void *)k_count_batched<2, CAP> : w == 4 ? (void *)k_count_batched<4, CAP>
+                                                             : (void *)k_count_batched<8, CAP>;
+}
+
+void *batched_fn(const pg_graph *g) {
+    void *fn = nullptr;
+    if (g->tune.batched_regcap) batched_kernel<1>(batched_warps(g), &fn);
+    else batched_kernel<0>(batched_warps(g), &fn);
+    return fn;
+}
+
 int batched_grid(const pg_graph *g) {
     const int w = batched_warps(g);
     int per_sm = 0;
-    if (w == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched<2>, 64, 0);
-    else if (w == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched<4>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_batched<8>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_fn(g), w * 32, 0);
     if (per_sm < 1) per_sm = 1;
     if (g->tune.batched_blocks_per_sm > 0) per_sm = std::min(per_sm, g->tune.batched_blocks_per_sm);
     return per_sm * g->num_sms;
@@ -636,10 +650,8 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
     if (b->n_roots > 0) {
         PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
-        const int w = batched_warps(g), grid = batched_grid(g);
-        if (w == 2) k_count_batched<2><<<grid, 64, 0, s>>>(a);
-        else if (w == 4) k_count_batched<4><<<grid, 128, 0, s>>>(a);
-        else k_count_batched<8><<<grid, 256, 0, s>>>(a);
+        void *args[] = {&a};
+        PG_CUDA(cudaLaunchKernel(batched_fn(g), dim3(batched_grid(g)), dim3(batched_warps(g) * 32), args, 0, s));
         PG_CUDA(cudaGetLastError());
     }
     if (b->clique_kmax) {

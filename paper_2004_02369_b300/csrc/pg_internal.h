@@ -61,6 +61,7 @@ inline pg_tuning pg_default_tuning() {
     t.hub_min_degree = PG_HUB_MIN_DEGREE;
     t.hub_max = PG_MAX_HUBS;
     t.batched_split_grain = 512;
+    t.batched_regcap = 0;
     return t;
 }
 
@@ -138,8 +139,10 @@ int pg_plan_upload(pg_plan *p);
 
 // count_generic.cu (persistent = dynamic task queue over a resident grid;
 // otherwise one warp per task, one launch per pattern)
+// target > 0: existence mode, stop once the count reaches target (*stop = 1)
 int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev,
-                      int queue_slot, bool persistent, cudaStream_t s);
+                      int queue_slot, bool persistent, cudaStream_t s,
+                      unsigned long long target = 0, unsigned long long *stop = nullptr);
 size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persistent);
 // per-warp level buffers of a level program (offsets per level, total ints)
 long long pg_level_layout(const pg_graph *g, const std::vector<PgOrder> &orders, bool listing, long long *off);
