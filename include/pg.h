@@ -79,6 +79,39 @@ typedef struct {
     int32_t vertex_induced;
 } pg_pattern_desc;
 
+/* Pattern-set construction from descriptions and element access (see the
+ * pattern generators below). */
+typedef struct pg_pattern_set pg_pattern_set;
+int pg_patterns_from(const pg_pattern_desc *descs, int64_t n, pg_pattern_set **out);
+int pg_patterns_get(const pg_pattern_set *s, int64_t i, int32_t *k, int32_t *n_edges, int32_t *edges,
+                    int32_t *vertex_induced);
+
+/*
+ * Pattern generators (Section 3.1, "Pattern Interface" figure:
+ * generateAllVertexInduced, generateAllEdgeInduced, extendByVertex,
+ * extendByEdge).  A pattern set is a host object holding unlabeled patterns
+ * without anti-edges or anti-vertices, one per isomorphism class.
+ *   pg_patterns_all     vertex_induced = 1: every connected pattern on
+ *                       `size` vertices (1..7), flagged vertex-induced;
+ *                       0: every connected pattern with `size` edges (1..7),
+ *                       edge-induced.
+ *   pg_patterns_from    a set from n descriptions (isomorphic ones merged).
+ *   pg_patterns_extend  by_vertex = 1: add one vertex joined to any
+ *                       non-empty subset of a pattern's vertices; 0: add one
+ *                       edge between two non-adjacent vertices or to a new
+ *                       vertex.  Results over all input patterns, merged by
+ *                       isomorphism; patterns already at 8 vertices only get
+ *                       edges.  The vertex-induced flag is kept.
+ *   pg_patterns_get     pattern i: k, its edges as pairs u < v into `edges`
+ *                       (room for 2 * 28 ints), and the flag.
+ * Host only.  Errors: PG_EINVAL (size out of range, labeled or anti-edged
+ * input, index out of range), PG_ENOMEM.
+ */
+int pg_patterns_all(int32_t size, int32_t vertex_induced, pg_pattern_set **out);
+int pg_patterns_extend(const pg_pattern_set *in, int32_t by_vertex, pg_pattern_set **out);
+int pg_patterns_size(const pg_pattern_set *s, int64_t *n);
+void pg_free_patterns(pg_pattern_set *s);
+
 /* Graph facts after loading (all counts of the undirected simple graph). */
 typedef struct {
     int64_t n;           /* vertices */

@@ -84,6 +84,13 @@ _lib.pg_batch_get_info.argtypes = [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i3
 _lib.pg_count_batch.argtypes = [_vp, _vp, _vp, _vp]
 _lib.pg_free_batch.argtypes = [_vp]
 _lib.pg_free_batch.restype = None
+_lib.pg_patterns_all.argtypes = [_i32, _i32, ctypes.POINTER(_vp)]
+_lib.pg_patterns_from.argtypes = [_vp, _i64, ctypes.POINTER(_vp)]
+_lib.pg_patterns_extend.argtypes = [_vp, _i32, ctypes.POINTER(_vp)]
+_lib.pg_patterns_size.argtypes = [_vp, ctypes.POINTER(_i64)]
+_lib.pg_patterns_get.argtypes = [_vp, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp, ctypes.POINTER(_i32)]
+_lib.pg_free_patterns.argtypes = [_vp]
+_lib.pg_free_patterns.restype = None
 _lib.pg_count_until.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.POINTER(_i32), _vp]
 _lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
@@ -294,6 +301,54 @@ def count_async(graph: Graph, plans, out, kernel: int = KERNEL_AUTO, stream=None
         raise ValueError("out must be a CUDA tensor with 2*len(plans) 64-bit elements")
     _check(_lib.pg_count_ex(graph.handle, _plan_array(plans), len(plans), out.data_ptr(),
                             kernel, _stream_ptr(stream)))
+
+
+def _pattern_list(h) -> list[dict]:
+    try:
+        n = _i64()
+        _check(_lib.pg_patterns_size(h, ctypes.byref(n)))
+        out = []
+        edges = (ctypes.c_int32 * 56)()
+        for i in range(n.value):
+            k, ne, vi = _i32(), _i32(), _i32()
+            _check(_lib.pg_patterns_get(h, i, ctypes.byref(k), ctypes.byref(ne), edges, ctypes.byref(vi)))
+            out.append(dict(k=k.value, edges=[(edges[2 * j], edges[2 * j + 1]) for j in range(ne.value)],
+                            anti_edges=[], labels=None, anti_vertex=None, vertex_induced=bool(vi.value)))
+        return out
+    finally:
+        _lib.pg_free_patterns(h)
+
+
+def generate_all(size: int, vertex_induced: bool = True) -> list[dict]:
+    """Every connected pattern with ``size`` vertices (vertex-induced) or
+    ``size`` edges (edge-induced), one per isomorphism class."""
+    h = _vp()
+    _check(_lib.pg_patterns_all(int(size), 1 if vertex_induced else 0, ctypes.byref(h)))
+    return _pattern_list(h)
+
+
+def extend(patterns, by_vertex: bool) -> list[dict]:
+    """extendByVertex / extendByEdge of a list of unlabeled pattern dicts."""
+    patterns = list(patterns)
+    keep = []
+    descs = (_PatternDesc * max(len(patterns), 1))()
+    for i, p in enumerate(patterns):
+        e = np.ascontiguousarray(np.asarray(p["edges"], dtype=np.int32).reshape(-1))
+        a = np.ascontiguousarray(np.asarray(p.get("anti_edges", []), dtype=np.int32).reshape(-1))
+        lab = None if p.get("labels") is None else np.ascontiguousarray(p["labels"], dtype=np.int32)
+        av = None if p.get("anti_vertex") is None else np.ascontiguousarray(p["anti_vertex"], dtype=np.uint8)
+        keep += [e, a, lab, av]
+        descs[i] = _PatternDesc(int(p["k"]), e.size // 2, e.ctypes.data if e.size else None, a.size // 2,
+                                a.ctypes.data if a.size else None, None if lab is None else lab.ctypes.data,
+                                None if av is None else av.ctypes.data, 1 if p.get("vertex_induced") else 0)
+    src = _vp()
+    _check(_lib.pg_patterns_from(descs, len(patterns), ctypes.byref(src)))
+    try:
+        h = _vp()
+        _check(_lib.pg_patterns_extend(src, 1 if by_vertex else 0, ctypes.byref(h)))
+    finally:
+        _lib.pg_free_patterns(src)
+    return _pattern_list(h)
 
 
 def count_until(graph: Graph, plan: Plan, target: int, stream=None):
