@@ -462,12 +462,14 @@ def run_motif5(args):
     fused = _events_ms(lambda: pg.count_batch(G, b, out), stream)
     counts = pg.decode_counts(out)
     o = torch.zeros(2, dtype=torch.int64, device="cuda")
-    sep = 0.0
-    for pl in plans:
-        sep += _events_ms(lambda: pg.count_async(G, [pl], o, kernel=pg.KERNEL_GENERIC), stream)
+    per = []
+    for p, pl in zip(pats, plans):
+        per.append({"edges": p["edges"], "count": counts[len(per)],
+                    "ms": _events_ms(lambda: pg.count_async(G, [pl], o, kernel=pg.KERNEL_GENERIC), stream)})
+    sep = sum(x["ms"] for x in per)
     print(json.dumps({"workload": "motif5_induced_rmat_scale12_ef16", "data": "synthetic", "n_gpus": 1,
                       "n": g.n, "m": g.m, "patterns": len(plans), "fused_batched_ms": fused,
-                      "separate_launches_ms": sep, "matches": sum(counts),
+                      "separate_launches_ms": sep, "per_pattern_interpreter": per, "matches": sum(counts),
                       "matches_per_s": sum(counts) / (fused / 1e3)}), flush=True)
     return 0
 
