@@ -464,6 +464,27 @@ int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *o
            int64_t *n_frequent, void *stream);
 
 /*
+ * pg_labeled_motif3 - labeled 3-motifs with label discovery (the paper's
+ * labeled motif workload, Section 6; labels discovered from the matches,
+ * Section 3.2.1): the number of vertex-induced matches of every labeled
+ * triangle and wedge present in the graph.
+ *   out        host array of `capacity` records, filled in no particular
+ *              order: shape PG_FSM_TRIANGLE with labels (a, b, c) sorted, or
+ *              PG_FSM_WEDGE with labels (centre, x, y), x <= y; count as a
+ *              128-bit (low, high) pair.  Only nonzero counts are listed.
+ *   n_out      host: number of records (exact even when capacity is short).
+ * Needs a labeled graph with labels 0..31.  Synchronous; allocates its
+ * tables.  Errors: PG_EINVAL (unlabeled graph), PG_EUNSUPPORTED (a label
+ * above 31), PG_ETRUNC (capacity too small), PG_ENOMEM, PG_EDEVICE.
+ */
+typedef struct {
+    int32_t shape;
+    int32_t labels[3];
+    uint64_t count_lo, count_hi;
+} pg_labeled_count;
+int pg_labeled_motif3(pg_graph *g, pg_labeled_count *out, int64_t capacity, int64_t *n_out, void *stream);
+
+/*
  * Serving: a request loop over a resident graph.  Queries are submitted at
  * any time from any host thread; a worker thread admits waiting queries into
  * batches whenever one of n_streams streams is free and the batch's scratch

@@ -91,6 +91,7 @@ _lib.pg_patterns_size.argtypes = [_vp, ctypes.POINTER(_i64)]
 _lib.pg_patterns_get.argtypes = [_vp, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp, ctypes.POINTER(_i32)]
 _lib.pg_free_patterns.argtypes = [_vp]
 _lib.pg_free_patterns.restype = None
+_lib.pg_labeled_motif3.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_count_until.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.POINTER(_i32), _vp]
 _lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
@@ -501,6 +502,27 @@ def fsm(graph: Graph, threshold: int, max_edges: int = 3, stream=None) -> dict:
         r = arr[i]
         out[(FSM_SHAPE_NAMES[r.shape], tuple(r.labels[j] for j in range(width[r.shape])))] = int(r.support)
     return out
+
+
+class LabeledCount(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("labels", ctypes.c_int32 * 3),
+                ("count_lo", ctypes.c_uint64), ("count_hi", ctypes.c_uint64)]
+
+
+def labeled_motif3(graph: Graph, stream=None) -> dict:
+    """Vertex-induced labeled 3-motif counts with label discovery:
+    {("triangle", (a, b, c)): n, ("wedge", (centre, x, y)): n}, nonzero only."""
+    cap = 4096
+    while True:
+        arr = (LabeledCount * cap)()
+        n = _i64()
+        rc = _lib.pg_labeled_motif3(graph.handle, arr, cap, ctypes.byref(n), _stream_ptr(stream))
+        if rc == PG_ETRUNC:
+            cap = int(n.value) + 1
+            continue
+        _check(rc)
+        break
+    return {(FSM_SHAPE_NAMES[r.shape], tuple(r.labels)): _u128(r.count_lo, r.count_hi) for r in arr[:n.value]}
 
 
 class ServerConfig(ctypes.Structure):

@@ -163,6 +163,9 @@ size_t pg_clique_slab_bytes(const pg_graph *g);
 int pg_fsm_run(pg_graph *g, int max_edges, unsigned long long threshold, pg_fsm_pattern *out, int64_t capacity,
                int64_t *n_frequent, cudaStream_t s);
 
+// labeled_motifs.cu
+int pg_labeled_motif3_run(pg_graph *g, pg_labeled_count *out, int64_t capacity, int64_t *n_out, cudaStream_t s);
+
 // count_batched.cu: many plans, one launch over a shared prefix tree
 int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out);
 int pg_batch_build_trie(pg_batch *b);
