@@ -367,23 +367,37 @@ int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out
         bool expanded = false;
         // room for this plan's terms while keeping one slot per later plan
         const int room = kMaxSlots - (int)bb->slot_plans.size() - (n_plans - p - 1);
-        if ((flags & PG_BATCH_EXPAND_ANTI) && !anti.empty() && !has_anti_vertex && anti.size() <= 6 &&
-            room >= (1 << anti.size())) {
-            // signed terms, merged by isomorphism class
-            std::map<int, long long> coef;
-            bool ok = true;
-            for (unsigned T = 0; T < (1u << anti.size()) && ok; ++T) {
+        long long perms = 1;
+        for (int i = 2; i <= h.pat.k; ++i) perms *= i;
+        // host cost of classifying the 2^|A| terms: at most about 5M permutations
+        if ((flags & PG_BATCH_EXPAND_ANTI) && !anti.empty() && !has_anti_vertex && anti.size() <= 10 &&
+            (perms << anti.size()) <= 5000000) {
+            // signed terms merged by isomorphism class first; only classes
+            // whose coefficients do not cancel need a slot
+            std::map<std::vector<int>, std::pair<long long, PgPattern>> terms;
+            for (unsigned T = 0; T < (1u << anti.size()); ++T) {
                 PgPattern q = h.pat;
                 for (size_t i = 0; i < anti.size(); ++i)
                     q.rel[anti[i].first][anti[i].second] = q.rel[anti[i].second][anti[i].first] =
                         (T >> i & 1) ? 1 : 0;
-                int slot;
-                int rc = slot_for(q, false, nullptr, &slot);
-                if (rc == PG_EUNSUPPORTED) { ok = false; break; }
-                if (rc) { pg_batch_free(bb); return rc; }
-                coef[slot] += (__builtin_popcount(T) & 1) ? -1 : 1;
+                std::vector<int> key = canonical(q);
+                key.push_back(1);
+                auto it = terms.find(key);
+                if (it == terms.end()) it = terms.emplace(key, std::make_pair(0ll, q)).first;
+                it->second.first += (__builtin_popcount(T) & 1) ? -1 : 1;
             }
-            if (ok) {
+            int new_slots = 0;
+            for (auto &kv : terms)
+                if (kv.second.first && !slot_of.count(kv.first)) ++new_slots;
+            if (new_slots <= room) {
+                std::map<int, long long> coef;
+                for (auto &kv : terms) {
+                    if (!kv.second.first) continue;
+                    int slot;
+                    int rc = slot_for(kv.second.second, false, nullptr, &slot);
+                    if (rc) { pg_batch_free(bb); return rc == PG_EUNSUPPORTED ? pg_set_error(rc, "batch slots exhausted") : rc; }
+                    coef[slot] += kv.second.first;
+                }
                 for (auto &kv : coef)
                     if (kv.second) {
                         bb->term_slot.push_back(kv.first);
@@ -391,9 +405,6 @@ int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out
                     }
                 bb->out_div.push_back(h.aut);
                 expanded = true;
-            } else {
-                bb->term_slot.resize(bb->out_first.back());
-                bb->term_coef.resize(bb->out_first.back());
             }
         }
         if (!expanded) {
