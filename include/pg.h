@@ -373,6 +373,10 @@ void pg_free_batch(pg_batch *b);
  *   batched_regcap        1: the batched kernel variant limited to 64
  *                         registers per thread (more resident warps, some
  *                         spilling); 0: the compiler's choice (default).
+ *   clique_min_blocks     k-clique kernel variant: 3 CTAs per SM (80
+ *                         registers, default) or 4 (64 registers, some
+ *                         spilling).
+ *   pad                   0.
  */
 typedef struct {
     int32_t clique_chunk;
@@ -385,6 +389,8 @@ typedef struct {
     int32_t hub_max;
     int32_t batched_split_grain;
     int32_t batched_regcap;
+    int32_t clique_min_blocks;
+    int32_t pad;
 } pg_tuning;
 
 /* Outcome of pg_autotune. */

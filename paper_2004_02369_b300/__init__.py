@@ -433,10 +433,11 @@ class Tuning(ctypes.Structure):
                 ("clique_heavy_min", ctypes.c_int32), ("batched_warps", ctypes.c_int32),
                 ("batched_chunk", ctypes.c_int32), ("batched_blocks_per_sm", ctypes.c_int32),
                 ("hub_min_degree", ctypes.c_int32), ("hub_max", ctypes.c_int32),
-                ("batched_split_grain", ctypes.c_int32), ("batched_regcap", ctypes.c_int32)]
+                ("batched_split_grain", ctypes.c_int32), ("batched_regcap", ctypes.c_int32),
+                ("clique_min_blocks", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "pad"}
 
 
 class TuneReport(ctypes.Structure):

@@ -42,6 +42,8 @@ int check_tuning(const pg_tuning &t) {
     if (t.batched_chunk < 1 || t.batched_chunk > 64) return pg_set_error(PG_EINVAL, "batched_chunk must be 1..64");
     if (t.hub_min_degree < 1 || t.hub_max < 0 || t.hub_max > 65536)
         return pg_set_error(PG_EINVAL, "hub_min_degree must be >= 1 and hub_max 0..65536");
+    if (t.clique_min_blocks != 3 && t.clique_min_blocks != 4)
+        return pg_set_error(PG_EINVAL, "clique_min_blocks must be 3 or 4");
     if (t.batched_regcap != 0 && t.batched_regcap != 1) return pg_set_error(PG_EINVAL, "batched_regcap must be 0 or 1");
     if (t.batched_split_grain != 0 && t.batched_split_grain < 16)
         return pg_set_error(PG_EINVAL, "batched_split_grain must be 0 or >= 16");
@@ -130,6 +132,7 @@ extern "C" int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         {&pg_tuning::clique_heavy_min, {16, 32, 48, 64}},
         {&pg_tuning::clique_chunk, {1, 2, 4, 8, 16}},
         {&pg_tuning::clique_blocks_per_sm, {1, 2, 0}},
+        {&pg_tuning::clique_min_blocks, {3, 4}},
     };
     if (kernel == PG_KERNEL_BATCHED) {
         knobs.push_back({&pg_tuning::batched_split_grain, {0, 128, 512, 2048}});

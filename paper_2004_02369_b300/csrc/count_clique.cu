@@ -326,7 +326,10 @@ __device__ __forceinline__ void drain(const Tile &t, Walker &wk, int kmax, int l
     wk.used = 0;
 }
 
-__global__ void __launch_bounds__(kBlock, 3) k_count_clique(CliqueArgs a) {
+// MINB CTAs per SM: 3 (80 registers) or 4 (64 registers, some spilling;
+// more resident warps against the fixed-latency dependency stalls).
+template <int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     extern __shared__ __align__(16) unsigned smem[];
     int *ctl = (int *)smem;
     unsigned *region = smem + kCtl;
@@ -458,14 +461,19 @@ Layout layout_for(const pg_graph *g) {
     return L;
 }
 
+void *clique_fn(const pg_graph *g) {
+    return g->tune.clique_min_blocks == 4 ? (void *)k_count_clique<4> : (void *)k_count_clique<3>;
+}
+
 int clique_grid(const pg_graph *g, size_t smem) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_count_clique, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_count_clique<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_count_clique<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_clique, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clique_fn(g), kBlock, smem);
     if (per_sm < 1) per_sm = 1;
     if (g->tune.clique_blocks_per_sm > 0) per_sm = std::min(per_sm, g->tune.clique_blocks_per_sm);
     return per_sm * g->num_sms;
@@ -496,7 +504,8 @@ int launch(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, unsi
     if (a.slab_words && blocks > max_slabs) blocks = max_slabs;
     if (blocks < 1) return pg_set_error(PG_EINVAL, "scratch holds no slab for a single block");
     PG_CUDA(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s));
-    k_count_clique<<<(unsigned)blocks, kBlock, L.smem_bytes, s>>>(a);
+    void *args[] = {&a};
+    PG_CUDA(cudaLaunchKernel(clique_fn(g), dim3((unsigned)blocks), dim3(kBlock), args, L.smem_bytes, s));
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }

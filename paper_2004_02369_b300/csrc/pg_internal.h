@@ -62,6 +62,8 @@ inline pg_tuning pg_default_tuning() {
     t.hub_max = PG_MAX_HUBS;
     t.batched_split_grain = 512;
     t.batched_regcap = 0;
+    t.clique_min_blocks = 3;
+    t.pad = 0;
     return t;
 }
 
