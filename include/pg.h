@@ -22,6 +22,11 @@
  *  - Vertex ids are int32 (n < 2^31); adjacency offsets are int64.
  *  - The library allocates its own device memory with cudaMalloc for graphs,
  *    plans and scratch, and frees it in the pg_free_* calls.
+ *  - One graph handle holds one scratch arena and one set of work-queue and
+ *    count words: calls on the same graph must be ordered (one stream, or
+ *    synchronised between streams).  For concurrent queries on one resident
+ *    graph use the server (pg_server_*), which gives each of its streams its
+ *    own arena, or load the graph once per stream.
  */
 #ifndef PG_H
 #define PG_H
