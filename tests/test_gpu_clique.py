@@ -77,6 +77,10 @@ def test_clique_full_chunglu_1m(pg):
     G = pg.Graph.from_synth(g)
     got = _count(pg, G, [3, 4, 5], pg.KERNEL_CLIQUE)
     assert got == [int(gold["3-clique"]), int(gold["4-clique"]), int(gold["5-clique"])]
+    # the launch configuration the benchmark times: parameters autotuned on
+    # this graph for the 4- and 5-clique plans, then counted
+    pg.autotune(G, [pg.Plan(k, sg.clique_edges(k)) for k in (4, 5)])
+    assert _count(pg, G, [4, 5], pg.KERNEL_AUTO) == [int(gold["4-clique"]), int(gold["5-clique"])]
     # sampled outputs: start-vertex subsets the oracle lists one by one agree
     # with the total through the partition identity
     assert got[0] == oracle.triangles(g)
