@@ -47,7 +47,8 @@ def workload_config(g):
 # --------------------------------------------------------------- clocks ----
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """Clock / throttle-reason sampling during the timed region: NVML in
+    process, else nvidia-smi.  Reads settings only; changes none."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -55,10 +56,83 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
+        self.nvml = None
         self.proc = None
         self.lines: list[str] = []
 
+    def _start_nvml(self) -> bool:
+        """In-process NVML sampling every 20 ms (enough samples even in a
+        sub-second timed region); the GPU is the one CUDA sees, found by its
+        PCI bus id.  Returns False (nothing started) on any NVML problem."""
+        try:
+            import pynvml
+            import torch
+            pynvml.nvmlInit()
+        except Exception:
+            return False
+        try:
+            p = torch.cuda.get_device_properties(self.gpu)
+            try:
+                h = pynvml.nvmlDeviceGetHandleByPciBusId(
+                    f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0")
+            except Exception:
+                h = pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
+            reasons = None  # the newer name first; older drivers only have the second
+            for name in ("nvmlDeviceGetCurrentClocksEventReasons", "nvmlDeviceGetCurrentClocksThrottleReasons"):
+                fn = getattr(pynvml, name, None)
+                try:
+                    if fn is not None:
+                        fn(h)
+                        reasons = fn
+                        break
+                except Exception:
+                    continue
+            if reasons is None:
+                raise RuntimeError("no clock-reason query")
+            smax = float(pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM))
+            pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+        except Exception:
+            try:
+                pynvml.nvmlShutdown()
+            except Exception:
+                pass
+            return False
+        self.nvml_samples: list[tuple[float, int]] = []
+        self.nvml_stop = threading.Event()
+
+        def loop():
+            while not self.nvml_stop.is_set():
+                try:
+                    self.nvml_samples.append((float(pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)),
+                                              int(reasons(h))))
+                except Exception:
+                    break
+                self.nvml_stop.wait(0.02)
+
+        self.nvml = (pynvml, smax)
+        self.thread = threading.Thread(target=loop, daemon=True)
+        self.thread.start()
+        return True
+
+    def _stop_nvml(self) -> dict:
+        pynvml, smax = self.nvml
+        self.nvml_stop.set()
+        self.thread.join(timeout=5)
+        try:
+            pynvml.nvmlShutdown()
+        except Exception:
+            pass
+        bits = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+        sm = [c for c, _ in self.nvml_samples]
+        seen = set()
+        for _, r in self.nvml_samples:
+            seen |= {name for name, b in bits.items() if r & b}
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(seen),
+                "samples": len(sm), "source": "nvml, 20 ms"}
+
     def start(self):
+        if self._start_nvml():
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -74,6 +148,8 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self) -> dict:
+        if self.nvml is not None:
+            return self._stop_nvml()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -96,7 +172,7 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 200 ms"}
 
 
 # --------------------------------------------------------------- helpers ---
@@ -165,13 +241,13 @@ def sum_over_ranks(world, x: float, device=None) -> float:
 
 # --------------------------------------------------------------- CPU arm ---
 
-def cpu_oracle_rate(g, steps: int, seed: int = 7):
-    """Oracle lister on `steps` seeded samples of start vertices."""
+def cpu_oracle_rate(g, steps: int, seed: int = 7, sources: int = CPU_SAMPLE_SOURCES):
+    """Oracle lister on `steps` seeded samples of `sources` start vertices."""
     import oracle
     rng = np.random.default_rng(seed)
     total, secs = 0, 0.0
     for _ in range(steps):
-        src = np.sort(rng.choice(g.n, CPU_SAMPLE_SOURCES, replace=False)).astype(np.int32)
+        src = np.sort(rng.choice(g.n, sources, replace=False)).astype(np.int32)
         t = time.perf_counter()
         for k in CLIQUE_SIZES:
             total += oracle.kcliques(g, k, sources=src)
