@@ -136,18 +136,29 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
             self.proc = None
 
+    def wait_ready(self, timeout: float = 2.0):
+        """Wait (bounded) until the sampler has produced its first sample."""
+        t = time.perf_counter()
+        while time.perf_counter() - t < timeout:
+            if self.nvml is not None or self.proc is None or self.lines or self.proc.poll() is not None:
+                return
+            time.sleep(0.01)
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self) -> dict:
+    def stop(self, window=None) -> dict:
+        """Stop sampling; with window = (t0, t1) in time.perf_counter()
+        seconds keep the samples that arrived in it (plus a 0.25 s grace for
+        the output delay), or every sample if none did."""
         if self.nvml is not None:
             return self._stop_nvml()
         if self.proc is None:
@@ -159,7 +170,11 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lines = [ln for t, ln in self.lines if window is None or window[0] <= t <= window[1] + 0.25]
+        in_window = bool(lines) and window is not None
+        if not lines:
+            lines = [ln for _, ln in self.lines]
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -172,7 +187,8 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 200 ms"}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 50 ms",
+                "window": "timed region" if in_window else "whole sampling run"}
 
 
 # --------------------------------------------------------------- helpers ---
@@ -299,13 +315,13 @@ def run_ours(args):
     # persistent variant); the search is not part of the timed steps
     tune = pg.autotune(G, plans, stream=stream) if args.autotune and args.kernel == 0 else None
 
+    clocks = ClockSampler(local)  # running before the timed region starts
+    clocks.start()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     expect = pg.decode_counts(counts)
-
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks.wait_ready()
     times = []
     barrier(world)
     torch.cuda.synchronize()
@@ -321,7 +337,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - t0
-    clk = clocks.stop()
+    clk = clocks.stop(window=(t0, t0 + wall))
     ms = [s.elapsed_time(e) for s, e in times]
     got = pg.decode_counts(counts)
     if got != expect:
