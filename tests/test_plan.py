@@ -173,3 +173,20 @@ def test_invalid_patterns_rejected():
         pg.Plan(3, [(0, 1), (1, 2)], anti_vertex=[0, 0, 1])
     with pytest.raises(pg.PgError):  # labeled anti-vertex
         pg.Plan(3, [(0, 1)], anti_edges=[(2, 0)], anti_vertex=[0, 0, 1], labels=[-1, -1, 2])
+
+
+def test_every_generated_pattern_plans_match_oracle():
+    """The counting and listing programs of every connected pattern the
+    generators produce (21 induced 5-vertex, 112 induced 6-vertex, and all
+    edge-induced ones with up to 5 edges) count what the oracle counts."""
+    pg = _pg()
+    pats = (pg.generate_all(5) + pg.generate_all(6)
+            + [p for e in range(1, 6) for p in pg.generate_all(e, vertex_induced=False)])
+    graphs = [sg.erdos_renyi(13, 0.45, 701), sg.chung_lu(24, 70, 2.1, 9.0, 702)]
+    for g in graphs:
+        for p in pats:
+            want = oracle.count(g, p)
+            got, _ = planeval.count(g, p)
+            assert got == want, (p, g.n)
+            got, _ = planeval.count(g, p, listing=True)
+            assert got == want, (p, g.n, "listing")
