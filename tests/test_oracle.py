@@ -427,3 +427,18 @@ def test_fsm_antimonotone():
             a, b, c, d = labels
             assert s <= sup[("wedge", (b, min(a, c), max(a, c)))]
             assert s <= sup[("wedge", (c, min(b, d), max(b, d)))]
+
+
+def test_labeled_counts_sum_to_unlabeled_closed_forms():
+    """Summed over every label combination, labeled triangle and induced
+    wedge counts give trace(A^3)/6 and sum C(d,2) - 3T: pins the oracle's
+    label filtering, which the labeled 3-motif parity relies on."""
+    g = sg.chung_lu(120, 500, 2.1, 25.0, 801)
+    g.labels = sg.uniform_labels(g.n, 3, 802)
+    tri = sum(oracle.count(g, sg.pattern(3, sg.clique_edges(3), labels=list(t)))
+              for t in itertools.combinations_with_replacement(range(3), 3))
+    assert tri == oracle.triangles(g)
+    wedges = sum(oracle.count(g, sg.pattern(3, [(0, 1), (1, 2)], labels=[x, c, y], vertex_induced=True))
+                 for c in range(3) for x, y in itertools.combinations_with_replacement(range(3), 2))
+    d = np.diff(g.offsets)
+    assert wedges == int(sum(comb(int(x), 2) for x in d)) - 3 * oracle.triangles(g)

@@ -78,3 +78,14 @@ def test_generator_arguments_checked(pg):
             pg.generate_all(*bad)
     with pytest.raises(pg.PgError):
         pg.extend([sg.pattern(3, sg.chain_edges(3), labels=[1, 1, 1])], by_vertex=True)
+
+
+def test_extension_chains_reach_every_size(pg):
+    """extendByEdge of all e-edge patterns gives all (e+1)-edge patterns;
+    extendByVertex of all k-vertex patterns gives all (k+1)-vertex ones."""
+    for e in range(1, 6):
+        ext = pg.extend(pg.generate_all(e, vertex_induced=False), by_vertex=False)
+        assert len(ext) == BY_EDGES[e]
+        assert len(_classes(ext + pg.generate_all(e + 1, vertex_induced=False))) == BY_EDGES[e]
+    for k in range(1, 6):
+        assert len(pg.extend(pg.generate_all(k), by_vertex=True)) == BY_VERTICES[k]
