@@ -313,7 +313,12 @@ def run_ours(args):
 
     # launch parameters chosen by measurement on this graph (the autotuned
     # persistent variant); the search is not part of the timed steps
-    tune = pg.autotune(G, plans, stream=stream) if args.autotune and args.kernel == 0 else None
+    if args.tuning_json:
+        fixed = json.loads(open(args.tuning_json).read() if os.path.exists(args.tuning_json) else args.tuning_json)
+        pg.set_tuning(G, stream=stream, **fixed)
+        tune = {"chosen": pg.get_tuning(G), "fixed": True}
+    else:
+        tune = pg.autotune(G, plans, stream=stream) if args.autotune and args.kernel == 0 else None
 
     clocks = ClockSampler(local)  # running before the timed region starts
     clocks.start()
@@ -742,6 +747,8 @@ def main():
     ap.add_argument("--serve-n", type=int, default=300, help="queries per arrival rate")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
     ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")
+    ap.add_argument("--tuning-json", default=None,
+                    help="launch parameters (JSON object or file) applied instead of the autotuner")
     ap.add_argument("--only-kernel", action="store_true",
                     help="time the counting steps only (for profiler runs)")
     ap.add_argument("--traffic", type=float, default=None,

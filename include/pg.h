@@ -47,6 +47,7 @@ extern "C" {
 #define PG_EUNSUPPORTED 6 /* valid request that this build does not implement */
 
 #define PG_MAX_PATTERN 8 /* pattern vertices, regular plus anti-vertices */
+#define PG_MAX_CLIQUE 16 /* k-cliques (unlabeled complete patterns) up to this size */
 
 typedef struct pg_graph pg_graph; /* device-resident data graph (opaque) */
 typedef struct pg_plan pg_plan;   /* compiled exploration plan (opaque, host) */
@@ -190,10 +191,15 @@ void pg_free_graph(pg_graph *g);
  * connected vertex cover as the core, matching orders, and the per-level set
  * operations of the core and of the non-core completion.  Host only; touches
  * no graph.
- * Errors: PG_EINVAL (k outside 1..8, self loop, pair both edge and anti-edge,
- * regular vertices not connected by edges, anti-vertex with a true edge or
- * with no anti-edge), PG_EUNSUPPORTED (anti-vertices: not in this build),
- * PG_ENOMEM.
+ * A pattern of 9..PG_MAX_CLIQUE vertices is accepted only as an unlabeled
+ * clique (every pair an edge; no anti-edges, labels or anti-vertices): its
+ * plan is the clique's total order u0 < ... < u(k-1) and it runs on the
+ * k-clique kernel only (pg_count, pg_count_ex with PG_KERNEL_AUTO or
+ * PG_KERNEL_CLIQUE, pg_count_until, pg_autotune); every other call refuses
+ * it with PG_EUNSUPPORTED.
+ * Errors: PG_EINVAL (k outside 1..8 for non-cliques or above PG_MAX_CLIQUE,
+ * self loop, pair both edge and anti-edge, regular vertices not connected by
+ * edges, anti-vertex with a true edge or with no anti-edge), PG_ENOMEM.
  */
 int pg_compile_pattern(const pg_pattern_desc *desc, pg_plan **out);
 
@@ -218,8 +224,11 @@ void pg_free_plan(pg_plan *p);
  *               counts_out[2i] + 2^64 * counts_out[2i+1] (exact; star counts
  *               on hub-heavy graphs exceed 2^64).
  * Synchronous: returns after the counts are on the host.  Kernel choice is
- * automatic (PG_KERNEL_AUTO).  Errors: PG_EINVAL, PG_ENOMEM, PG_EDEVICE,
- * PG_ETIMEOUT.
+ * automatic (PG_KERNEL_AUTO).  With a work budget on the graph
+ * (pg_set_time_budget) the kernels stop once it is spent and the call returns
+ * PG_ETIMEOUT without counts.  Errors: PG_EINVAL, PG_ENOMEM, PG_EDEVICE,
+ * PG_ETIMEOUT, PG_EUNSUPPORTED (a clique above 8 vertices on a graph with
+ * out-degrees of 65536 or more).
  */
 int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_out,
              void *stream);
@@ -234,6 +243,7 @@ int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *coun
  * Only enqueues work (no host synchronisation, no allocation once the
  * graph's scratch has been sized by a first call with the same plans), so a
  * sequence of calls can be captured in a CUDA graph after one warm-up call.
+ * The graph's work budget does not apply (the call cannot report it).
  */
 int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev,
                 int32_t kernel, void *stream);
@@ -250,12 +260,47 @@ int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *c
  *              before exploration stopped.  Exact when *reached is 0 (the
  *              whole graph was explored); otherwise a partial count >= target.
  *   reached    host: 1 if at least `target` matches exist, else 0.
- * Runs on the plan interpreter (PG_KERNEL_GENERIC).  Synchronous.  Errors:
- * PG_EINVAL (target 0, NULL argument, labeled pattern on an unlabeled
- * graph), PG_ENOMEM, PG_EDEVICE.
+ * Unlabeled cliques (3..PG_MAX_CLIQUE vertices, e.g. the 14-clique existence
+ * query of the paper's evaluation) run on the k-clique kernel, which
+ * publishes its count after every first-level row of the start vertex's
+ * sub-graph and cuts branches too small to reach k; other patterns run on
+ * the plan interpreter (PG_KERNEL_GENERIC).  Honours the graph's work budget
+ * (PG_ETIMEOUT).  Synchronous.  Errors: PG_EINVAL (target 0, NULL argument,
+ * labeled pattern on an unlabeled graph), PG_ENOMEM, PG_EDEVICE, PG_ETIMEOUT.
  */
 int pg_count_until(pg_graph *g, pg_plan *p, uint64_t target, uint64_t *count_out, int32_t *reached,
                    void *stream);
+
+/*
+ * pg_clustering_coefficient_above - the clustering-coefficient program of
+ * Section 3.2.3: whether the global clustering coefficient 3T / W of g
+ * exceeds `bound`, with W = connected triples (3-vertex star matches,
+ * counted exactly) and T = triangles, counted only until 3T > bound * W is
+ * established (pg_count_until).  Outputs (host): *answer 1 or 0;
+ * triangles_out[2] = (low, high) triangles counted before the stop (exact
+ * when *answer is 0); wedges_out[2] = (low, high) W.  The paper counts
+ * "triplets" as twice the star matches; this call uses the standard 3T / W
+ * (1 on a complete graph).  Synchronous.  Errors: PG_EINVAL (NULL argument,
+ * negative or non-finite bound), PG_ENOMEM, PG_EDEVICE, PG_ETIMEOUT.
+ */
+int pg_clustering_coefficient_above(pg_graph *g, double bound, int32_t *answer, uint64_t *triangles_out,
+                                    uint64_t *wedges_out, void *stream);
+
+/*
+ * pg_set_time_budget - device work budget of the synchronous calls on g
+ * (pg_count, pg_count_until, pg_match, pg_match_range): budget_ms > 0 limits
+ * each call's kernels to about that much device time, 0 removes the limit.
+ * The persistent kernels read %globaltimer between tasks and between
+ * first-level candidates, so a launch ends within one such step of the
+ * budget; the call then returns PG_ETIMEOUT and its partial results are
+ * discarded.  The paper has no counterpart (its runtime runs a program to
+ * completion); this bounds a query on a resident graph without killing the
+ * process or the device context.  Host only.  Errors: PG_EINVAL (NULL graph,
+ * negative or non-finite budget).
+ * pg_get_time_budget - the current budget in milliseconds (host double out).
+ */
+int pg_set_time_budget(pg_graph *g, double budget_ms);
+int pg_get_time_budget(const pg_graph *g, double *budget_ms);
 
 /*
  * pg_match - list the distinct matches of one plan's pattern (Section 3.2,
@@ -270,8 +315,10 @@ int pg_count_until(pg_graph *g, pg_plan *p, uint64_t target, uint64_t *count_out
  *   n_total   host uint64: the number of matches, whatever the capacity.
  * Synchronous (returns after *n_total is on the host).  If n_total exceeds
  * capacity the first `capacity` rows are valid, distinct matches and the call
- * returns PG_ETRUNC.  Errors: PG_EINVAL (NULL argument, labeled pattern on
- * an unlabeled graph), PG_ETRUNC, PG_ENOMEM, PG_EDEVICE.
+ * returns PG_ETRUNC.  Honours the graph's work budget (PG_ETIMEOUT; rows
+ * written before the stop are valid matches, the total is not).  Errors:
+ * PG_EINVAL (NULL argument, labeled pattern on an unlabeled graph),
+ * PG_ETRUNC, PG_ENOMEM, PG_EDEVICE, PG_ETIMEOUT.
  */
 int pg_match(pg_graph *g, pg_plan *p, int32_t *out_dev, uint64_t capacity, uint64_t *n_total,
              void *stream);
@@ -305,6 +352,12 @@ int pg_match_range(pg_graph *g, pg_plan *p, int64_t rank_begin, int64_t rank_end
  * device that loads libpg holds it until the process exits).  The first call
  * on a device looks the array's device address up (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * With the CUDA runtime's lazy module loading (its default) that first call
+ * is also when the array's 32 MiB (and the kernel's code) are reserved on
+ * the device: a caller that hands the rest of device memory to a pool
+ * should make one call at start-up, before filling the pool.  The address
+ * is kept for the life of the process; after cudaDeviceReset the library's
+ * state on that device (graphs, this address) is invalid.
  * All calls share the array and each call clears what must start at zero, so
  * calls that overlap on the GPU (other streams, other host threads) race:
  * serialise them.  Asynchronous: only enqueues work on `stream`.
@@ -525,6 +578,11 @@ typedef struct {
     int64_t memory_budget;
     int32_t serial;
     int32_t pad;
+    double query_timeout_s; /* > 0: a query not done this long after its
+                               submission fails with PG_ETIMEOUT (enforced as
+                               the device work budget of its launch, see
+                               pg_set_time_budget; every query of that launch
+                               gets PG_ETIMEOUT); 0: no limit */
 } pg_server_config;
 
 typedef struct {

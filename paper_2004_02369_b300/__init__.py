@@ -12,7 +12,6 @@ CUDA tensor on the caller's stream.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -23,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libpg.so")
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETRUNC, PG_ETIMEOUT, PG_EDEVICE, PG_EUNSUPPORTED = range(7)
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_BATCHED = range(5)
 MAX_PATTERN = 8
+MAX_CLIQUE = 16
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2004_02369_b300/build.py`")
@@ -98,6 +98,9 @@ _lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctyp
 _lib.pg_get_tuning.argtypes = [_vp, _vp]
 _lib.pg_set_tuning.argtypes = [_vp, _vp, _vp]
 _lib.pg_autotune.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
+_lib.pg_set_time_budget.argtypes = [_vp, ctypes.c_double]
+_lib.pg_clustering_coefficient_above.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(_i32), _vp, _vp, _vp]
+_lib.pg_get_time_budget.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
 _lib.pg_last_error.restype = ctypes.c_char_p
 
 
@@ -368,14 +371,26 @@ def exists(graph: Graph, plan: Plan, stream=None) -> bool:
 
 
 def clustering_coefficient_above(graph: Graph, bound: float, stream=None):
-    """Whether the global clustering coefficient 3T / W exceeds ``bound``
-    (Section 3.2.3): W = connected triples = matches of the 3-vertex star,
-    counted exactly first; triangles are then counted only until 3T > bound W.
+    """pg_clustering_coefficient_above: whether 3T / W exceeds ``bound``.
     Returns (answer, triangles counted, W)."""
-    wedges = count(graph, [Plan(3, [(0, 1), (0, 2)])], stream)[0]
-    need = max(1, math.floor(bound * wedges / 3) + 1)  # smallest T with 3T > bound * W
-    tri, reached = count_until(graph, Plan(3, [(0, 1), (1, 2), (0, 2)]), need, stream)
-    return reached and 3 * tri > bound * wedges, tri, wedges
+    ans = _i32()
+    t = np.zeros(2, dtype=np.uint64)
+    w = np.zeros(2, dtype=np.uint64)
+    _check(_lib.pg_clustering_coefficient_above(graph.handle, float(bound), ctypes.byref(ans), t.ctypes.data,
+                                                w.ctypes.data, _stream_ptr(stream)))
+    return bool(ans.value), _u128(t[0], t[1]), _u128(w[0], w[1])
+
+
+def set_time_budget(graph: Graph, budget_ms: float):
+    """Device work budget of the synchronous calls on ``graph`` (0 = none);
+    a call that runs out raises PgError with code PG_ETIMEOUT."""
+    _check(_lib.pg_set_time_budget(graph.handle, float(budget_ms)))
+
+
+def get_time_budget(graph: Graph) -> float:
+    out = ctypes.c_double()
+    _check(_lib.pg_get_time_budget(graph.handle, ctypes.byref(out)))
+    return out.value
 
 
 def match(graph: Graph, plan: Plan, out=None, rank_range=None, stream=None):
@@ -528,7 +543,8 @@ def labeled_motif3(graph: Graph, stream=None) -> dict:
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("memory_budget", ctypes.c_int64), ("serial", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("memory_budget", ctypes.c_int64), ("serial", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("query_timeout_s", ctypes.c_double)]
 
 
 class QueryResult(ctypes.Structure):
@@ -548,9 +564,9 @@ class Server:
     """Request loop over a resident graph (native worker thread, see pg.h)."""
 
     def __init__(self, graph: Graph, n_streams: int = 4, max_batch: int = 32, memory_budget: int = 0,
-                 serial: bool = False):
+                 serial: bool = False, query_timeout_s: float = 0.0):
         self.graph = graph  # keep the graph alive
-        cfg = ServerConfig(n_streams, max_batch, memory_budget, 1 if serial else 0, 0)
+        cfg = ServerConfig(n_streams, max_batch, memory_budget, 1 if serial else 0, 0, float(query_timeout_s))
         h = _vp()
         _check(_lib.pg_server_create(graph.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

@@ -2,6 +2,7 @@
 // dispatch.  No compute happens here; every step of the path runs in the
 // library's kernels.
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <string>
 
@@ -155,10 +156,61 @@ int pg_ensure_scratch(pg_graph *g, size_t bytes, cudaStream_t s) {
 
 // ---------------------------------------------------------------- plans ----
 
+namespace {
+
+std::atomic<uint64_t> g_next_serial{1};
+
+// A pattern above PGP_MAXK vertices is accepted only as an unlabeled clique
+// (every pair an edge, no anti-edges or anti-vertices): its plan is the total
+// order u0 < ... < u(k-1) of Section 4.1 for a clique, run by the k-clique
+// kernel, with no level program for the interpreters.
+int compile_big_clique(const pg_pattern_desc *d, pg_plan **out) {
+    const int k = d->k;
+    if (k > PG_MAX_CLIQUE)
+        return pg_set_error(PG_EINVAL, "pattern size must be 1..8 (unlabeled cliques: up to 16)");
+    const char *why = "patterns above 8 vertices must be unlabeled cliques (up to 16 vertices)";
+    if (d->n_anti > 0 || d->n_edges < 0 || (d->n_edges > 0 && !d->edges)) return pg_set_error(PG_EINVAL, why);
+    for (int u = 0; u < k; ++u) {
+        if (d->labels && d->labels[u] != -1) return pg_set_error(PG_EINVAL, why);
+        if (d->anti_vertex && d->anti_vertex[u]) return pg_set_error(PG_EINVAL, why);
+    }
+    uint32_t adj[PG_MAX_CLIQUE] = {};
+    for (int i = 0; i < d->n_edges; ++i) {
+        const int u = d->edges[2 * i], w = d->edges[2 * i + 1];
+        if (u < 0 || w < 0 || u >= k || w >= k) return pg_set_error(PG_EINVAL, "pattern vertex out of range");
+        if (u == w) return pg_set_error(PG_EINVAL, "self loop in pattern");
+        adj[u] |= 1u << w;
+        adj[w] |= 1u << u;
+    }
+    const uint32_t all = (1u << k) - 1;
+    for (int u = 0; u < k; ++u)
+        if ((adj[u] | (1u << u)) != all) return pg_set_error(PG_EINVAL, why);
+    pg_plan *pl = new (std::nothrow) pg_plan();
+    if (!pl) return pg_set_error(PG_ENOMEM, "host allocation failed");
+    PgPlanHost &h = pl->h;
+    h.pat = PgPattern{};
+    h.big_clique = true;
+    h.is_clique = true;
+    h.clique_k = k;
+    h.n_regular = k;
+    h.aut = 1;
+    for (int i = 2; i <= k; ++i) h.aut *= (uint64_t)i;
+    for (int i = 0; i + 1 < k; ++i) h.po.push_back({i, i + 1});
+    h.core_mask = all & ~1u;
+    h.counted_group = 1;
+    pl->serial = g_next_serial++;
+    pl->kernel_auto = PG_KERNEL_CLIQUE;
+    *out = pl;
+    return PG_OK;
+}
+
+}  // namespace
+
 extern "C" int pg_compile_pattern(const pg_pattern_desc *d, pg_plan **out) {
     if (!d || !out) return pg_set_error(PG_EINVAL, "NULL argument");
     *out = nullptr;
-    if (d->k < 1 || d->k > PG_MAX_PATTERN) return pg_set_error(PG_EINVAL, "pattern size must be 1..8");
+    if (d->k > PG_MAX_PATTERN) return compile_big_clique(d, out);
+    if (d->k < 1) return pg_set_error(PG_EINVAL, "pattern size must be 1..8 (unlabeled cliques: up to 16)");
     PgPattern p;
     p.k = d->k;
     auto add = [&](const int32_t *pairs, int32_t np, uint8_t val) -> int {
@@ -188,8 +240,7 @@ extern "C" int pg_compile_pattern(const pg_pattern_desc *d, pg_plan **out) {
         delete pl;
         return pg_set_error(rc, err);
     }
-    static std::atomic<uint64_t> next_serial{1};
-    pl->serial = next_serial++;
+    pl->serial = g_next_serial++;
     pl->kernel_auto = (pl->h.is_clique && pl->h.pat.k >= 3) ? PG_KERNEL_CLIQUE
                       : pl->h.anti_vertices                  ? PG_KERNEL_GENERIC
                                                              : PG_KERNEL_BATCHED;
@@ -201,7 +252,7 @@ extern "C" int pg_plan_get_info(const pg_plan *pl, pg_plan_info *out) {
     if (!pl || !out) return pg_set_error(PG_EINVAL, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     const PgPlanHost &h = pl->h;
-    out->k = h.pat.k;
+    out->k = pg_plan_size(h);
     out->n_regular = h.n_regular;
     out->automorphisms = h.aut;
     out->n_po = (int32_t)h.po.size();
@@ -227,10 +278,11 @@ extern "C" int pg_plan_describe(const pg_plan *pl, char *buf, int64_t size) {
         for (int i = 0; i < n; ++i) s += (i ? "," : "") + std::to_string(src[i]);
         return s + "]";
     };
-    out += "k=" + std::to_string(h.pat.k) + " aut=" + std::to_string(h.aut) + " core_mask=" +
+    out += "k=" + std::to_string(pg_plan_size(h)) + " aut=" + std::to_string(h.aut) + " core_mask=" +
            std::to_string(h.core_mask) + " orders=" + std::to_string(h.orders.size()) + " po=";
     for (auto &e : h.po) out += "(" + std::to_string(e.first) + "<" + std::to_string(e.second) + ")";
     out += "\n";
+    if (h.big_clique) out += "k-clique above 8 vertices: counted by the k-clique kernel (no level program)\n";
     for (size_t o = 0; o < h.orders.size(); ++o) {
         const PgOrder &ord = h.orders[o];
         out += "order " + std::to_string(o) + ":\n";
@@ -271,27 +323,52 @@ int pg_plan_upload(pg_plan *pl) {
 
 // ---------------------------------------------------------------- count ----
 
-extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev,
-                           int32_t kernel, void *stream) {
-    if (!g || (n_plans > 0 && (!plans || !counts_dev)) || n_plans < 0)
-        return pg_set_error(PG_EINVAL, "NULL argument");
-    if (n_plans > PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "at most 64 plans per call");
-    if (n_plans == 0) return PG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    bool all_clique = true, any_anti_vertex = false;
-    int kmin = PG_MAX_PATTERN + 1, kmax = 0;
+int pg_run_ctl(pg_graph *g, unsigned long long target, cudaStream_t s, PgRunCtl *out) {
+    *out = PgRunCtl{};
+    if (!target && !g->budget_ns) return PG_OK;
+    out->words = g->ex->queues + PG_CTL_WORDS_SLOT;
+    out->target = target;
+    out->budget_ns = g->budget_ns;
+    PG_CUDA(cudaMemsetAsync(out->words, 0, 3 * sizeof(unsigned long long), s));
+    return PG_OK;
+}
+
+int pg_run_ctl_check(const PgRunCtl &ctl, cudaStream_t s) {
+    if (!ctl.words || !ctl.budget_ns) return PG_OK;
+    unsigned long long timed_out = 0;
+    PG_CUDA(cudaMemcpyAsync(&timed_out, ctl.words + 1, sizeof(timed_out), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    if (timed_out) return pg_set_error(PG_ETIMEOUT, "the graph's device work budget ran out; partial results discarded");
+    return PG_OK;
+}
+
+namespace {
+
+// Counting of n_plans plans with one kernel family (see pg_count_ex);
+// ctl: run control of a synchronous caller, or null.
+int count_dispatch(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev, int32_t kernel,
+                   cudaStream_t s, const PgRunCtl *ctl) {
+    bool all_clique = true, any_anti_vertex = false, any_big = false;
+    int kmin = PG_MAX_CLIQUE + 1, kmax = 0;
     for (int i = 0; i < n_plans; ++i) {
         if (!plans[i]) return pg_set_error(PG_EINVAL, "NULL plan");
         const PgPlanHost &h = plans[i]->h;
         if (h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
-        all_clique &= h.is_clique && h.pat.k >= 3;
+        const int k = pg_plan_size(h);
+        all_clique &= h.is_clique && k >= 3;
         any_anti_vertex |= h.anti_vertices;
-        kmin = std::min(kmin, h.pat.k);
-        kmax = std::max(kmax, h.pat.k);
+        any_big |= h.big_clique;
+        kmin = std::min(kmin, k);
+        kmax = std::max(kmax, k);
     }
-    if (all_clique && g->max_out >= 65536) all_clique = false;
+    if (all_clique && g->max_out >= 65536) {
+        if (any_big) return pg_set_error(PG_EUNSUPPORTED, "the k-clique kernel needs out-degrees below 65536");
+        all_clique = false;
+    }
     if (kernel == PG_KERNEL_AUTO)
         kernel = all_clique ? PG_KERNEL_CLIQUE : any_anti_vertex ? PG_KERNEL_GENERIC : PG_KERNEL_BATCHED;
+    if (any_big && kernel != PG_KERNEL_CLIQUE)
+        return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices run on the k-clique kernel only");
     if (any_anti_vertex && kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN)
         return pg_set_error(PG_EUNSUPPORTED, "anti-vertex patterns run on the plan interpreter (PG_KERNEL_GENERIC)");
     if (kernel == PG_KERNEL_CLIQUE && !all_clique)
@@ -313,7 +390,11 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
             g->batch_cache = b;
             g->batch_key = key;
         }
-        return pg_count_batch(g, g->batch_cache, counts_dev, stream);
+        const pg_batch *b = g->batch_cache;
+        int rc = pg_ensure_scratch(g, pg_batch_scratch_bytes(g, b), s);
+        if (rc) return rc;
+        PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * pg_batch_slots(b), s));
+        return pg_launch_batched(g, b, (unsigned long long *)counts_dev, 0, s, ctl);
     }
     size_t need = 0;
     for (int i = 0; i < n_plans; ++i) {
@@ -322,25 +403,49 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         if (kernel == PG_KERNEL_GENERIC) need = std::max(need, pg_generic_scratch_bytes(g, plans[i], true));
         if (kernel == PG_KERNEL_CLIQUE_PLAIN) need = std::max(need, pg_generic_scratch_bytes(g, plans[i], false));
     }
-    if (kernel == PG_KERNEL_CLIQUE) need = pg_clique_scratch_bytes(g);
+    if (kernel == PG_KERNEL_CLIQUE) need = pg_clique_scratch_bytes(g, kmax);
     int rc = pg_ensure_scratch(g, need, s);
     if (rc) return rc;
     PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * n_plans, s));
     if (kernel == PG_KERNEL_CLIQUE) {
         // one launch counts every size kmin..kmax; copy each plan's size out
         PG_CUDA(cudaMemsetAsync(g->ex->tmp_counts, 0, 2 * sizeof(uint64_t) * (kmax - kmin + 1), s));
-        rc = pg_launch_clique(g, kmin, kmax, g->ex->tmp_counts, 0, s);
+        rc = pg_launch_clique(g, kmin, kmax, g->ex->tmp_counts, 0, s, ctl);
         if (rc) return rc;
         for (int i = 0; i < n_plans; ++i)
-            PG_CUDA(cudaMemcpyAsync(counts_dev + 2 * i, g->ex->tmp_counts + 2 * (plans[i]->h.pat.k - kmin),
+            PG_CUDA(cudaMemcpyAsync(counts_dev + 2 * i, g->ex->tmp_counts + 2 * (pg_plan_size(plans[i]->h) - kmin),
                                     2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
         return PG_OK;
     }
+    // one launch per plan, in stream order (each launch resets its queue word)
     for (int i = 0; i < n_plans; ++i) {
-        rc = pg_launch_generic(g, plans[i], (unsigned long long *)counts_dev + 2 * i, i,
-                               kernel == PG_KERNEL_GENERIC, s);
+        rc = pg_launch_generic(g, plans[i], (unsigned long long *)counts_dev + 2 * i, i % 8,
+                               kernel == PG_KERNEL_GENERIC, s, ctl);
         if (rc) return rc;
     }
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_dev,
+                           int32_t kernel, void *stream) {
+    if (!g || (n_plans > 0 && (!plans || !counts_dev)) || n_plans < 0)
+        return pg_set_error(PG_EINVAL, "NULL argument");
+    if (n_plans > PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "at most 64 plans per call");
+    if (n_plans == 0) return PG_OK;
+    return count_dispatch(g, plans, n_plans, counts_dev, kernel, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int pg_set_time_budget(pg_graph *g, double budget_ms) {
+    if (!g || !(budget_ms >= 0.0) || budget_ms > 1e12) return pg_set_error(PG_EINVAL, "bad argument");
+    g->budget_ns = (unsigned long long)(budget_ms * 1e6);
+    return PG_OK;
+}
+
+extern "C" int pg_get_time_budget(const pg_graph *g, double *budget_ms) {
+    if (!g || !budget_ms) return pg_set_error(PG_EINVAL, "NULL argument");
+    *budget_ms = (double)g->budget_ns / 1e6;
     return PG_OK;
 }
 
@@ -376,13 +481,18 @@ extern "C" int pg_count_batch(pg_graph *g, const pg_batch *b, uint64_t *counts_d
 }
 
 extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *counts_out, void *stream) {
-    if (n_plans > 0 && !counts_out) return pg_set_error(PG_EINVAL, "NULL counts_out");
+    if (!g || (n_plans > 0 && (!plans || !counts_out)) || n_plans < 0) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (n_plans > PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "at most 64 plans per call");
     if (n_plans == 0) return PG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
     DevTmp c;
     PG_CUDA(cudaMalloc(&c.p, 2 * sizeof(uint64_t) * n_plans));
-    int rc = pg_count_ex(g, plans, n_plans, (uint64_t *)c.p, PG_KERNEL_AUTO, stream);
+    PgRunCtl ctl;
+    int rc = pg_run_ctl(g, 0, s, &ctl);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
+    rc = count_dispatch(g, plans, n_plans, (uint64_t *)c.p, PG_KERNEL_AUTO, s, &ctl);
+    if (rc) return rc;
+    if ((rc = pg_run_ctl_check(ctl, s)) != PG_OK) return rc;
     PG_CUDA(cudaMemcpyAsync(counts_out, c.p, 2 * sizeof(uint64_t) * n_plans, cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
     return PG_OK;
@@ -396,16 +506,22 @@ extern "C" int pg_count_until(pg_graph *g, pg_plan *pl, uint64_t target, uint64_
     if (target < 1) return pg_set_error(PG_EINVAL, "target must be >= 1");
     if (pl->h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
     cudaStream_t s = (cudaStream_t)stream;
+    const int k = pg_plan_size(pl->h);
+    const bool clique = pl->h.is_clique && k >= 3 && g->max_out < 65536;
+    if (pl->h.big_clique && !clique)
+        return pg_set_error(PG_EUNSUPPORTED, "the k-clique kernel needs out-degrees below 65536");
     int rc = pg_plan_upload(pl);
     if (rc) return rc;
-    rc = pg_ensure_scratch(g, pg_generic_scratch_bytes(g, pl, true), s);
+    rc = pg_ensure_scratch(g, clique ? pg_clique_scratch_bytes(g, k) : pg_generic_scratch_bytes(g, pl, true), s);
     if (rc) return rc;
-    unsigned long long *counts = g->ex->tmp_counts;          // (low, high)
-    unsigned long long *stop = g->ex->queues + PG_MAX_QUEUES - 1;
+    unsigned long long *counts = g->ex->tmp_counts; // (low, high)
     PG_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
-    PG_CUDA(cudaMemsetAsync(stop, 0, sizeof(unsigned long long), s));
-    rc = pg_launch_generic(g, pl, counts, 0, true, s, target, stop);
+    PgRunCtl ctl;
+    if ((rc = pg_run_ctl(g, target, s, &ctl)) != PG_OK) return rc;
+    // cliques: the bitmap kernel, publishing after every first-level row
+    rc = clique ? pg_launch_clique(g, k, k, counts, 0, s, &ctl) : pg_launch_generic(g, pl, counts, 0, true, s, &ctl);
     if (rc) return rc;
+    if ((rc = pg_run_ctl_check(ctl, s)) != PG_OK) return rc;
     unsigned long long host[2];
     PG_CUDA(cudaMemcpyAsync(host, counts, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
@@ -413,6 +529,43 @@ extern "C" int pg_count_until(pg_graph *g, pg_plan *pl, uint64_t target, uint64_
     count_out[1] = host[1];
     *reached = (host[1] != 0 || host[0] >= target) ? 1 : 0;
     return PG_OK;
+}
+
+// The clustering-coefficient program of Section 3.2.3: W = matches of the
+// 3-vertex star (connected triples), counted exactly; triangles T are then
+// counted only until 3T > bound * W is established (existence with a target).
+extern "C" int pg_clustering_coefficient_above(pg_graph *g, double bound, int32_t *answer, uint64_t *triangles_out,
+                                               uint64_t *wedges_out, void *stream) {
+    if (!g || !answer || !triangles_out || !wedges_out) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (!(bound >= 0.0) || bound > 1e300) return pg_set_error(PG_EINVAL, "bound must be finite and >= 0");
+    const int32_t star[4] = {0, 1, 0, 2}, tri[6] = {0, 1, 1, 2, 0, 2};
+    pg_pattern_desc ds{3, 2, star, 0, nullptr, nullptr, nullptr, 0};
+    pg_pattern_desc dt{3, 3, tri, 0, nullptr, nullptr, nullptr, 0};
+    pg_plan *ps = nullptr, *pt = nullptr;
+    int rc = pg_compile_pattern(&ds, &ps);
+    if (rc == PG_OK) rc = pg_compile_pattern(&dt, &pt);
+    uint64_t w[2] = {0, 0}, t[2] = {0, 0};
+    if (rc == PG_OK) rc = pg_count(g, &ps, 1, w, stream);
+    int32_t reached = 0;
+    if (rc == PG_OK) {
+        const long double W = (long double)w[0] + 18446744073709551616.0L * (long double)w[1];
+        // smallest T with 3T > bound * W
+        const long double x = (long double)bound * W / 3.0L;
+        const long double need = floorl(x) + 1.0L;
+        const uint64_t target = need >= 18446744073709551615.0L ? UINT64_MAX : (uint64_t)need;
+        rc = pg_count_until(g, pt, target, t, &reached, stream);
+        if (rc == PG_OK) {
+            const long double T = (long double)t[0] + 18446744073709551616.0L * (long double)t[1];
+            *answer = (reached && 3.0L * T > (long double)bound * W) ? 1 : 0;
+            triangles_out[0] = t[0];
+            triangles_out[1] = t[1];
+            wedges_out[0] = w[0];
+            wedges_out[1] = w[1];
+        }
+    }
+    pg_free_plan(ps);
+    pg_free_plan(pt);
+    return rc;
 }
 
 // ---------------------------------------------------------------- match ----
@@ -423,6 +576,7 @@ extern "C" int pg_match_range(pg_graph *g, pg_plan *pl, int64_t rank_begin, int6
     if (rank_begin < 0 || rank_end < rank_begin || rank_end > g->n)
         return pg_set_error(PG_EINVAL, "start-vertex rank range out of bounds");
     if (pl->h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+    if (pl->h.big_clique) return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices are counted, not listed");
     if (capacity > (uint64_t)INT64_MAX / (uint64_t)pl->h.pat.k) return pg_set_error(PG_EINVAL, "capacity too large");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = pg_plan_upload(pl);
@@ -430,8 +584,11 @@ extern "C" int pg_match_range(pg_graph *g, pg_plan *pl, int64_t rank_begin, int6
     rc = pg_ensure_scratch(g, pg_match_scratch_bytes(g, pl), s);
     if (rc) return rc;
     unsigned long long *counter = g->ex->tmp_counts;
-    rc = pg_launch_match(g, pl, rank_begin, rank_end, out_dev, capacity, counter, s);
+    PgRunCtl ctl;
+    if ((rc = pg_run_ctl(g, 0, s, &ctl)) != PG_OK) return rc;
+    rc = pg_launch_match(g, pl, rank_begin, rank_end, out_dev, capacity, counter, s, &ctl);
     if (rc) return rc;
+    if ((rc = pg_run_ctl_check(ctl, s)) != PG_OK) return rc;
     unsigned long long total = 0;
     PG_CUDA(cudaMemcpyAsync(&total, counter, sizeof(total), cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));

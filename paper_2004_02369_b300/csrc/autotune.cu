@@ -121,7 +121,7 @@ extern "C" int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
         if (!plans[i]) return pg_set_error(PG_EINVAL, "NULL plan");
         const PgPlanHost &h = plans[i]->h;
         if (h.anti_vertices) return pg_set_error(PG_EUNSUPPORTED, "anti-vertex plans run untuned on PG_KERNEL_GENERIC");
-        const bool c = h.is_clique && h.pat.k >= 3;
+        const bool c = h.is_clique && pg_plan_size(h) >= 3;
         all_clique &= c;
         any_clique |= c;
     }

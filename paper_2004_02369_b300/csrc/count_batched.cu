@@ -66,6 +66,7 @@ struct BatchArgs {
     int n_split;
     long long n_split_tasks;
     unsigned long long *counts; // 2 words per slot
+    PgRunCtl ctl;               // work budget (polled between tasks and first-level candidates)
 };
 
 __device__ __forceinline__ void add_slot(unsigned long long *acc, int slot, unsigned __int128 x) {
@@ -102,7 +103,10 @@ __global__ void __launch_bounds__(W * 32, CAP ? 32 / W : 0) k_count_batched(Batc
     const DevGraph &g = a.g;
     int m[PGP_MAXK], node[PGP_MAXK], sz[PGP_MAXK], ci[PGP_MAXK], ch[PGP_MAXK];
     long long task = 0, task_end = 0;
+    const bool polled = a.ctl.words != nullptr;
+    if (polled && lane == 0) ctl_begin(a.ctl);
     for (;;) {
+        if (polled && ctl_stop(a.ctl, lane)) break;
         if (task >= task_end) {
             unsigned long long t = 0;
             if (lane == 0) t = atomicAdd(a.queue, (unsigned long long)a.chunk);
@@ -148,6 +152,10 @@ __global__ void __launch_bounds__(W * 32, CAP ? 32 / W : 0) k_count_batched(Batc
                         ++ch[l];
                         continue;
                     }
+                }
+                if (l == 1 && ch[l] == 0 && polled && ctl_stop(a.ctl, lane)) {
+                    l = 0;
+                    break;
                 }
                 if (l > 0) m[l] = wbuf[a.lvl_off[l] + ci[l]];
                 const int child = N.first_child + ch[l];
@@ -328,6 +336,9 @@ std::vector<int> canonical(const PgPattern &q) {
 // merged and counted once by their own (edge-induced) plans.
 int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out) {
     if (n_plans < 1 || n_plans > kMaxSlots) return pg_set_error(PG_EINVAL, "a batch holds 1..64 plans");
+    for (int i = 0; i < n_plans; ++i)
+        if (plans[i]->h.big_clique)
+            return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices run on the k-clique kernel only (pg_count)");
     for (int i = 0; i < n_plans; ++i)
         if (plans[i]->h.anti_vertices)
             return pg_set_error(PG_EUNSUPPORTED, "anti-vertex patterns run on the plan interpreter (PG_KERNEL_GENERIC)");
@@ -631,12 +642,12 @@ long long batch_layout(const pg_graph *g, const pg_batch *b, long long *off) {
 size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b) {
     long long off[PGP_MAXK];
     size_t bytes = (size_t)batched_grid(g) * batched_warps(g) * (size_t)batch_layout(g, b, off) * sizeof(int);
-    if (b->clique_kmax) bytes = std::max(bytes, pg_clique_scratch_bytes(g));
+    if (b->clique_kmax) bytes = std::max(bytes, pg_clique_scratch_bytes(g, b->clique_kmax));
     return bytes;
 }
 
 int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts_dev, int queue_slot,
-                      cudaStream_t s) {
+                      cudaStream_t s, const PgRunCtl *ctl) {
     if (g->n == 0) {
         PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_out, s));
         return PG_OK;
@@ -658,6 +669,7 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.n_split_tasks = g->n_split_tasks;
     a.n_tasks = (g->n_split_tasks + (g->n - g->n_split) + a.stride - 1) / a.stride;
     a.counts = b->d_slot_counts;
+    a.ctl = ctl ? *ctl : PgRunCtl{};
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
     if (b->n_roots > 0) {
         PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
@@ -669,7 +681,7 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
         if (g->max_out >= 65536) return pg_set_error(PG_EUNSUPPORTED, "clique kernel needs out-degrees below 65536");
         const int span = b->clique_kmax - b->clique_kmin + 1;
         PG_CUDA(cudaMemsetAsync(g->ex->tmp_counts, 0, 2 * sizeof(unsigned long long) * span, s));
-        int rc = pg_launch_clique(g, b->clique_kmin, b->clique_kmax, g->ex->tmp_counts, queue_slot + 2, s);
+        int rc = pg_launch_clique(g, b->clique_kmin, b->clique_kmax, g->ex->tmp_counts, queue_slot + 2, s, ctl);
         if (rc) return rc;
         for (int p = 0; p < b->n_slots; ++p)
             if (b->clique_k[p])

@@ -24,6 +24,17 @@
 //  * Traversal: warp-uniform loops over all levels but the last; the last
 //    level is lane-parallel over a compacted candidate list, so every lane
 //    does one popcount-of-AND row product per candidate.
+//  * Sizes: KMAX = 8 (the tuned variant) or 16 (large cliques, e.g. the
+//    14-clique existence query of the paper's evaluation).  A branch whose
+//    candidate set is too small to reach kmin is cut (cardinality pruning).
+//  * Exact counts: lane counters are 64-bit and are moved into the 128-bit
+//    totals after any start vertex that leaves them at 2^62 or more (see
+//    bump); the final warp sums are 128-bit.
+//  * Run control (PgRunCtl): existence mode publishes counts after every
+//    row and stops all warps once the target is reached; a device work
+//    budget stops the launch and flags it as timed out.
+#include <mutex>
+
 #include "device_sets.cuh"
 
 namespace {
@@ -35,7 +46,6 @@ constexpr int kLightWs = (kLightD / 32) | 1;
 // per-warp light tile: list, rows, row start / length / element prefix
 constexpr int kLightTile = kLightD + kLightD * kLightWs + 3 * kLightD + 1;
 constexpr int kItems = 256; // queued (candidate set, vertex) products per warp
-constexpr int kMaxK = 8;
 constexpr int kCtl = 8;
 constexpr size_t kSmemBudget = 96 * 1024;
 
@@ -60,7 +70,30 @@ struct CliqueArgs {
     int stride;                // every stride-th start vertex (timing samples)
     long long n_light_tasks;   // ceil(n / stride)
     long long n_heavy_tasks;   // ceil(n_heavy / stride)
+    PgRunCtl ctl;              // early termination / work budget (words null: none)
 };
+
+// cnt[S] = lane counter of (S+3)-cliques.  A lane adds at most 2^16 per
+// row product and a product takes at least one issue slot, so a counter
+// below 2^62 needs more than 2^63 / 2^16 products (over 19 hours of one
+// lane at 2 GHz) to wrap: checking after every start vertex and moving
+// counters of 2^62 or more into the 128-bit totals keeps the counts exact.
+template <int S>
+__device__ __forceinline__ void bump(unsigned long long *cnt, unsigned long long x, const CliqueArgs &) {
+    cnt[S] += x;
+}
+
+// (run-time indexed loops keep the counters in local memory, off the
+// register budget of the traversal)
+template <int KMAX>
+__device__ __forceinline__ void guard_counts(unsigned long long *cnt, const CliqueArgs &a) {
+#pragma unroll 1
+    for (int s = 0; s < KMAX; ++s)
+        if (cnt[s] >> 62) {
+            if (s + 3 >= a.kmin && s + 3 <= a.kmax) atomic_add_u128(a.counts + 2 * (s + 3 - a.kmin), cnt[s]);
+            cnt[s] = 0;
+        }
+}
 
 // Sub-graph tile of one start vertex: list = N+(v) (d entries), rows[i] =
 // bitmap of j < i adjacent to i, and per-row build bookkeeping.
@@ -75,7 +108,7 @@ struct Tile {
 
 // Per-warp traversal scratch.
 struct Walker {
-    unsigned *cbuf; // kMaxK level bitmaps of cws words
+    unsigned *cbuf; // KMAX level bitmaps of cws words
     unsigned *ring; // nslots candidate bitmaps
     int *items;     // kItems packed (slot << 16 | l)
     unsigned *bsh;  // 32 re-indexed rows of compressed_row
@@ -181,10 +214,10 @@ __device__ __forceinline__ unsigned long long flush(const Tile &t, Walker &wk, i
 // level; the result counts into cnt[P].
 template <int P>
 __device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *C, int limit, int lane,
-                                     unsigned long long *cnt) {
+                                     unsigned long long *cnt, const CliqueArgs &a) {
     const int nw = (limit + 31) >> 5;
     if (wk.used == wk.nslots) {
-        cnt[P] += flush(t, wk, lane);
+        bump<P>(cnt, flush(t, wk, lane), a);
         wk.used = 0;
     }
     const int slot = wk.used++;
@@ -194,7 +227,7 @@ __device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *
     for (int w = 0; w < nw; ++w) {
         const unsigned x = S[w];
         const int c = __popc(x);
-        if (wk.m + c > kItems) cnt[P] += flush(t, wk, lane);
+        if (wk.m + c > kItems) bump<P>(cnt, flush(t, wk, lane), a);
         if ((x >> lane) & 1u) wk.items[wk.m + __popc(x & ((1u << lane) - 1))] = (slot << 16) | (w * 32 + lane);
         wk.m += c;
     }
@@ -203,18 +236,22 @@ __device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *
 // Candidate set C after a prefix of P sub-graph vertices (bits below
 // `limit`): popc(C) has been counted as (P + 2)-cliques by the caller; count
 // every larger size up to kmax.  All levels but the last are warp-uniform
-// loops; the last level is queued as lane-parallel products.
-template <int P>
-__device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, int kmax, int lane,
-                     unsigned long long *cnt) {
-    if constexpr (P >= kMaxK - 2) {
+// loops; the last level is queued as lane-parallel products.  A candidate
+// whose extension N has fewer than kmin - P - 2 bits cannot lie in a
+// kmin-clique, and neither can any branch below it: skipped.
+template <int P, int KMAX, bool XT>
+__device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, int lane, unsigned long long *cnt,
+                     const CliqueArgs &a) {
+    if constexpr (P >= KMAX - 2) {
         return;
     } else {
+        const int kmax = a.kmax;
         if (P + 3 > kmax) return;
         if (P + 3 == kmax) {
-            emit<P>(t, wk, C, limit, lane, cnt);
+            emit<P>(t, wk, C, limit, lane, cnt, a);
             return;
         }
+        const bool prune = XT && a.kmin > P + 3;
         const int nw = (limit + 31) >> 5;
         unsigned *N = wk.cbuf + (size_t)P * wk.cws;
         for (int w = 0; w < nw; ++w) {
@@ -230,9 +267,10 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
                     N[v] = y;
                     c += __popc(y);
                 }
-                cnt[P] += c;
+                bump<P>(cnt, c, a);
                 __syncwarp();
-                walk<P + 1>(t, wk, N, l, kmax, lane, cnt);
+                if (!prune || (int)__reduce_add_sync(PG_FULL, c) >= a.kmin - P - 2)
+                    walk<P + 1, KMAX, XT>(t, wk, N, l, lane, cnt, a);
                 __syncwarp();
             }
         }
@@ -248,7 +286,7 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
 //   6-cliques:  sum_a sum_{b in B_a} sum_{q in B_a & B_b} popc(B_a & B_b & B_q)
 // Returns false (nothing counted) when R_i has more than 32 bits.
 __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, unsigned *bsh, int lane,
-                                               unsigned long long *cnt) {
+                                               unsigned long long *cnt, const CliqueArgs &a) {
     const unsigned *Ri = t.rows + (size_t)i * t.ws;
     const int nw = (i + 31) >> 5;
     int c = 0;
@@ -282,7 +320,7 @@ __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, u
             pre += __popc(riw);
         }
     }
-    cnt[1] += __popc(B);
+    bump<1>(cnt, __popc(B), a);
     if (kmax >= 5) {
         bsh[lane] = B;
         __syncwarp();
@@ -302,33 +340,51 @@ __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, u
                 }
             }
         }
-        cnt[2] += s5;
-        cnt[3] += s6;
+        bump<2>(cnt, s5, a);
+        bump<3>(cnt, s6, a);
         __syncwarp();
     }
     return true;
 }
 
 // Pending products of the last level belong to size kmax: cnt[kmax - 3].
-__device__ __forceinline__ void drain(const Tile &t, Walker &wk, int kmax, int lane, unsigned long long *cnt) {
+template <int KMAX>
+__device__ __forceinline__ void drain(const Tile &t, Walker &wk, int lane, unsigned long long *cnt,
+                                      const CliqueArgs &a) {
     if (wk.m == 0) {
         wk.used = 0;
         return;
     }
-    const unsigned long long s = flush(t, wk, lane);
-    switch (kmax) {
-        case 4: cnt[1] += s; break;
-        case 5: cnt[2] += s; break;
-        case 6: cnt[3] += s; break;
-        case 7: cnt[4] += s; break;
-        default: cnt[5] += s; break;
-    }
+    cnt[a.kmax - 3] += flush(t, wk, lane);
     wk.used = 0;
 }
 
+// Traversal of one row i of a tile (the cliques through v and list[i]).
+template <int KMAX, bool XT>
+__device__ __forceinline__ void run_row(const Tile &t, Walker &wk, int i, int lane, unsigned long long *cnt,
+                                        const CliqueArgs &a) {
+    if (KMAX <= 8 && a.kmax <= 6 && compressed_row(t, i, a.kmax, wk.bsh, lane, cnt, a)) return;
+    walk<1, KMAX, XT>(t, wk, t.rows + (size_t)i * t.ws, i, lane, cnt, a);
+}
+
+// Existence mode: publish the warp's kmax count after a row (kmin == kmax).
+template <int KMAX>
+__device__ __forceinline__ void publish_row(const Tile &t, Walker &wk, int lane, unsigned long long *cnt,
+                                            const CliqueArgs &a) {
+    drain<KMAX>(t, wk, lane, cnt, a);
+    const unsigned long long mine = cnt[a.kmax - 3];
+    cnt[a.kmax - 3] = 0;
+    const unsigned __int128 tot = warp_sum_u128(mine);
+    if (lane == 0) ctl_publish(a.ctl, a.counts, tot);
+}
+
 // MINB CTAs per SM: 3 (80 registers) or 4 (64 registers, some spilling;
-// more resident warps against the fixed-latency dependency stalls).
-template <int MINB>
+// more resident warps against the fixed-latency dependency stalls).  KMAX:
+// largest clique size the traversal can reach (8 or 16).  XT: the extended
+// variant with cardinality pruning and run control (large kmin, existence
+// queries, work budgets); the plain variants keep their registers for the
+// traversal.
+template <int MINB, int KMAX, bool XT>
 __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     extern __shared__ __align__(16) unsigned smem[];
     int *ctl = (int *)smem;
@@ -337,19 +393,23 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     const int warp = threadIdx.x >> 5;
     const DevGraph &g = a.g;
     unsigned *slab = a.slabs ? a.slabs + (size_t)blockIdx.x * a.slab_words : nullptr;
+    const bool polled = XT && a.ctl.words != nullptr;
+    const bool exist = XT && a.ctl.target > 0;
+    if (polled && lane == 0) ctl_begin(a.ctl);
 
     Walker wk;
     wk.cws = a.cws;
     wk.nslots = a.nslots;
     wk.cbuf = smem + kCtl + a.region_words + (size_t)warp * a.warp_words;
-    wk.ring = wk.cbuf + (size_t)kMaxK * a.cws;
+    wk.ring = wk.cbuf + (size_t)KMAX * a.cws;
     wk.items = (int *)(wk.ring + (size_t)a.nslots * a.cws);
     wk.bsh = (unsigned *)(wk.items + kItems);
     wk.m = 0;
     wk.used = 0;
 
-    unsigned long long cnt[kMaxK];
-    for (int s = 0; s < kMaxK; ++s) cnt[s] = 0;
+    unsigned long long cnt[KMAX];
+#pragma unroll 1
+    for (int s = 0; s < KMAX; ++s) cnt[s] = 0;
 
     // ---- heavy vertices: one CTA each --------------------------------------
     Tile ht;
@@ -364,8 +424,12 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     }
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned long long h = atomicAdd(a.queue + 1, 1ull);
-            ctl[0] = h < (unsigned long long)a.n_heavy_tasks ? a.heavy[h * (unsigned long long)a.stride] : -1;
+            int v = -1;
+            if (!polled || !ctl_poll(a.ctl)) {
+                const unsigned long long h = atomicAdd(a.queue + 1, 1ull);
+                if (h < (unsigned long long)a.n_heavy_tasks) v = a.heavy[h * (unsigned long long)a.stride];
+            }
+            ctl[0] = v;
             ctl[1] = 0; // rows traversed
         }
         __syncthreads();
@@ -384,11 +448,13 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
                 r = __shfl_sync(PG_FULL, r, 0);
                 const int i = d - 1 - r; // longest rows first
                 if (i < 2) break;
-                if (a.kmax > 6 || !compressed_row(ht, i, a.kmax, wk.bsh, lane, cnt))
-                    walk<1>(ht, wk, ht.rows + (size_t)i * ht.ws, i, a.kmax, lane, cnt);
+                if (polled && ctl_stop(a.ctl, lane)) break;
+                run_row<KMAX, XT>(ht, wk, i, lane, cnt, a);
+                if (exist) publish_row<KMAX>(ht, wk, lane, cnt, a);
             }
-            drain(ht, wk, a.kmax, lane, cnt);
+            drain<KMAX>(ht, wk, lane, cnt, a);
         }
+        guard_counts<KMAX>(cnt, a);
         __syncthreads();
     }
 
@@ -404,6 +470,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
         lt.ws = kLightWs;
     }
     for (;;) {
+        if (polled && ctl_stop(a.ctl, lane)) break;
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(a.queue, (unsigned long long)a.chunk);
         base = __shfl_sync(PG_FULL, base, 0);
@@ -420,18 +487,22 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
             __syncwarp();
             build_rows<false>(g, lt, d, lane, 32, cnt[0]);
             if (a.kmax >= 4) {
-                for (int i = d - 1; i >= 2; --i)
-                    if (a.kmax > 6 || !compressed_row(lt, i, a.kmax, wk.bsh, lane, cnt))
-                        walk<1>(lt, wk, lt.rows + (size_t)i * lt.ws, i, a.kmax, lane, cnt);
-                drain(lt, wk, a.kmax, lane, cnt);
+                for (int i = d - 1; i >= 2; --i) {
+                    if (polled && ctl_stop(a.ctl, lane)) break;
+                    run_row<KMAX, XT>(lt, wk, i, lane, cnt, a);
+                    if (exist) publish_row<KMAX>(lt, wk, lane, cnt, a);
+                }
+                drain<KMAX>(lt, wk, lane, cnt, a);
             }
+            guard_counts<KMAX>(cnt, a);
             __syncwarp();
         }
     }
 
-    for (int k = a.kmin; k <= a.kmax; ++k) {
-        const unsigned long long tot = warp_sum_u64(cnt[k - 3]);
-        if (lane == 0 && tot) atomic_add_u128(a.counts + 2 * (k - a.kmin), tot);
+#pragma unroll 1
+    for (int s = a.kmin - 3; s <= a.kmax - 3; ++s) {
+        const unsigned __int128 tot = warp_sum_u128(cnt[s]);
+        if (lane == 0 && tot) atomic_add_u128(a.counts + 2 * (s + 3 - a.kmin), tot);
     }
 }
 
@@ -442,7 +513,14 @@ struct Layout {
     size_t smem_bytes;
 };
 
-Layout layout_for(const pg_graph *g) {
+int kmax_variant(int kmax) { return kmax <= 8 ? 8 : 16; }
+
+// the extended variant: run control, or pruning worth its registers
+bool extended_variant(int kmin, int kmax, const PgRunCtl *ctl) {
+    return (ctl && ctl->words) || kmin >= 6 || kmax > 8;
+}
+
+Layout layout_for(const pg_graph *g, int kvar) {
     Layout L{};
     CliqueArgs &a = L.a;
     const long long D = std::max<long long>(g->max_out, 1);
@@ -450,7 +528,7 @@ Layout layout_for(const pg_graph *g) {
     a.hws = (int)(((D + 31) / 32) | 1);
     a.cws = std::max(a.hws, kLightWs);
     a.nslots = (int)std::min<long long>(32, std::max<long long>(2, 1024 / a.cws));
-    a.warp_words = (int)(((size_t)kMaxK * a.cws + (size_t)a.nslots * a.cws + kItems + 32 + 3) & ~3ull);
+    a.warp_words = (int)(((size_t)kvar * a.cws + (size_t)a.nslots * a.cws + kItems + 32 + 3) & ~3ull);
     const size_t heavy_words = (size_t)4 * a.dpad + 4 + (size_t)D * a.hws;
     const size_t light_words = (size_t)kWarps * kLightTile;
     const size_t warps_words = (size_t)kWarps * a.warp_words;
@@ -461,30 +539,53 @@ Layout layout_for(const pg_graph *g) {
     return L;
 }
 
-void *clique_fn(const pg_graph *g) {
-    return g->tune.clique_min_blocks == 4 ? (void *)k_count_clique<4> : (void *)k_count_clique<3>;
+void *clique_fn(const pg_graph *g, int kvar, bool xt) {
+    if (kvar > 8) return (void *)k_count_clique<3, 16, true>;
+    if (xt) return (void *)k_count_clique<3, 8, true>;
+    return g->tune.clique_min_blocks == 4 ? (void *)k_count_clique<4, 8, false> : (void *)k_count_clique<3, 8, false>;
 }
 
-int clique_grid(const pg_graph *g, size_t smem) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_count_clique<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_count_clique<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+// The dynamic shared-memory limit is a per-device function attribute: set
+// once per device (thread-safe), checked.
+constexpr int kMaxDevices = 64;
+std::once_flag g_attr_once[kMaxDevices];
+cudaError_t g_attr_err[kMaxDevices];
+
+int ensure_attributes(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return pg_set_error(PG_EINVAL, "device index out of range");
+    std::call_once(g_attr_once[dev], [dev] {
+        const int bytes = 200 * 1024;
+        void *fns[] = {(void *)k_count_clique<3, 8, false>, (void *)k_count_clique<4, 8, false>,
+                       (void *)k_count_clique<3, 8, true>, (void *)k_count_clique<3, 16, true>};
+        cudaError_t e = cudaSuccess;
+        for (void *f : fns)
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        g_attr_err[dev] = e;
+    });
+    if (g_attr_err[dev] != cudaSuccess) return pg_cuda_error(g_attr_err[dev], "cudaFuncSetAttribute(k_count_clique)");
+    return PG_OK;
+}
+
+int clique_grid(const pg_graph *g, size_t smem, int kvar, bool xt, int *grid) {
+    int rc = ensure_attributes(g->device);
+    if (rc) return rc;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clique_fn(g), kBlock, smem);
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, clique_fn(g, kvar, xt), kBlock, smem));
     if (per_sm < 1) per_sm = 1;
     if (g->tune.clique_blocks_per_sm > 0) per_sm = std::min(per_sm, g->tune.clique_blocks_per_sm);
-    return per_sm * g->num_sms;
+    *grid = per_sm * g->num_sms;
+    return PG_OK;
 }
 
 int launch(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, unsigned long long *queue,
-           void *slabs, long long max_slabs, cudaStream_t s) {
-    if (kmin < 3 || kmax > kMaxK || kmin > kmax) return pg_set_error(PG_EINVAL, "clique sizes must be 3..8");
+           void *slabs, long long max_slabs, cudaStream_t s, const PgRunCtl *rctl) {
+    if (kmin < 3 || kmax > PG_MAX_CLIQUE || kmin > kmax)
+        return pg_set_error(PG_EINVAL, "clique sizes must satisfy 3 <= kmin <= kmax <= 16");
+    if (kmax > 8 && kmax - kmin > 7) return pg_set_error(PG_EINVAL, "at most 8 clique sizes per launch");
     if (g->n == 0) return PG_OK;
     if (g->max_out >= 65536) return pg_set_error(PG_EUNSUPPORTED, "clique kernel needs out-degrees below 65536");
-    Layout L = layout_for(g);
+    const int kvar = kmax_variant(kmax);
+    Layout L = layout_for(g, kvar);
     CliqueArgs a = L.a;
     a.g = g->d;
     a.kmin = kmin;
@@ -500,30 +601,41 @@ int launch(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, unsi
     a.stride = std::max(1, g->sample_stride);
     a.n_light_tasks = (g->n + a.stride - 1) / a.stride;
     a.n_heavy_tasks = (g->n_heavy + a.stride - 1) / a.stride;
-    long long blocks = clique_grid(g, L.smem_bytes);
-    if (a.slab_words && blocks > max_slabs) blocks = max_slabs;
+    a.ctl = rctl ? *rctl : PgRunCtl{};
+    if (a.ctl.target > 0 && (kmin != kmax || !a.ctl.words))
+        return pg_set_error(PG_EINVAL, "internal: existence mode needs one clique size and control words");
+    const bool xt = extended_variant(kmin, kmax, rctl);
+    int blocks = 0;
+    int rc = clique_grid(g, L.smem_bytes, kvar, xt, &blocks);
+    if (rc) return rc;
+    if (a.slab_words && blocks > max_slabs) blocks = (int)max_slabs;
     if (blocks < 1) return pg_set_error(PG_EINVAL, "scratch holds no slab for a single block");
     PG_CUDA(cudaMemsetAsync(queue, 0, 2 * sizeof(unsigned long long), s));
     void *args[] = {&a};
-    PG_CUDA(cudaLaunchKernel(clique_fn(g), dim3((unsigned)blocks), dim3(kBlock), args, L.smem_bytes, s));
+    PG_CUDA(cudaLaunchKernel(clique_fn(g, kvar, xt), dim3((unsigned)blocks), dim3(kBlock), args, L.smem_bytes, s));
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }
 
 }  // namespace
 
-size_t pg_clique_slab_bytes(const pg_graph *g) { return (size_t)layout_for(g).a.slab_words * sizeof(unsigned); }
+size_t pg_clique_slab_bytes(const pg_graph *g, int kmax) {
+    return (size_t)layout_for(g, kmax_variant(kmax)).a.slab_words * sizeof(unsigned);
+}
 
-size_t pg_clique_scratch_bytes(const pg_graph *g) {
-    const Layout L = layout_for(g);
-    return (size_t)clique_grid(g, L.smem_bytes) * (size_t)L.a.slab_words * sizeof(unsigned);
+size_t pg_clique_scratch_bytes(const pg_graph *g, int kmax) {
+    const int kvar = kmax_variant(kmax);
+    const Layout L = layout_for(g, kvar);
+    int blocks = 0;
+    if (clique_grid(g, L.smem_bytes, kvar, kvar > 8, &blocks) != PG_OK) blocks = 4 * g->num_sms;
+    return (size_t)blocks * (size_t)L.a.slab_words * sizeof(unsigned);
 }
 
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, int queue_slot,
-                     cudaStream_t s) {
-    if (queue_slot + 1 >= PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "queue slot out of range");
+                     cudaStream_t s, const PgRunCtl *ctl) {
+    if (queue_slot + 1 >= PG_CTL_WORDS_SLOT) return pg_set_error(PG_EINVAL, "queue slot out of range");
     return launch(g, kmin, kmax, counts_dev, g->ex->queues + queue_slot, g->ex->scratch,
-                  (long long)(g->ex->scratch_bytes / std::max<size_t>(pg_clique_slab_bytes(g), 1)), s);
+                  (long long)(g->ex->scratch_bytes / std::max<size_t>(pg_clique_slab_bytes(g, kmax), 1)), s, ctl);
 }
 
 // Same kernel on caller-supplied scratch: `queue` = two 64-bit counters
@@ -531,5 +643,5 @@ int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts
 // pg_clique_slab_bytes() bytes; the grid is cut to max_slabs CTAs.
 int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
                         unsigned long long *queue, void *slabs, long long max_slabs, cudaStream_t s) {
-    return launch(g, kmin, kmax, counts_dev, queue, slabs, max_slabs, s);
+    return launch(g, kmin, kmax, counts_dev, queue, slabs, max_slabs, s, nullptr);
 }

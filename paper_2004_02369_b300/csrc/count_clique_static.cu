@@ -47,7 +47,7 @@ extern "C" int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax,
     int dev = -1;
     PG_CUDA(cudaGetDevice(&dev));
     if (dev != g->device) return pg_set_error(PG_EINVAL, "the graph lives on another device than the current one");
-    const size_t slab = pg_clique_slab_bytes(g);
+    const size_t slab = pg_clique_slab_bytes(g, kmax);
     const size_t room = PG_STATIC_SCRATCH_BYTES - kQueueBytes;
     long long max_slabs = slab ? (long long)(room / slab) : (1ll << 40);
     if (slab && max_slabs < g->num_sms)

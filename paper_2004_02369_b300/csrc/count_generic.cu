@@ -40,20 +40,13 @@ struct GenericArgs {
     unsigned long long n_tasks;
     int persistent;             // 0: one task per warp, no queue
     unsigned long long *counts; // (low, high)
-    // existence mode (target > 0): counts are published after every task and
-    // the warp that sees the total reach `target` raises *stop; warps poll
-    // it between tasks and between first-level candidates (Section 5.4,
-    // early termination)
-    unsigned long long target;
-    unsigned long long *stop;
+    // run control: existence mode (ctl.target > 0) publishes counts after
+    // every task and the warp that sees the total reach the target raises
+    // the stop flag; with a work budget the launch stops once it is spent.
+    // Warps poll between tasks and between first-level candidates (Section
+    // 5.4, early termination).
+    PgRunCtl ctl;
 };
-
-// *stop as seen by lane 0, broadcast (keeps the warp converged)
-__device__ __forceinline__ bool stop_raised(const GenericArgs &a, int lane) {
-    int f = 0;
-    if (lane == 0) f = *(volatile unsigned long long *)a.stop != 0ull;
-    return __shfl_sync(PG_FULL, f, 0) != 0;
-}
 
 __device__ unsigned __int128 run_task(const GenericArgs &a, int v, const PgOrder &ord, int *wbuf, int lane) {
     const DevGraph &g = a.g;
@@ -82,7 +75,7 @@ __device__ unsigned __int128 run_task(const GenericArgs &a, int v, const PgOrder
         // advance to the next unexplored candidate
         while (l >= 1 && (l == L - 1 || idx[l] >= sz[l])) --l;
         if (l < 1) break;
-        if (l == 1 && a.target && stop_raised(a, lane)) break;
+        if (l == 1 && a.ctl.words && ctl_stop(a.ctl, lane)) break;
         m[l] = wbuf[a.lvl_off[l] + idx[l]];
         ++idx[l];
         ++l;
@@ -95,8 +88,9 @@ __global__ void __launch_bounds__(kBlock) k_count_generic(GenericArgs a) {
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     int *wbuf = a.scratch + gw * a.warp_stride;
     unsigned __int128 acc = 0;
+    if (a.ctl.words && lane == 0) ctl_begin(a.ctl);
     for (;;) {
-        if (a.target && stop_raised(a, lane)) break;
+        if (a.ctl.words && ctl_stop(a.ctl, lane)) break;
         unsigned long long t = (unsigned long long)gw;
         if (a.persistent) {
             if (lane == 0) t = atomicAdd(a.queue, 1ull);
@@ -106,14 +100,8 @@ __global__ void __launch_bounds__(kBlock) k_count_generic(GenericArgs a) {
         const int v = (int)(t / (unsigned long long)a.n_orders);
         const int o = (int)(t % (unsigned long long)a.n_orders);
         acc += run_task(a, v, a.orders[o], wbuf, lane);
-        if (a.target && acc) {
-            if (lane == 0) {
-                atomic_add_u128(a.counts, acc);
-                // high word first: a torn read can only under-estimate
-                const unsigned long long hi = *(volatile unsigned long long *)(a.counts + 1);
-                const unsigned long long lo = *(volatile unsigned long long *)a.counts;
-                if (hi || lo >= a.target) atomicExch(a.stop, 1ull);
-            }
+        if (a.ctl.target && acc) {
+            if (lane == 0) ctl_publish(a.ctl, a.counts, acc);
             acc = 0;
         }
         if (!a.persistent) break;
@@ -174,7 +162,8 @@ size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persis
 }
 
 int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev, int queue_slot,
-                      bool persistent, cudaStream_t s, unsigned long long target, unsigned long long *stop) {
+                      bool persistent, cudaStream_t s, const PgRunCtl *ctl) {
+    if (p->h.big_clique) return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices run on the k-clique kernel only");
     if (g->n == 0 || p->h.orders.empty()) return PG_OK;
     GenericArgs a;
     a.g = g->d;
@@ -186,8 +175,7 @@ int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_
     a.n_tasks = n_tasks_of(g, p);
     a.persistent = persistent ? 1 : 0;
     a.counts = counts_dev;
-    a.target = target;
-    a.stop = stop;
+    a.ctl = ctl ? *ctl : PgRunCtl{};
     if (persistent) PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
     k_count_generic<<<grid_of(g, p, persistent), kBlock, 0, s>>>(a);
     PG_CUDA(cudaGetLastError());

@@ -100,3 +100,61 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long x)
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(PG_FULL, x, o);
     return x;
 }
+
+// Exact warp sum of 64-bit lane values as a 128-bit integer (every lane
+// gets the total).
+__device__ __forceinline__ unsigned __int128 warp_sum_u128(unsigned long long x) {
+    unsigned long long lo = x, hi = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long l2 = __shfl_xor_sync(PG_FULL, lo, o), h2 = __shfl_xor_sync(PG_FULL, hi, o);
+        const unsigned long long s = lo + l2;
+        hi += h2 + (s < lo ? 1ull : 0ull);
+        lo = s;
+    }
+    return ((unsigned __int128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Run control (PgRunCtl).  ctl_begin: the first warp of the launch to call
+// it stores the launch's start time; call from one lane.  ctl_poll: true
+// when the launch must stop; raises the stop and timed-out flags when the
+// budget has run out.  Call from one lane and broadcast the answer.
+__device__ __forceinline__ void ctl_begin(const PgRunCtl &c) {
+    if (c.words && c.budget_ns) atomicCAS(c.words + 2, 0ull, globaltimer_ns());
+}
+
+__device__ __forceinline__ bool ctl_poll(const PgRunCtl &c) {
+    if (!c.words) return false;
+    if (*(volatile unsigned long long *)c.words) return true;
+    if (c.budget_ns && globaltimer_ns() - *(volatile unsigned long long *)(c.words + 2) > c.budget_ns) {
+        atomicExch(c.words + 1, 1ull);
+        atomicExch(c.words, 1ull);
+        return true;
+    }
+    return false;
+}
+
+// Warp-uniform stop decision (lane 0 polls).
+__device__ __forceinline__ bool ctl_stop(const PgRunCtl &c, int lane) {
+    int f = 0;
+    if (lane == 0) f = ctl_poll(c) ? 1 : 0;
+    return __shfl_sync(PG_FULL, f, 0) != 0;
+}
+
+// Existence mode: add a warp's 128-bit partial count to the launch total
+// (counts, (low, high)) and raise the stop flag once the total reaches the
+// target.  Call from one lane.
+__device__ __forceinline__ void ctl_publish(const PgRunCtl &c, unsigned long long *counts, unsigned __int128 x) {
+    if (!x) return;
+    atomic_add_u128(counts, x);
+    // high word first: a torn read can only under-estimate
+    const unsigned long long hi = *(volatile unsigned long long *)(counts + 1);
+    const unsigned long long lo = *(volatile unsigned long long *)counts;
+    if (hi || lo >= c.target) atomicExch(c.words, 1ull);
+}

@@ -39,6 +39,7 @@ struct MatchArgs {
     int *out;                    // capacity rows of k ints
     unsigned long long capacity;
     unsigned long long *n_total;
+    PgRunCtl ctl; // work budget (polled between tasks and first-level candidates)
 };
 
 // Rows for the candidates buf[0, n) of the last level l (lanes stride rows).
@@ -81,6 +82,7 @@ __device__ void list_task(const MatchArgs &a, int v, const PgOrder &ord, int *wb
         if (l == L - 1) emit(a, ord, l, m, buf, sz[l], lane);
         while (l >= 1 && (l == L - 1 || idx[l] >= sz[l])) --l;
         if (l < 1) break;
+        if (l == 1 && a.ctl.words && ctl_stop(a.ctl, lane)) break;
         m[l] = wbuf[a.lvl_off[l] + idx[l]];
         ++idx[l];
         ++l;
@@ -91,7 +93,9 @@ __global__ void __launch_bounds__(kBlock) k_match_list(MatchArgs a) {
     const int lane = threadIdx.x & 31;
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     int *wbuf = a.scratch + gw * a.warp_stride;
+    if (a.ctl.words && lane == 0) ctl_begin(a.ctl);
     for (;;) {
+        if (a.ctl.words && ctl_stop(a.ctl, lane)) break;
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(a.queue, 1ull);
         t = __shfl_sync(PG_FULL, t, 0) + a.task_begin;
@@ -118,7 +122,9 @@ size_t pg_match_scratch_bytes(const pg_graph *g, const pg_plan *p) {
 }
 
 int pg_launch_match(pg_graph *g, const pg_plan *p, int64_t rank_begin, int64_t rank_end, int32_t *out,
-                    unsigned long long capacity, unsigned long long *n_total_dev, cudaStream_t s) {
+                    unsigned long long capacity, unsigned long long *n_total_dev, cudaStream_t s,
+                    const PgRunCtl *ctl) {
+    if (p->h.big_clique) return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices run on the k-clique kernel only");
     PG_CUDA(cudaMemsetAsync(n_total_dev, 0, sizeof(unsigned long long), s));
     if (rank_end <= rank_begin || p->h.list_orders.empty()) return PG_OK;
     MatchArgs a;
@@ -138,6 +144,7 @@ int pg_launch_match(pg_graph *g, const pg_plan *p, int64_t rank_begin, int64_t r
     a.out = out;
     a.capacity = capacity;
     a.n_total = n_total_dev;
+    a.ctl = ctl ? *ctl : PgRunCtl{};
     PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
     k_match_list<<<match_grid(g), kBlock, 0, s>>>(a);
     PG_CUDA(cudaGetLastError());

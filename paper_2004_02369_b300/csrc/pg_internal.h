@@ -36,6 +36,20 @@ struct DevGraph {
 
 #define PG_MAX_QUEUES 64
 
+// Run control of one persistent launch: early termination (existence
+// queries, Section 5.4) and a device work budget.  `words` (device, zeroed
+// before the launch): [0] stop flag, [1] set when the budget ran out, [2]
+// start time of the launch in %globaltimer nanoseconds (first warp to poll).
+// A warp polls between tasks and between first-level candidates, so a
+// launch ends soon after the stop flag is raised.
+struct PgRunCtl {
+    unsigned long long *words = nullptr; // null: no polling at all
+    unsigned long long target = 0;       // > 0: stop once the count reaches target
+    unsigned long long budget_ns = 0;    // > 0: stop after this much device time
+};
+// queue words of an execution context reserved for run control
+#define PG_CTL_WORDS_SLOT (PG_MAX_QUEUES - 4)
+
 // Per-launch-stream device state: the scratch arena (grown on demand), the
 // work-queue counters and small count buffers.  Launches that may overlap on
 // the device use different contexts.
@@ -103,11 +117,22 @@ struct pg_graph {
     // launches take every sample_stride-th start vertex (timing samples of
     // pg_autotune only; 1 otherwise)
     int sample_stride = 1;
+    // device work budget of the synchronous calls (pg_set_time_budget), ns; 0 = none
+    unsigned long long budget_ns = 0;
 };
+
+// Run control of a synchronous call on g: the graph's work budget (if any)
+// and, for existence queries, a target.  Zeroes the control words on s.
+int pg_run_ctl(pg_graph *g, unsigned long long target, cudaStream_t s, PgRunCtl *out);
+// PG_ETIMEOUT if the launch behind ctl ran out of budget (synchronises s).
+int pg_run_ctl_check(const PgRunCtl &ctl, cudaStream_t s);
 
 #define PG_STATIC_SCRATCH_BYTES (32u << 20) // fixed scratch of pg_count_cliques_noalloc
 
 struct pg_batch;
+
+// pattern vertices of a plan (cliques above PGP_MAXK keep no pattern matrix)
+inline int pg_plan_size(const PgPlanHost &h) { return h.big_clique ? h.clique_k : h.pat.k; }
 
 struct pg_plan {
     PgPlanHost h;
@@ -141,10 +166,9 @@ int pg_plan_upload(pg_plan *p);
 
 // count_generic.cu (persistent = dynamic task queue over a resident grid;
 // otherwise one warp per task, one launch per pattern)
-// target > 0: existence mode, stop once the count reaches target (*stop = 1)
+// ctl (may be null): existence mode (target) and work budget
 int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev,
-                      int queue_slot, bool persistent, cudaStream_t s,
-                      unsigned long long target = 0, unsigned long long *stop = nullptr);
+                      int queue_slot, bool persistent, cudaStream_t s, const PgRunCtl *ctl = nullptr);
 size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persistent);
 // per-warp level buffers of a level program (offsets per level, total ints)
 long long pg_level_layout(const pg_graph *g, const std::vector<PgOrder> &orders, bool listing, long long *off);
@@ -152,14 +176,16 @@ long long pg_level_layout(const pg_graph *g, const std::vector<PgOrder> &orders,
 // match_list.cu: listing of the matches whose start vertex has rank in
 // [rank_begin, rank_end); rows of k original ids (-1 at anti-vertices)
 int pg_launch_match(pg_graph *g, const pg_plan *p, int64_t rank_begin, int64_t rank_end, int32_t *out,
-                    unsigned long long capacity, unsigned long long *n_total_dev, cudaStream_t s);
+                    unsigned long long capacity, unsigned long long *n_total_dev, cudaStream_t s,
+                    const PgRunCtl *ctl = nullptr);
 size_t pg_match_scratch_bytes(const pg_graph *g, const pg_plan *p);
 
 // count_clique.cu: sizes kmin..kmax in one launch, counts_dev[2*(k-kmin)]
+// (sizes up to PG_MAX_CLIQUE; ctl: existence mode / work budget, may be null)
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
-                     int queue_slot, cudaStream_t s);
-size_t pg_clique_scratch_bytes(const pg_graph *g);
-size_t pg_clique_slab_bytes(const pg_graph *g);
+                     int queue_slot, cudaStream_t s, const PgRunCtl *ctl = nullptr);
+size_t pg_clique_scratch_bytes(const pg_graph *g, int kmax);
+size_t pg_clique_slab_bytes(const pg_graph *g, int kmax);
 
 // fsm.cu
 int pg_fsm_run(pg_graph *g, int max_edges, unsigned long long threshold, pg_fsm_pattern *out, int64_t capacity,
@@ -180,6 +206,6 @@ int pg_batch_slots(const pg_batch *b);
 bool pg_batch_labeled(const pg_batch *b);
 size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b);
 int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts_dev, int queue_slot,
-                      cudaStream_t s);
+                      cudaStream_t s, const PgRunCtl *ctl = nullptr);
 int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
                         unsigned long long *queue, void *slabs, long long max_warps, cudaStream_t s);

@@ -514,6 +514,7 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
         for (int w = 0; w < k; ++w)
             if (u != w && p.rel[u][w] != 1) clique = false;
     out.is_clique = clique && k >= 2;
+    out.clique_k = out.is_clique ? k : 0;
     out.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return PG_OK;
 }

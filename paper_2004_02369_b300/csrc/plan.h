@@ -90,6 +90,9 @@ struct PgPlanHost {
     int n_regular = 0;
     int counted_group = 1;
     bool is_clique = false;               // k-clique (edge- or vertex-induced), unlabeled
+    int clique_k = 0;                     // k of a k-clique plan (any size), else 0
+    bool big_clique = false;              // k-clique with k > PGP_MAXK: no level program,
+                                          // counted by the k-clique kernel only (pat unused)
     bool labeled = false;
     bool anti_vertices = false;           // pattern has anti-vertices (checks in the orders)
     std::vector<PgOrder> orders;          // counting program: last level counted

@@ -12,6 +12,13 @@
 // up).  With serial = 1 the same kernels run one query per launch, one
 // launch at a time -- the one-query-at-a-time baseline.
 //
+// A query time limit (query_timeout_s) becomes the device work budget of
+// the launch that counts it (the smallest remaining time over the batch):
+// the kernels stop when it runs out and every query of that launch gets
+// PG_ETIMEOUT, so one slow pattern cannot hold a stream indefinitely.  A
+// stream whose launch fails with a device error is retired and its queries
+// get PG_EDEVICE; when no stream is left, waiting queries fail the same way.
+//
 // Section 5.1 processing model (tasks = start vertices) applied to a stream
 // of patterns; the paper itself runs one mining program at a time.
 #include <algorithm>
@@ -47,6 +54,8 @@ struct Slot {
     pg_batch *batch = nullptr;
     double t_start = 0;
     bool busy = false;
+    bool dead = false;     // retired after a device error
+    PgRunCtl ctl;          // run control of the launch in flight
 };
 
 constexpr size_t kAreaBytes = 4u << 20;
@@ -109,23 +118,53 @@ void emit(pg_server *S, const ServerQuery &q, int status, const uint64_t *cnt, d
     S->results.push_back(r);
 }
 
+// Work budget of a launch counting qs: the smallest remaining query time
+// (ns), 0 without a limit; false if some query has no time left (reported).
+bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
+    s.view.budget_ns = 0;
+    if (S->cfg.query_timeout_s <= 0) return true;
+    const double now = S->now();
+    double left = 1e300;
+    for (auto &q : qs) left = std::min(left, S->cfg.query_timeout_s - (now - q.t_submit));
+    if (left <= 0) {
+        for (auto &q : qs) emit(S, q, PG_ETIMEOUT, nullptr, now, now, (int)qs.size());
+        S->outstanding -= (int64_t)qs.size();
+        return false;
+    }
+    s.view.budget_ns = (unsigned long long)(left * 1e9) + 1;
+    return true;
+}
+
+// After the counts: copy the timed-out flag of the launch behind the host
+// counts, then record completion.
+void finish_launch(Slot &s, size_t n) {
+    unsigned long long *flag = (unsigned long long *)(s.h_counts + 2 * PG_MAX_QUEUES);
+    *flag = 0;
+    cudaMemcpyAsync(s.h_counts, s.d_counts, 2 * sizeof(uint64_t) * n, cudaMemcpyDeviceToHost, s.stream);
+    if (s.ctl.words)
+        cudaMemcpyAsync(flag, s.ctl.words + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s.stream);
+    cudaEventRecord(s.done, s.stream);
+}
+
 // An anti-vertex query runs alone on the plan interpreter (batches refuse
 // anti-vertex plans); returns 1 if launched.
 int launch_alone(pg_server *S, Slot &s, const ServerQuery &q) {
+    std::vector<ServerQuery> one{q};
+    if (!set_budget(S, s, one)) return 0;
     int rc = pg_plan_upload(q.plan);
     if (rc == PG_OK && pg_generic_scratch_bytes(&s.view, q.plan, true) > s.ex.scratch_bytes) rc = PG_ENOMEM;
     if (rc == PG_OK && cudaMemsetAsync(s.d_counts, 0, 2 * sizeof(uint64_t), s.stream) != cudaSuccess) rc = PG_EDEVICE;
+    if (rc == PG_OK) rc = pg_run_ctl(&s.view, 0, s.stream, &s.ctl);
     if (rc == PG_OK) {
         s.t_start = S->now();
-        rc = pg_launch_generic(&s.view, q.plan, (unsigned long long *)s.d_counts, 0, true, s.stream);
+        rc = pg_launch_generic(&s.view, q.plan, (unsigned long long *)s.d_counts, 0, true, s.stream, &s.ctl);
     }
     if (rc != PG_OK) {
         emit(S, q, rc, nullptr, S->now(), S->now(), 1);
         S->outstanding--;
         return 0;
     }
-    cudaMemcpyAsync(s.h_counts, s.d_counts, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s.stream);
-    cudaEventRecord(s.done, s.stream);
+    finish_launch(s, 1);
     s.batch = nullptr;
     s.qs = {q};
     s.busy = true;
@@ -154,15 +193,18 @@ int launch_batch(pg_server *S, Slot &s, std::vector<ServerQuery> qs) {
         if (rc == PG_OK) {
             const size_t need = pg_batch_scratch_bytes(&s.view, b);
             if (need <= s.ex.scratch_bytes) {
+                if (!set_budget(S, s, qs)) {
+                    pg_batch_free(b);
+                    return 0;
+                }
                 rc = pg_batch_stage(b, s.d_area, s.h_area, s.area_bytes, s.stream);
+                if (rc == PG_OK) rc = pg_run_ctl(&s.view, 0, s.stream, &s.ctl);
                 if (rc == PG_OK) {
                     s.t_start = S->now();
-                    rc = pg_launch_batched(&s.view, b, (unsigned long long *)s.d_counts, 0, s.stream);
+                    rc = pg_launch_batched(&s.view, b, (unsigned long long *)s.d_counts, 0, s.stream, &s.ctl);
                 }
                 if (rc == PG_OK) {
-                    cudaMemcpyAsync(s.h_counts, s.d_counts, 2 * sizeof(uint64_t) * qs.size(), cudaMemcpyDeviceToHost,
-                                    s.stream);
-                    cudaEventRecord(s.done, s.stream);
+                    finish_launch(s, qs.size());
                     s.batch = b;
                     s.qs = qs;
                     s.busy = true;
@@ -192,15 +234,40 @@ int launch_batch(pg_server *S, Slot &s, std::vector<ServerQuery> qs) {
     return 0;
 }
 
+// Fail every waiting query with `status` (no stream left to run them).
+void fail_pending(pg_server *S, int status) {
+    std::deque<ServerQuery> qs;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        qs.swap(S->pending);
+    }
+    const double t = S->now();
+    for (auto &q : qs) emit(S, q, status, nullptr, t, t, 0);
+    S->outstanding -= (int64_t)qs.size();
+}
+
 void worker_loop(pg_server *S) {
     cudaSetDevice(S->device);
     const int max_batch = S->cfg.serial ? 1 : std::max(1, std::min(S->cfg.max_batch, (int)PG_MAX_QUEUES));
     while (!S->stop.load()) {
         bool progress = false;
         for (Slot &s : S->slots) {
-            if (!s.busy || cudaEventQuery(s.done) != cudaSuccess) continue;
+            if (!s.busy) continue;
+            const cudaError_t e = cudaEventQuery(s.done);
+            if (e == cudaErrorNotReady) continue;
             const double t = S->now();
-            for (size_t i = 0; i < s.qs.size(); ++i) emit(S, s.qs[i], PG_OK, s.h_counts + 2 * i, s.t_start, t, (int)s.qs.size());
+            if (e != cudaSuccess) {
+                // a failed launch or a device error: these queries fail, the
+                // stream is retired
+                cudaGetLastError();
+                for (auto &q : s.qs) emit(S, q, PG_EDEVICE, nullptr, s.t_start, t, (int)s.qs.size());
+                s.dead = true;
+            } else {
+                const bool timed_out = *(const unsigned long long *)(s.h_counts + 2 * PG_MAX_QUEUES) != 0;
+                for (size_t i = 0; i < s.qs.size(); ++i)
+                    emit(S, s.qs[i], timed_out ? PG_ETIMEOUT : PG_OK, timed_out ? nullptr : s.h_counts + 2 * i,
+                         s.t_start, t, (int)s.qs.size());
+            }
             S->outstanding -= (int64_t)s.qs.size();
             pg_batch_free(s.batch);
             s.batch = nullptr;
@@ -208,8 +275,10 @@ void worker_loop(pg_server *S) {
             s.busy = false;
             progress = true;
         }
+        bool any_alive = false;
         for (Slot &s : S->slots) {
-            if (s.busy) continue;
+            any_alive |= !s.dead;
+            if (s.busy || s.dead) continue;
             std::vector<ServerQuery> take;
             {
                 std::lock_guard<std::mutex> lock(S->mu);
@@ -223,6 +292,10 @@ void worker_loop(pg_server *S) {
             progress = true;
             if (S->cfg.serial) break;
         }
+        if (!any_alive) {
+            fail_pending(S, PG_EDEVICE);
+            progress = false;
+        }
         if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
@@ -231,6 +304,7 @@ void worker_loop(pg_server *S) {
 
 extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_server **out) {
     if (!g || !cfg || !out) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (!(cfg->query_timeout_s >= 0.0)) return pg_set_error(PG_EINVAL, "query_timeout_s must be >= 0");
     *out = nullptr;
     pg_server *S = new (std::nothrow) pg_server();
     if (!S) return pg_set_error(PG_ENOMEM, "host allocation failed");
@@ -259,12 +333,13 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
         s.view.is_view = true;
         s.view.batch_cache = nullptr;
         s.view.batch_key.clear();
+        s.view.budget_ns = 0;
         if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaMalloc(&s.d_area, kAreaBytes)) != cudaSuccess ||
             (e = cudaMallocHost(&s.h_area, kAreaBytes)) != cudaSuccess ||
             (e = cudaMalloc(&s.d_counts, 2 * sizeof(uint64_t) * PG_MAX_QUEUES)) != cudaSuccess ||
-            (e = cudaMallocHost(&s.h_counts, 2 * sizeof(uint64_t) * PG_MAX_QUEUES)) != cudaSuccess) {
+            (e = cudaMallocHost(&s.h_counts, 2 * sizeof(uint64_t) * PG_MAX_QUEUES + sizeof(uint64_t))) != cudaSuccess) {
             rc = pg_cuda_error(e, "server stream setup");
             break;
         }

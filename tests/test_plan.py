@@ -163,8 +163,14 @@ def test_invalid_patterns_rejected():
     with pytest.raises(pg.PgError) as e:
         pg.Plan(3, [(0, 1)])  # vertex 2 disconnected
     assert e.value.code == pg.PG_EINVAL
-    with pytest.raises(pg.PgError):
-        pg.Plan(9, sg.clique_edges(9))
+    with pytest.raises(pg.PgError):  # above 8 vertices only cliques
+        pg.Plan(9, [(i, i + 1) for i in range(8)])
+    with pytest.raises(pg.PgError):  # cliques up to 16
+        pg.Plan(17, sg.clique_edges(17))
+    with pytest.raises(pg.PgError):  # a 9-clique without one edge
+        pg.Plan(9, sg.clique_edges(9)[1:])
+    with pytest.raises(pg.PgError):  # labeled large clique
+        pg.Plan(10, sg.clique_edges(10), labels=[0] * 10)
     with pytest.raises(pg.PgError):
         pg.Plan(3, [(0, 1), (1, 2)], anti_edges=[(0, 1)])
     with pytest.raises(pg.PgError):
@@ -173,6 +179,22 @@ def test_invalid_patterns_rejected():
         pg.Plan(3, [(0, 1), (1, 2)], anti_vertex=[0, 0, 1])
     with pytest.raises(pg.PgError):  # labeled anti-vertex
         pg.Plan(3, [(0, 1)], anti_edges=[(2, 0)], anti_vertex=[0, 0, 1], labels=[-1, -1, 2])
+
+
+def test_large_clique_plans():
+    """Cliques of 9..16 vertices compile to the clique's total order (no
+    level program): |Aut| = k!, k - 1 order pairs, the k-clique kernel."""
+    import math
+    pg = _pg()
+    for k in (9, 12, 14, 16):
+        p = pg.Plan(k, sg.clique_edges(k), vertex_induced=(k % 2 == 0))
+        info = p.info()
+        assert info.k == k and info.n_regular == k
+        assert info.automorphisms == math.factorial(k)
+        assert info.n_po == k - 1
+        assert [(info.po[2 * i], info.po[2 * i + 1]) for i in range(k - 1)] == [(i, i + 1) for i in range(k - 1)]
+        assert info.kernel == pg.KERNEL_CLIQUE and info.n_orders == 0
+        assert "k-clique kernel" in p.describe()
 
 
 def test_every_generated_pattern_plans_match_oracle():

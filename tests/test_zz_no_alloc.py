@@ -53,6 +53,26 @@ def test_noalloc_matches_regular_entry_point(pg, which):
     assert second == want
 
 
+def test_noalloc_allocates_nothing_on_a_fresh_graph(pg):
+    """After one warm-up call (which loads the kernel and the array), a call
+    on a graph never counted through the allocating entry points leaves the
+    device's free memory unchanged, and its counts equal the oracle's."""
+    import torch
+    import oracle
+    warm = pg.Graph.from_synth(sg.chung_lu(2000, 12000, 2.1, 200.0, 205))
+    _noalloc(pg, warm, 3, 6)
+    g = sg.chung_lu(3000, 30000, 2.1, 500.0, 206)
+    G = pg.Graph.from_synth(g)
+    out = torch.full((8,), -1, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        pg.count_cliques_noalloc(G, 3, 6, out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before
+        assert pg.decode_counts(out) == [oracle.kcliques(g, k) for k in range(3, 7)]
+
+
 def test_noalloc_rejects_oversized_and_bad_sizes(pg):
     import torch
     G = pg.Graph.from_synth(sg.complete_graph(1400))  # out-degree 1399: fewer slabs than SMs
