@@ -14,6 +14,9 @@ adds the few closed forms that are easier to read in Python:
 * ``fsm_mni``          labeled frequent subgraphs up to three edges with MNI
                        support (Section 2.1 FSM / MNI; Section 3.2.1 label
                        discovery), by per-vertex existence of a match.
+* ``domain_sizes``     MNI domains by their definition, vertex by vertex
+                       (backtracking from u -> v, first hit); checks the
+                       table-based FSM oracle above.
 """
 from __future__ import annotations
 
@@ -73,6 +76,9 @@ def lib():
         L.or_kcliques.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_int64, u64p]
         L.or_motif4_noninduced.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, u64p]
+        L.or_domain_sizes.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), ctypes.c_int, u64p]
+        L.or_domain_member.argtypes = [ctypes.POINTER(_Graph), ctypes.POINTER(_Pattern), ctypes.c_int,
+                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
         L.or_fsm_domains.argtypes = [ctypes.POINTER(_Graph), ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 8
         _lib = L
     return _lib
@@ -200,6 +206,28 @@ def mni_domains_bruteforce(g, p: dict) -> list[int]:
     out = (ctypes.c_uint64 * MAXK)()
     _check(lib().or_mni_bruteforce(ctypes.byref(gr.s), ctypes.byref(_pattern_struct(p)), out))
     return [int(out[i]) for i in range(p["k"])]
+
+
+def domain_sizes(g, p: dict, threads: int = 0) -> list[int]:
+    """|D(u)| per pattern vertex by per-vertex existence of a map u -> v
+    (first hit ends the search); MNI support = min over regular vertices."""
+    gr = _GraphRef(g)
+    out = (ctypes.c_uint64 * MAXK)()
+    _check(lib().or_domain_sizes(ctypes.byref(gr.s), ctypes.byref(_pattern_struct(p)), threads, out))
+    return [int(out[i]) for i in range(p["k"])]
+
+
+def domain_member(g, p: dict, u: int, v: int) -> bool:
+    gr = _GraphRef(g)
+    m = ctypes.c_int()
+    _check(lib().or_domain_member(ctypes.byref(gr.s), ctypes.byref(_pattern_struct(p)), u, v, ctypes.byref(m)))
+    return bool(m.value)
+
+
+def mni_support(g, p: dict, threads: int = 0) -> int:
+    """MNI support (Section 2.1): the smallest domain over pattern vertices."""
+    d = domain_sizes(g, p, threads)
+    return min(d[u] for u in range(p["k"]) if not (p.get("anti_vertex") or [0] * p["k"])[u])
 
 
 def triangles(g, threads: int = 0) -> int:

@@ -35,6 +35,10 @@
  *                    sends it to; support = the smallest such set.
  *  or_fsm_domains    domain sizes of every labeled pattern with 1..3 edges by
  *                    per-vertex search (see the function).
+ *  or_domain_sizes   MNI domains by their plain definition, one vertex at a
+ *                    time: v is in D(u) iff backtracking from u -> v finds
+ *                    one valid map (first hit ends the search).  Shares no
+ *                    shortcut with or_fsm_domains, so it checks it.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -364,6 +368,81 @@ int or_mni_bruteforce(const or_graph *g, const or_pattern *p, uint64_t *domain_s
         domain_size_out[u] = s;
     }
     free(m.dom);
+    return OR_OK;
+}
+
+/* ---------------------------- domain membership ---------------------------- */
+
+/* BFS order of the regular vertices rooted at `root`. */
+static int make_order_from(const or_pattern *p, int root, bfs_order *o) {
+    int k = p->k, seen[OR_MAXK] = {0};
+    if (root < 0 || root >= k || p->anti_vertex[root]) return OR_EINVAL;
+    o->order[0] = root; o->parent[0] = -1; seen[root] = 1; o->nreg = 1;
+    for (int i = 0; i < o->nreg; ++i) {
+        int u = o->order[i];
+        for (int w = 0; w < k; ++w) {
+            if (seen[w] || p->anti_vertex[w] || pat_rel(p, u, w) != 1) continue;
+            seen[w] = 1;
+            o->order[o->nreg] = w; o->parent[o->nreg] = i; o->nreg++;
+        }
+    }
+    int nreg_total = 0;
+    for (int u = 0; u < k; ++u) nreg_total += !p->anti_vertex[u];
+    return o->nreg == nreg_total ? OR_OK : OR_EINVAL;
+}
+
+/* 1 as soon as one valid completion of the positions pos.. exists. */
+static int bt_exists(bt_ctx *c, int pos) {
+    if (pos == c->o.nreg) return anti_vertices_ok(c);
+    int u = c->o.order[pos];
+    int64_t par = c->phi[c->o.order[c->o.parent[pos]]];
+    for (int64_t e = c->g->off[par]; e < c->g->off[par + 1]; ++e) {
+        int64_t x = c->g->adj[e];
+        if (!compatible(c, pos, x)) continue;
+        c->phi[u] = x;
+        if (bt_exists(c, pos + 1)) return 1;
+    }
+    return 0;
+}
+
+/* Is data vertex v the image of pattern vertex u under some valid map? */
+int or_domain_member(const or_graph *g, const or_pattern *p, int u, int64_t v, int *member) {
+    if (validate_pattern(p) || v < 0 || v >= g->n) return OR_EINVAL;
+    bt_ctx c;
+    c.g = g; c.p = p;
+    if (make_order_from(p, u, &c.o)) return OR_EINVAL;
+    *member = 0;
+    if (!compatible(&c, 0, v)) return OR_OK;
+    c.phi[u] = v;
+    *member = bt_exists(&c, 1);
+    return OR_OK;
+}
+
+/* |D(u)| for every pattern vertex u (0 for anti-vertices): the number of
+ * data vertices v with or_domain_member(u, v).  OpenMP over v. */
+int or_domain_sizes(const or_graph *g, const or_pattern *p, int nthreads, uint64_t *size_out) {
+    if (validate_pattern(p)) return OR_EINVAL;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    for (int u = 0; u < p->k; ++u) {
+        size_out[u] = 0;
+        if (p->anti_vertex[u]) continue;
+        bfs_order o;
+        if (make_order_from(p, u, &o)) return OR_EINVAL;
+        uint64_t s = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : s)
+        for (int64_t v = 0; v < g->n; ++v) {
+            bt_ctx c;
+            c.g = g; c.p = p; c.o = o;
+            if (!compatible(&c, 0, v)) continue;
+            c.phi[u] = v;
+            s += (uint64_t)bt_exists(&c, 1);
+        }
+        size_out[u] = s;
+    }
     return OR_OK;
 }
 

@@ -69,3 +69,23 @@ def test_fsm_chunglu_500k_full(pg):
     g = sg.workload_graph(4)
     G = pg.Graph.from_synth(g)
     assert pg.fsm(G, threshold=1000) == want
+
+
+def test_fsm_full_size_against_domain_search(pg):
+    """Full FSM workload: pg_fsm's supports against the per-vertex domain
+    search oracle (oracle.domain_sizes, first-hit backtracking from u -> v,
+    no label-count shortcut) on its stored seeded sample: every sampled
+    frequent pattern over the five shapes has that support, and every sampled
+    infrequent candidate is absent from the result."""
+    search = json.load(open(GOLDEN))["fsm_domains"]["counts"]
+    g = sg.workload_graph(4)
+    G = pg.Graph.from_synth(g)
+    got = {f"{shape}:{','.join(map(str, labels))}": v for (shape, labels), v in pg.fsm(G, threshold=1000).items()}
+    n_freq = 0
+    for key, v in search.items():
+        if int(v) >= 1000:
+            assert got.get(key) == int(v), key
+            n_freq += 1
+        else:
+            assert key not in got, key
+    assert n_freq >= 2000

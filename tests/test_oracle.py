@@ -429,6 +429,142 @@ def test_fsm_antimonotone():
             assert s <= sup[("wedge", (c, min(b, d), max(b, d)))]
 
 
+# ---------------------------------------- MNI domains, vertex by vertex ----
+#
+# oracle.domain_sizes decides v in D(u) by backtracking from u -> v until the
+# first valid map: the definition of a domain (Section 2.1, MNI over all
+# isomorphisms) with no label-count shortcut.  It is pinned by networkx and
+# by enumerating every map, and it in turn checks the table-based FSM oracle
+# (oracle.fsm_supports), whose leaf positions are decided from label counts.
+
+DOMAIN_PATTERNS = [
+    sg.pattern(2, [(0, 1)]),
+    sg.pattern(3, sg.chain_edges(3)),
+    sg.pattern(3, sg.clique_edges(3)),
+    sg.pattern(4, sg.chain_edges(4)),
+    sg.pattern(4, sg.star_edges(4)),
+    sg.pattern(4, sg.cycle_edges(4)),
+    sg.pattern(5, sg.chain_edges(5)),                       # 4 edges
+    sg.pattern(5, [(0, 1), (0, 2), (0, 3), (3, 4)]),        # chair, 4 edges
+    sg.pattern(4, [(0, 1), (1, 2), (0, 2), (2, 3)]),        # tailed triangle
+    sg.pattern(4, sg.chain_edges(4), anti_edges=[(0, 3)]),
+    sg.pattern(4, sg.cycle_edges(4), vertex_induced=True),
+]
+
+
+def _labelled_variants(p, rng, nl):
+    out = [p]
+    for _ in range(2):
+        out.append(dict(p, labels=[int(x) for x in rng.integers(-1, nl, p["k"])]))
+    return out
+
+
+def test_domain_sizes_match_networkx_and_enumeration():
+    rng = np.random.default_rng(61)
+    graphs = [sg.erdos_renyi(16, 0.3, 62), sg.chung_lu(40, 100, 2.1, 14.0, 63), sg.from_edges(
+        9, [(0, 1), (0, 2), (0, 3), (0, 4), (0, 5), (1, 2), (3, 4), (5, 6), (6, 7), (7, 8), (8, 5)])]
+    for gi, g in enumerate(graphs):
+        g.labels = sg.uniform_labels(g.n, 3, 64 + gi)
+        G = to_nx(g)
+        for base in DOMAIN_PATTERNS:
+            for p in _labelled_variants(base, rng, 3):
+                d = oracle.domain_sizes(g, p)
+                assert d == oracle.mni_domains_bruteforce(g, p), (gi, p)
+                if not p["anti_edges"] and not p["vertex_induced"]:
+                    assert d == nx_domains(G, pat_nx(p)), (gi, p)
+                for u in range(p["k"]):  # single-vertex form agrees with the sizes
+                    assert sum(oracle.domain_member(g, p, u, v) for v in range(g.n)) == d[u]
+
+
+def _check_tables(g, nl, keys=None):
+    sup = oracle.fsm_supports(g, nl)
+    for key in (keys if keys is not None else sup):
+        shape, labels = key
+        want = oracle.mni_support(g, oracle.fsm_pattern(shape, labels))
+        assert sup[key] == want, (key, sup[key], want)
+    return sup
+
+
+def test_fsm_tables_match_domain_search_dense_tiny_graphs():
+    """Dense tiny graphs with 2-3 labels, every labeled pattern with 1..3
+    edges: labels that occur exactly once, twice or three times next to an
+    already used vertex (the cases the tables handle by subtraction and by
+    coincidence tests) occur throughout."""
+    rng = np.random.default_rng(65)
+    for i in range(60):
+        n = int(rng.integers(5, 12))
+        g = sg.erdos_renyi(n, float(rng.uniform(0.35, 0.8)), 660 + i)
+        nl = int(rng.integers(2, 4))
+        g.labels = sg.uniform_labels(g.n, nl, 760 + i)
+        _check_tables(g, nl)
+
+
+@pytest.mark.parametrize("n,m,gamma,w,seed", [(2000, 12000, 2.1, 400.0, 67), (5000, 30000, 2.3, 700.0, 68)])
+def test_fsm_tables_match_domain_search_hub_graphs(n, m, gamma, w, seed):
+    """Chung-Lu graphs with hubs and 20 Zipf(1.2) labels (the FSM workload's
+    label law): every edge, wedge and triangle, and 400 sampled paths and
+    stars (supported ones and unsupported ones), against the domain search."""
+    g = sg.chung_lu(n, m, gamma, w, seed)
+    g.labels = sg.zipf_labels(g.n, 20, 1.2, seed + 1)
+    sup = oracle.fsm_supports(g, 20)
+    rng = np.random.default_rng(seed + 2)
+    keys = [k for k in sup if k[0] in ("edge", "wedge", "triangle")]
+    for shape in ("path", "star"):
+        pos = [k for k in sup if k[0] == shape and sup[k] > 0]
+        zero = [k for k in sup if k[0] == shape and sup[k] == 0]
+        for pool, take in ((pos, 300), (zero, 100)):
+            idx = rng.choice(len(pool), min(take, len(pool)), replace=False)
+            keys += [pool[i] for i in idx]
+    assert max(sup[k] for k in keys) > 50  # hubs make large domains
+    _check_tables(g, 20, keys)
+
+
+def test_fsm_label_count_corner_cases_by_hand():
+    """Hand-built cases where a leaf label occurs exactly 1, 2 or 3 times
+    next to an already used vertex; expected supports derived by hand."""
+    def sup(n, edges, labels, shape, key):
+        g = sg.from_edges(n, edges)
+        g.labels = np.array(labels, dtype=np.int32)
+        tables = _check_tables(g, max(labels) + 1)
+        p = oracle.fsm_pattern(shape, key)
+        assert oracle.mni_support(g, p) == min(oracle.mni_domains_bruteforce(g, p))
+        return tables[(shape, key)]
+    # wedge leaf: the only label-1 neighbour of the centre is v itself
+    assert sup(3, [(0, 1), (1, 2)], [1, 0, 2], "wedge", (0, 1, 1)) == 0
+    assert sup(4, [(0, 1), (1, 2), (1, 3)], [1, 0, 2, 1], "wedge", (0, 1, 1)) == 1
+    # star leaf: two label-1 neighbours of the centre (one is v) vs three
+    assert sup(4, [(0, 1), (0, 2), (0, 3)], [0, 1, 1, 2], "star", (0, 1, 1, 1)) == 0
+    assert sup(5, [(0, 1), (0, 2), (0, 3), (0, 4)], [0, 1, 1, 2, 1], "star", (0, 1, 1, 1)) == 1
+    assert sup(4, [(0, 1), (0, 2), (0, 3)], [0, 1, 1, 2], "star", (0, 1, 1, 2)) == 1
+    # path end: the only label-1 neighbour of u other than w is v (triangle)
+    assert sup(3, [(0, 1), (1, 2), (0, 2)], [1, 0, 0], "path", (0, 0, 1, 1)) == 0
+    assert sup(4, [(0, 1), (1, 2), (0, 2), (2, 3)], [1, 0, 0, 1], "path", (1, 0, 0, 1)) == 2
+    # path inner: the single a' next to v and the single d' next to w coincide
+    assert sup(3, [(0, 1), (0, 2), (1, 2)], [0, 0, 2], "path", (2, 0, 0, 2)) == 0
+    assert sup(4, [(0, 1), (0, 2), (1, 2), (1, 3)], [0, 0, 2, 2], "path", (2, 0, 0, 2)) == 2
+
+
+def test_fsm_full_size_two_oracles_agree():
+    """FSM workload at full size (Chung-Lu 500K / 5M, Zipf labels over 20,
+    threshold 1000): the stored supports of the per-vertex domain search
+    (seeded sample over all five shapes, frequent and infrequent candidates)
+    equal the table oracle's stored frequent set: equal supports where
+    frequent, below the threshold and absent where not."""
+    data = json.load(open(os.path.join(GOLDEN, "workload_counts.json")))
+    table = data["fsm"]["counts"]
+    search = data["fsm_domains"]["counts"]
+    shapes = {}
+    for key, v in search.items():
+        shape = key.split(":")[0]
+        if key in table:
+            assert int(table[key]) == int(v), key
+            shapes[shape] = shapes.get(shape, 0) + 1
+        else:
+            assert int(v) < 1000, key
+    assert set(shapes) == {"edge", "wedge", "triangle", "path", "star"}
+    assert sum(shapes.values()) >= 2000 and len(search) - sum(shapes.values()) >= 1000
+
+
 def test_labeled_counts_sum_to_unlabeled_closed_forms():
     """Summed over every label combination, labeled triangle and induced
     wedge counts give trace(A^3)/6 and sum C(d,2) - 3T: pins the oracle's
