@@ -11,7 +11,9 @@
 // one or more programs end is counted once by cardinality and adds
 // C(|S|, g) into each such plan's counter.  For the six induced 4-vertex
 // motifs the 22 programs share their first level (the start vertex's
-// out-neighbourhood) and most of their second.
+// out-neighbourhood) and most of their second.  Two counted patterns leave
+// the tree for kernels of their own: unlabeled k-cliques (the bitmap clique
+// kernel) and the unlabeled edge-induced 4-cycle (co-degree accumulation).
 //
 // GPU mapping: one warp per start vertex (device atomic queue, highest
 // degree first, Section 5.2); depth-first walk of the tree with an explicit
@@ -280,6 +282,7 @@ struct pg_batch {
     std::vector<PgPlanHost> slot_plans;
     std::vector<int> clique_k;          // per slot: k when counted by the clique kernel, else 0
     int clique_kmin = 0, clique_kmax = 0;
+    int c4_slot = -1;                   // slot of the unlabeled edge-induced 4-cycle (co-degree kernel)
     std::vector<int> out_first, out_n;  // per output plan: range in out_terms
     std::vector<int> term_slot;
     std::vector<long long> term_coef;   // signed, includes |Aut| of the term pattern
@@ -435,6 +438,24 @@ int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out
     return PG_OK;
 }
 
+namespace {
+// Unlabeled edge-induced 4-cycle without anti-edges or anti-vertices.
+bool is_plain_c4(const PgPlanHost &h) {
+    if (h.big_clique || h.labeled || h.anti_vertices || h.pat.k != 4) return false;
+    int edges = 0;
+    for (int u = 0; u < 4; ++u) {
+        int d = 0;
+        for (int w = 0; w < 4; ++w) {
+            if (h.pat.rel[u][w] == 2) return false;
+            d += h.pat.rel[u][w] == 1;
+        }
+        if (d != 2) return false;
+        edges += d;
+    }
+    return edges == 8; // 2-regular on 4 vertices, connected (plans are): the 4-cycle
+}
+}  // namespace
+
 int pg_batch_build_trie(pg_batch *b) {
     const int n_plans = (int)b->slot_plans.size();
     // tree with child lists, then laid out so that siblings are contiguous
@@ -458,6 +479,10 @@ int pg_batch_build_trie(pg_batch *b) {
             b->clique_k[p] = sp.pat.k;
             b->clique_kmin = b->clique_kmin ? std::min(b->clique_kmin, sp.pat.k) : sp.pat.k;
             b->clique_kmax = std::max(b->clique_kmax, sp.pat.k);
+            continue;
+        }
+        if (b->c4_slot < 0 && is_plain_c4(sp)) {
+            b->c4_slot = p;
             continue;
         }
         for (const PgOrder &o : b->slot_plans[p].orders) {
@@ -643,6 +668,7 @@ size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b) {
     long long off[PGP_MAXK];
     size_t bytes = (size_t)batched_grid(g) * batched_warps(g) * (size_t)batch_layout(g, b, off) * sizeof(int);
     if (b->clique_kmax) bytes = std::max(bytes, pg_clique_scratch_bytes(g, b->clique_kmax));
+    if (b->c4_slot >= 0) bytes = std::max(bytes, pg_c4_scratch_bytes(g));
     return bytes;
 }
 
@@ -687,6 +713,10 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
             if (b->clique_k[p])
                 PG_CUDA(cudaMemcpyAsync(b->d_slot_counts + 2 * p, g->ex->tmp_counts + 2 * (b->clique_k[p] - b->clique_kmin),
                                         2 * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    }
+    if (b->c4_slot >= 0) {
+        int rc = pg_launch_c4(g, b->d_slot_counts + 2 * b->c4_slot, queue_slot + 4, s, ctl);
+        if (rc) return rc;
     }
     k_combine<<<(b->n_out + 63) / 64, 64, 0, s>>>(b->d_slot_counts, b->d_term_slot, b->d_term_coef, b->d_out_first,
                                                  b->d_out_n, b->d_out_div, b->n_out, counts_dev);

@@ -1,0 +1,300 @@
+// Edge-induced 4-cycles by co-degree accumulation.
+//
+// The 4-cycle's exploration plan (Section 4.1) binds a path of three core
+// vertices and completes the fourth, non-core vertex by a set intersection
+// per matched path (Section 5.1).  On a GPU that is one intersection of two
+// adjacency lists per out-neighbour pair of the start vertex, which is the
+// dominant term of 4-vertex motif counting (Section 6, non-core completion
+// dominating the time).  This kernel counts the same number with the
+// non-core completion done by cardinality over a whole neighbourhood at once:
+//
+//   every 4-cycle has a unique vertex w of smallest degree rank (highest
+//   degree, Section 5.2 order); its opposite vertex x and its two cycle
+//   neighbours a, b all rank after w.  With c_w(x) = |{a in adj(w) : a > w,
+//   x in adj(a), x > w}| (x != a, b holds since the graph has no loops), the
+//   cycles anchored at w are sum over x of C(c_w(x), 2).
+//
+// Raising c_w(x) from k to k+1 adds k new pairs, so the count is the sum of
+// the counters' old values over all increments, and no pass over the
+// counters is needed.  The increments of w are the suffixes of adj(a) above
+// w for a in adj(w) above w; their total T_w is bounded by sum over a of
+// deg(a) * out-degree(a) (the Chiba-Nishizeki bound), so hubs are anchors of
+// few cycles' worth of work each.
+//
+// B300 mapping (two launches of one persistent grid of 4-warp CTAs):
+//  * first launch: anchors one per warp in rank order; counters live in a
+//    per-warp open-addressing hash table in shared memory sized for T_w.  An
+//    anchor of degree above kLightDeg, or with more than kLightT increments,
+//    is appended to a deferred list instead;
+//  * second launch: deferred anchors one per CTA; the counters are a dense
+//    n-entry array per CTA in global memory, incremented with atomicAdd and
+//    cleared by a second walk over the same suffixes.
+//  Both walk the suffixes 32 neighbours a at a time: lanes binary-search
+//  their a's suffix start, a warp prefix sum flattens the 32 suffixes, and
+//  lanes read the flattened increments with coalesced loads.
+#include "device_sets.cuh"
+
+namespace {
+
+constexpr int kWarps = 4;
+constexpr int kBlock = kWarps * 32;
+constexpr int kLightDeg = 512;        // light anchors: degree <= kLightDeg
+constexpr int kHashCap = 2048;        // per-warp hash slots (power of two)
+constexpr int kLightT = kHashCap / 2; // light anchors: at most this many increments
+constexpr int kEmpty = -1;
+
+struct C4Args {
+    DevGraph g;
+    int n;
+    unsigned *dense;        // per-CTA counter arrays of n entries, all zero between anchors
+    int *deferred;          // anchors left to the CTAs
+    unsigned long long *q;  // [0] warp cursor, [1] deferred count, [2] deferred cursor
+    unsigned long long *count; // (low, high)
+    int mode;               // 0: anchors per warp; 1: deferred anchors per CTA
+    int stride;             // every stride-th anchor (timing samples)
+    PgRunCtl ctl;
+};
+
+// Per-warp shared memory of the light path.
+struct WarpSmem {
+    int keys[kHashCap];
+    unsigned vals[kHashCap];
+    unsigned start[kLightDeg]; // suffix start in adj(a) (absolute adj index)
+    int len[kLightDeg];        // suffix length
+};
+
+__device__ __forceinline__ int upper_bound_g(const int *__restrict__ a, int len, int x) {
+    int lo = 0, hi = len;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a + mid) <= x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Suffix of adj(a) above w (lane-local): absolute start index and length.
+__device__ __forceinline__ void suffix_of(const DevGraph &g, int a, int w, unsigned *start, int *len) {
+    const int4 ai = __ldg(&g.vinfo[a]);
+    const int *aa = adj_of(g, ai);
+    const int q = upper_bound_g(aa, ai.y, w);
+    *start = ((unsigned)ai.x << 2) + (unsigned)q;
+    *len = ai.y - q;
+}
+
+// Walks the flattened suffixes of a chunk of up to 32 neighbours (lane j
+// holds neighbour j's suffix start and length) and calls f(x) for every
+// element, lanes reading consecutive elements.
+template <class F>
+__device__ __forceinline__ void walk_chunk(const DevGraph &g, unsigned my_start, int my_len, int lane, F &&f) {
+    int incl = my_len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(PG_FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(PG_FULL, incl, 31);
+    const int excl = incl - my_len;
+    for (int base = 0; base < total; base += 32) {
+        const int e = base + lane;
+        // owner: the last lane j with excl_j <= e (binary search over lanes)
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int ex = __shfl_sync(PG_FULL, excl, lo + step);
+            if (ex <= e) lo += step;
+        }
+        const unsigned st = __shfl_sync(PG_FULL, my_start, lo);
+        const int ex = __shfl_sync(PG_FULL, excl, lo);
+        if (e < total) f(__ldg(g.adj + (size_t)st + (unsigned)(e - ex)));
+    }
+}
+
+// Heavy anchor w by the whole CTA on the dense counters C.  Returns this
+// thread's share of the anchored count.
+__device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, int *s_next, int *s_p) {
+    const DevGraph &g = a.g;
+    const int lane = threadIdx.x & 31;
+    const int4 wi = __ldg(&g.vinfo[w]);
+    const int *aw = adj_of(g, wi);
+    if (threadIdx.x == 0) {
+        *s_p = upper_bound_g(aw, wi.y, w);
+        *s_next = 0;
+    }
+    __syncthreads();
+    const int p = *s_p, na = wi.y - p;
+    unsigned long long cnt = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(s_next, 32);
+            c = __shfl_sync(PG_FULL, c, 0);
+            if (c >= na) break;
+            unsigned st = 0;
+            int ln = 0;
+            if (c + lane < na) suffix_of(g, __ldg(aw + p + c + lane), w, &st, &ln);
+            if (pass == 0)
+                walk_chunk(g, st, ln, lane, [&](int x) { cnt += atomicAdd(C + x, 1u); });
+            else
+                walk_chunk(g, st, ln, lane, [&](int x) { C[x] = 0u; });
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) *s_next = 0;
+        __syncthreads();
+    }
+    return cnt;
+}
+
+__device__ __forceinline__ unsigned hash_inc(int *keys, unsigned *vals, unsigned mask, int x) {
+    unsigned s = ((unsigned)x * 0x9E3779B1u) >> 7;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        s &= mask;
+        const int k = keys[s];
+        if (k == x) return atomicAdd(vals + s, 1u);
+        if (k == kEmpty) {
+            const int prev = atomicCAS(keys + s, kEmpty, x);
+            if (prev == kEmpty || prev == x) return atomicAdd(vals + s, 1u);
+        }
+        ++s;
+    }
+    return 0u; // unreachable: the table is sized at twice the increments
+}
+
+// Light anchor w by one warp with a shared-memory hash table.  Returns
+// false (nothing counted) when its degree exceeds kLightDeg or its
+// increments exceed kLightT.
+__device__ bool light_anchor(const C4Args &a, int w, WarpSmem &sm, int lane, unsigned long long &cnt) {
+    const DevGraph &g = a.g;
+    const int4 wi = __ldg(&g.vinfo[w]);
+    if (wi.y > kLightDeg) return false;
+    const int *aw = adj_of(g, wi);
+    int p = 0;
+    if (lane == 0) p = upper_bound_g(aw, wi.y, w);
+    p = __shfl_sync(PG_FULL, p, 0);
+    const int na = wi.y - p;
+    if (na < 2) return true;
+    int total = 0;
+    for (int c = lane; c < na; c += 32) {
+        unsigned st;
+        int ln;
+        suffix_of(g, __ldg(aw + p + c), w, &st, &ln);
+        sm.start[c] = st;
+        sm.len[c] = ln;
+        total += ln;
+    }
+    total = __reduce_add_sync(PG_FULL, total);
+    if (total > kLightT) return false;
+    if (total < 2) return true;
+    unsigned cap = 64;
+    while (cap < 2u * (unsigned)total) cap <<= 1;
+    for (unsigned i = lane; i < cap; i += 32) {
+        sm.keys[i] = kEmpty;
+        sm.vals[i] = 0u;
+    }
+    __syncwarp();
+    const unsigned mask = cap - 1;
+    for (int c = 0; c < na; c += 32) {
+        unsigned st = 0;
+        int ln = 0;
+        if (c + lane < na) {
+            st = sm.start[c + lane];
+            ln = sm.len[c + lane];
+        }
+        walk_chunk(g, st, ln, lane, [&](int x) { cnt += hash_inc(sm.keys, sm.vals, mask, x); });
+    }
+    __syncwarp();
+    return true;
+}
+
+__global__ void __launch_bounds__(kBlock) k_count_c4(C4Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_task, s_next, s_p;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const bool polled = a.ctl.words != nullptr;
+    if (polled && threadIdx.x == 0) ctl_begin(a.ctl);
+    unsigned long long cnt = 0;
+    if (a.mode == 0) {
+        // ---- one warp per anchor, rank order; heavy ones deferred
+        WarpSmem &sm = ((WarpSmem *)smem_raw)[warp];
+        const long long n_tasks = ((long long)a.n + a.stride - 1) / a.stride;
+        for (;;) {
+            if (polled && ctl_stop(a.ctl, lane)) break;
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(a.q, 1ull);
+            t = __shfl_sync(PG_FULL, t, 0);
+            if ((long long)t >= n_tasks) break;
+            const int w = (int)(t * (unsigned long long)a.stride);
+            if (!light_anchor(a, w, sm, lane, cnt) && lane == 0) a.deferred[atomicAdd(a.q + 1, 1ull)] = w;
+        }
+    } else {
+        // ---- one CTA per deferred anchor, dense counters
+        unsigned *C = a.dense + (size_t)blockIdx.x * (size_t)a.n;
+        const unsigned long long n_def = *(volatile unsigned long long *)(a.q + 1);
+        for (;;) {
+            if (threadIdx.x == 0) {
+                int w = -1;
+                if (!polled || !ctl_poll(a.ctl)) {
+                    const unsigned long long t = atomicAdd(a.q + 2, 1ull);
+                    if (t < n_def) w = a.deferred[t];
+                }
+                s_task = w;
+            }
+            __syncthreads();
+            const int w = s_task;
+            __syncthreads();
+            if (w < 0) break;
+            cnt += dense_anchor(a, w, C, &s_next, &s_p);
+        }
+    }
+    const unsigned __int128 tot = warp_sum_u128(cnt);
+    if (lane == 0 && tot) atomic_add_u128(a.count, tot);
+}
+
+int c4_grid(const pg_graph *g, int *grid) {
+    int per_sm = 0;
+    const size_t smem = (size_t)kWarps * sizeof(WarpSmem);
+    PG_CUDA(cudaFuncSetAttribute(k_count_c4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_c4, kBlock, smem));
+    *grid = std::max(1, per_sm) * g->num_sms;
+    return PG_OK;
+}
+
+}  // namespace
+
+size_t pg_c4_scratch_bytes(const pg_graph *g) {
+    int grid = 0;
+    if (c4_grid(g, &grid) != PG_OK) grid = 2 * g->num_sms;
+    return (size_t)grid * (size_t)g->n * sizeof(unsigned) + (size_t)(g->n + 1) * sizeof(int) + 256;
+}
+
+// Adds the number of edge-induced 4-cycles of g into count_dev (128-bit,
+// low / high).  Uses the graph's scratch arena (pg_c4_scratch_bytes) and
+// queue words queue_slot .. queue_slot + 3.
+int pg_launch_c4(pg_graph *g, unsigned long long *count_dev, int queue_slot, cudaStream_t s, const PgRunCtl *ctl) {
+    if (g->n < 4) return PG_OK;
+    if (queue_slot + 3 > PG_CTL_WORDS_SLOT) return pg_set_error(PG_EINVAL, "queue slot out of range");
+    if (g->adj_entries >= (1ll << 32)) return pg_set_error(PG_EUNSUPPORTED, "4-cycle kernel: adjacency above 2^32 entries");
+    int grid = 0;
+    int rc = c4_grid(g, &grid);
+    if (rc) return rc;
+    const size_t dense_bytes = (size_t)grid * (size_t)g->n * sizeof(unsigned);
+    if (pg_c4_scratch_bytes(g) > g->ex->scratch_bytes) return pg_set_error(PG_ENOMEM, "scratch smaller than the 4-cycle kernel needs");
+    C4Args a;
+    a.g = g->d;
+    a.n = (int)g->n;
+    a.dense = (unsigned *)g->ex->scratch;
+    a.deferred = (int *)((unsigned char *)g->ex->scratch + dense_bytes);
+    a.q = g->ex->queues + queue_slot;
+    a.count = count_dev;
+    a.stride = std::max(1, g->sample_stride);
+    a.ctl = ctl ? *ctl : PgRunCtl{};
+    PG_CUDA(cudaMemsetAsync(a.dense, 0, dense_bytes, s));
+    PG_CUDA(cudaMemsetAsync(a.q, 0, 3 * sizeof(unsigned long long), s));
+    const size_t smem = (size_t)kWarps * sizeof(WarpSmem);
+    for (int mode = 0; mode < 2; ++mode) {
+        a.mode = mode;
+        k_count_c4<<<grid, kBlock, smem, s>>>(a);
+        PG_CUDA(cudaGetLastError());
+    }
+    return PG_OK;
+}

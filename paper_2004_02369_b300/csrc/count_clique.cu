@@ -79,7 +79,7 @@ struct CliqueArgs {
 // lane at 2 GHz) to wrap: checking after every start vertex and moving
 // counters of 2^62 or more into the 128-bit totals keeps the counts exact.
 template <int S>
-__device__ __forceinline__ void bump(unsigned long long *cnt, unsigned long long x, const CliqueArgs &) {
+__device__ __forceinline__ void bump(unsigned long long *cnt, unsigned long long x) {
     cnt[S] += x;
 }
 
@@ -115,6 +115,7 @@ struct Walker {
     int cws, nslots;
     int m;          // queued items
     int used;       // ring slots in use
+    int kmin;       // smallest size counted (cardinality pruning)
 };
 
 // Group-wide barrier: the CTA for heavy vertices, the warp for light ones.
@@ -214,10 +215,10 @@ __device__ __forceinline__ unsigned long long flush(const Tile &t, Walker &wk, i
 // level; the result counts into cnt[P].
 template <int P>
 __device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *C, int limit, int lane,
-                                     unsigned long long *cnt, const CliqueArgs &a) {
+                                     unsigned long long *cnt) {
     const int nw = (limit + 31) >> 5;
     if (wk.used == wk.nslots) {
-        bump<P>(cnt, flush(t, wk, lane), a);
+        bump<P>(cnt, flush(t, wk, lane));
         wk.used = 0;
     }
     const int slot = wk.used++;
@@ -227,7 +228,7 @@ __device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *
     for (int w = 0; w < nw; ++w) {
         const unsigned x = S[w];
         const int c = __popc(x);
-        if (wk.m + c > kItems) bump<P>(cnt, flush(t, wk, lane), a);
+        if (wk.m + c > kItems) bump<P>(cnt, flush(t, wk, lane));
         if ((x >> lane) & 1u) wk.items[wk.m + __popc(x & ((1u << lane) - 1))] = (slot << 16) | (w * 32 + lane);
         wk.m += c;
     }
@@ -240,18 +241,17 @@ __device__ __forceinline__ void emit(const Tile &t, Walker &wk, const unsigned *
 // whose extension N has fewer than kmin - P - 2 bits cannot lie in a
 // kmin-clique, and neither can any branch below it: skipped.
 template <int P, int KMAX, bool XT>
-__device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, int lane, unsigned long long *cnt,
-                     const CliqueArgs &a) {
+__device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, int kmax, int lane,
+                     unsigned long long *cnt) {
     if constexpr (P >= KMAX - 2) {
         return;
     } else {
-        const int kmax = a.kmax;
         if (P + 3 > kmax) return;
         if (P + 3 == kmax) {
-            emit<P>(t, wk, C, limit, lane, cnt, a);
+            emit<P>(t, wk, C, limit, lane, cnt);
             return;
         }
-        const bool prune = XT && a.kmin > P + 3;
+        const bool prune = XT && wk.kmin > P + 3;
         const int nw = (limit + 31) >> 5;
         unsigned *N = wk.cbuf + (size_t)P * wk.cws;
         for (int w = 0; w < nw; ++w) {
@@ -267,10 +267,10 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
                     N[v] = y;
                     c += __popc(y);
                 }
-                bump<P>(cnt, c, a);
+                bump<P>(cnt, c);
                 __syncwarp();
-                if (!prune || (int)__reduce_add_sync(PG_FULL, c) >= a.kmin - P - 2)
-                    walk<P + 1, KMAX, XT>(t, wk, N, l, lane, cnt, a);
+                if (!prune || (int)__reduce_add_sync(PG_FULL, c) >= wk.kmin - P - 2)
+                    walk<P + 1, KMAX, XT>(t, wk, N, l, kmax, lane, cnt);
                 __syncwarp();
             }
         }
@@ -286,7 +286,7 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
 //   6-cliques:  sum_a sum_{b in B_a} sum_{q in B_a & B_b} popc(B_a & B_b & B_q)
 // Returns false (nothing counted) when R_i has more than 32 bits.
 __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, unsigned *bsh, int lane,
-                                               unsigned long long *cnt, const CliqueArgs &a) {
+                                               unsigned long long *cnt) {
     const unsigned *Ri = t.rows + (size_t)i * t.ws;
     const int nw = (i + 31) >> 5;
     int c = 0;
@@ -320,7 +320,7 @@ __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, u
             pre += __popc(riw);
         }
     }
-    bump<1>(cnt, __popc(B), a);
+    bump<1>(cnt, __popc(B));
     if (kmax >= 5) {
         bsh[lane] = B;
         __syncwarp();
@@ -340,38 +340,52 @@ __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, u
                 }
             }
         }
-        bump<2>(cnt, s5, a);
-        bump<3>(cnt, s6, a);
+        bump<2>(cnt, s5);
+        bump<3>(cnt, s6);
         __syncwarp();
     }
     return true;
 }
 
-// Pending products of the last level belong to size kmax: cnt[kmax - 3].
+// Pending products of the last level belong to size kmax: cnt[kmax - 3]
+// (a switch over constant indices).
 template <int KMAX>
-__device__ __forceinline__ void drain(const Tile &t, Walker &wk, int lane, unsigned long long *cnt,
-                                      const CliqueArgs &a) {
+__device__ __forceinline__ void drain(const Tile &t, Walker &wk, int kmax, int lane, unsigned long long *cnt) {
     if (wk.m == 0) {
         wk.used = 0;
         return;
     }
-    cnt[a.kmax - 3] += flush(t, wk, lane);
+    const unsigned long long s = flush(t, wk, lane);
+    switch (kmax) {
+        case 4: cnt[1] += s; break;
+        case 5: cnt[2] += s; break;
+        case 6: cnt[3] += s; break;
+        case 7: cnt[4] += s; break;
+        case 8: cnt[5] += s; break;
+        default:
+            if constexpr (KMAX > 8) {
+#pragma unroll
+                for (int k = 9; k <= KMAX; ++k)
+                    if (k == kmax) cnt[k - 3] += s;
+            }
+            break;
+    }
     wk.used = 0;
 }
 
 // Traversal of one row i of a tile (the cliques through v and list[i]).
 template <int KMAX, bool XT>
-__device__ __forceinline__ void run_row(const Tile &t, Walker &wk, int i, int lane, unsigned long long *cnt,
-                                        const CliqueArgs &a) {
-    if (KMAX <= 8 && a.kmax <= 6 && compressed_row(t, i, a.kmax, wk.bsh, lane, cnt, a)) return;
-    walk<1, KMAX, XT>(t, wk, t.rows + (size_t)i * t.ws, i, lane, cnt, a);
+__device__ __forceinline__ void run_row(const Tile &t, Walker &wk, int i, int kmax, int lane,
+                                        unsigned long long *cnt) {
+    if (KMAX <= 8 && kmax <= 6 && compressed_row(t, i, kmax, wk.bsh, lane, cnt)) return;
+    walk<1, KMAX, XT>(t, wk, t.rows + (size_t)i * t.ws, i, kmax, lane, cnt);
 }
 
 // Existence mode: publish the warp's kmax count after a row (kmin == kmax).
 template <int KMAX>
 __device__ __forceinline__ void publish_row(const Tile &t, Walker &wk, int lane, unsigned long long *cnt,
                                             const CliqueArgs &a) {
-    drain<KMAX>(t, wk, lane, cnt, a);
+    drain<KMAX>(t, wk, a.kmax, lane, cnt);
     const unsigned long long mine = cnt[a.kmax - 3];
     cnt[a.kmax - 3] = 0;
     const unsigned __int128 tot = warp_sum_u128(mine);
@@ -406,6 +420,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     wk.bsh = (unsigned *)(wk.items + kItems);
     wk.m = 0;
     wk.used = 0;
+    wk.kmin = a.kmin;
 
     unsigned long long cnt[KMAX];
 #pragma unroll 1
@@ -449,10 +464,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
                 const int i = d - 1 - r; // longest rows first
                 if (i < 2) break;
                 if (polled && ctl_stop(a.ctl, lane)) break;
-                run_row<KMAX, XT>(ht, wk, i, lane, cnt, a);
+                run_row<KMAX, XT>(ht, wk, i, a.kmax, lane, cnt);
                 if (exist) publish_row<KMAX>(ht, wk, lane, cnt, a);
             }
-            drain<KMAX>(ht, wk, lane, cnt, a);
+            drain<KMAX>(ht, wk, a.kmax, lane, cnt);
         }
         guard_counts<KMAX>(cnt, a);
         __syncthreads();
@@ -489,10 +504,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
             if (a.kmax >= 4) {
                 for (int i = d - 1; i >= 2; --i) {
                     if (polled && ctl_stop(a.ctl, lane)) break;
-                    run_row<KMAX, XT>(lt, wk, i, lane, cnt, a);
+                    run_row<KMAX, XT>(lt, wk, i, a.kmax, lane, cnt);
                     if (exist) publish_row<KMAX>(lt, wk, lane, cnt, a);
                 }
-                drain<KMAX>(lt, wk, lane, cnt, a);
+                drain<KMAX>(lt, wk, a.kmax, lane, cnt);
             }
             guard_counts<KMAX>(cnt, a);
             __syncwarp();

@@ -207,5 +207,9 @@ bool pg_batch_labeled(const pg_batch *b);
 size_t pg_batch_scratch_bytes(const pg_graph *g, const pg_batch *b);
 int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts_dev, int queue_slot,
                       cudaStream_t s, const PgRunCtl *ctl = nullptr);
+// count_c4.cu: edge-induced 4-cycles by co-degree accumulation (adds into
+// the 128-bit count_dev; queue words queue_slot .. queue_slot + 2)
+int pg_launch_c4(pg_graph *g, unsigned long long *count_dev, int queue_slot, cudaStream_t s, const PgRunCtl *ctl);
+size_t pg_c4_scratch_bytes(const pg_graph *g);
 int pg_launch_clique_on(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
                         unsigned long long *queue, void *slabs, long long max_warps, cudaStream_t s);
