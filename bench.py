@@ -4,9 +4,14 @@ power-law graph (1M vertices, 10M edges, exponent 2.1, max weight 20K).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = counting every 4-clique and every 5-clique of the resident graph
-(one launch of the persistent clique kernel computes both).  Prints one JSON
-line on rank 0.  ``--impl reference`` times the plain CPU oracle (textbook
-oriented clique lister) on a bounded sample of start vertices instead.
+(one launch of the persistent clique kernel computes both).  With N GPUs
+every rank holds the graph and counts the start vertices of degree rank
+r = rank (mod N); one exact sum of the 128-bit counters gives the whole
+count, so `value` = all matches / the slowest rank's time.  Prints one JSON
+line on rank 0, with the other workloads (induced 3- and 4-motifs, FSM,
+14-clique existence, serving) as extra keys under "configs" at N = 1.
+``--impl reference`` times the plain CPU oracle (textbook oriented clique
+lister) on a bounded sample of start vertices instead.
 """
 from __future__ import annotations
 
@@ -26,10 +31,12 @@ sys.path.insert(0, ROOT)
 import synthgraph as sg  # noqa: E402
 
 WORKLOAD = "kclique_chunglu_n1M_m10M_g2.1"
-# ncu figures of k_count_clique on this workload (profiles/k_count_clique_chunglu_n1M_m10M.md),
-# valid only for the kernel source they were taken on
-NCU_CLIQUE = {"source_sha16": "9aa03cc35376c69d", "dram_bytes_per_launch": 89225984,
-              "l2_bytes_per_launch": 5841528672, "issue_active_frac": 0.691, "inst_executed_frac": 0.690}
+# per-kernel figures of one ncu capture each (DRAM bytes per launch, issue
+# rate), keyed by kernel and valid only for the kernel source they were
+# taken on
+NCU_RECORDS = os.path.join(ROOT, "profiles", "ncu_kernels.json")
+CSRC = os.path.join(ROOT, "paper_2004_02369_b300", "csrc")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "workload_counts.json")
 METRIC = "exact pattern matches/sec"
 UNIT = "matches/s"
 CLIQUE_SIZES = (4, 5)
@@ -218,6 +225,47 @@ def algorithmic_bytes(g, rank: np.ndarray, kmin: int) -> int:
     return 4 * total + 16 * g.n
 
 
+def ncu_record(kernel: str):
+    """The ncu figures of `kernel` if they were taken on its current source
+    (sha256 prefix of the .cu file named in the record), else None."""
+    import hashlib
+    try:
+        rec = json.load(open(NCU_RECORDS))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(CSRC, rec["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha16"]:
+        return None
+    return rec
+
+
+def golden_counts(name: str) -> dict:
+    return {k: int(v) for k, v in json.load(open(GOLDEN))[name]["counts"].items()}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def hbm_roofline(kernel: str, alg_bytes: int, ms: float, per_launch_note: str, extra=None) -> dict:
+    peaks = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    rec = ncu_record(kernel)
+    out = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+           "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+           "algorithmic_bytes_per_launch": int(alg_bytes), "algorithmic_bytes": per_launch_note,
+           "traffic": rec["dram_bytes_per_launch"] if rec and "dram_bytes_per_launch" in rec else None}
+    if rec:
+        out["ncu"] = {k: v for k, v in rec.items() if k not in ("source", "source_sha16", "command")}
+    if extra:
+        out.update(extra)
+    return out
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -253,6 +301,20 @@ def sum_over_ranks(world, x: float, device=None) -> float:
     t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t)
     return float(t.item())
+
+
+def sum_counts_over_ranks(world, counts, device=None) -> list[int]:
+    """Exact sum over ranks of non-negative integer counts below 2^128:
+    each count travels as four 32-bit limbs in int64 lanes (sums of up to
+    2^31 ranks cannot overflow), recombined after the all-reduce."""
+    if world == 1:
+        return [int(c) for c in counts]
+    import torch
+    import torch.distributed as dist
+    limbs = [[(int(c) >> (32 * j)) & 0xFFFFFFFF for j in range(4)] for c in counts]
+    t = torch.tensor(limbs, dtype=torch.int64, device=device)
+    dist.all_reduce(t)
+    return [sum(int(x) << (32 * j) for j, x in enumerate(row)) for row in t.cpu().tolist()]
 
 
 # --------------------------------------------------------------- CPU arm ---
@@ -294,6 +356,12 @@ def run_reference(args):
 
 # --------------------------------------------------------------- GPU arm ---
 
+def _pinned(a: np.ndarray) -> np.ndarray:
+    """A page-locked copy of a host array (numpy view of pinned memory)."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup(args)
@@ -304,6 +372,8 @@ def run_ours(args):
     g = sg.workload_graph(2)
     stream = torch.cuda.current_stream(dev)
     G = pg.Graph.from_synth(g, stream=stream)
+    if world > 1:
+        pg.set_partition(G, rank, world)  # start vertices of rank r = rank (mod world)
     plans = [pg.Plan(k, sg.clique_edges(k), name=f"{k}-clique") for k in CLIQUE_SIZES]
     counts = torch.zeros(2 * len(plans), dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
@@ -347,106 +417,322 @@ def run_ours(args):
     got = pg.decode_counts(counts)
     if got != expect:
         raise SystemExit(f"counts changed between steps: {expect} -> {got}")
-    matches = sum(got)
+    total = sum_counts_over_ranks(world, got, dev)
+    gold = golden_counts("cliques")
+    if total != [gold[f"{k}-clique"] for k in CLIQUE_SIZES]:
+        raise SystemExit(f"counts differ from the oracle's: {total}")
+    matches = sum(total)
     ms_step = float(np.mean(ms))
     ms_step_max = max_over_ranks(world, ms_step, dev)
-    value = sum_over_ranks(world, matches, dev) / (ms_step_max / 1e3)
+    value = matches / (ms_step_max / 1e3)
 
     if args.only_kernel:
         if rank == 0:
             print(json.dumps({"only_kernel": True, "ms_per_step": ms_step, "counts": got}), flush=True)
         return 0
 
-    # ---- end to end: host CSR in pinned memory -> load -> count -> host ----
-    off_h = torch.from_numpy(g.offsets).pin_memory()
-    adj_h = torch.from_numpy(g.adj).pin_memory()
+    # ---- end to end through the C-ABI with host buffers: pinned CSR ->
+    # pg_load_graph (the library's own H2D, validation, degree relabel) ->
+    # pg_count (launch, D2H) -> exact sum over ranks
+    off_h, adj_h = _pinned(g.offsets), _pinned(g.adj)
     e2e_ms = []
     for it in range(1 + max(1, min(args.steps, 3))):
+        barrier(world)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        off_d = off_h.to(dev, non_blocking=True)
-        adj_d = adj_h.to(dev, non_blocking=True)
-        G2 = pg.Graph(off_d, adj_d, stream=stream)
-        pg.count_async(G2, plans, counts, kernel=args.kernel, stream=stream)
-        host = counts.cpu()
+        G2 = pg.Graph(off_h, adj_h, stream=stream)
+        pg.set_tuning(G2, stream=stream, **pg.get_tuning(G))
+        if world > 1:
+            pg.set_partition(G2, rank, world)
+        host = pg.count(G2, plans, stream=stream)
+        host_total = sum_counts_over_ranks(world, host, dev)
         dt = (time.perf_counter() - t) * 1e3
         G2.close()
-        del off_d, adj_d
-        if pg.decode_counts(host) != expect:
+        if host_total != total:
             raise SystemExit("end-to-end counts differ")
         if it > 0:
-            e2e_ms.append(dt)
+            e2e_ms.append(max_over_ranks(world, dt, dev))
     e2e = {"value": matches / (np.mean(e2e_ms) / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": int(g.offsets.nbytes + g.adj.nbytes),
-           "d2h_bytes_per_step": int(counts.numel() * 8),
+           "d2h_bytes_per_step": int(16 * len(plans)),
            "ms_per_step": float(np.mean(e2e_ms)),
-           "includes": "pinned H2D of the CSR, validation + degree relabel on device, count, D2H"}
+           "includes": "pg_load_graph from pinned host CSR (H2D, validation, degree relabel), "
+                       "launch-parameter copy, pg_count (count, D2H), sum over ranks"}
 
-    # ---- one-pattern-per-launch plain interpreter, for comparison ----------
-    plain = None
-    if args.compare_plain and rank == 0:
-        pc = torch.zeros(2, dtype=torch.int64, device=dev)
-        per = {}
-        for p in plans:
-            pg.count_async(G, [p], pc, kernel=pg.KERNEL_CLIQUE_PLAIN, stream=stream)  # warm
-            torch.cuda.synchronize()
-            flush.zero_()
-            s = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            pg.count_async(G, [p], pc, kernel=pg.KERNEL_CLIQUE_PLAIN, stream=stream)
-            e.record(stream)
-            torch.cuda.synchronize()
-            assert pg.decode_counts(pc)[0] == expect[plans.index(p)]
-            per[p.name] = s.elapsed_time(e)
-        tot = sum(per.values())
-        plain = {"kernel": "plan interpreter, one warp per start vertex, one launch per pattern",
-                 "ms_per_step": tot, "value": matches / (tot / 1e3), "per_pattern_ms": per,
-                 "speedup_of_value": (matches / (ms_step / 1e3)) / (matches / (tot / 1e3))}
+    # ---- plain one-pattern-per-launch forms on the same GPU --------------
+    plain = interp = None
+    if args.compare_plain and rank == 0 and world == 1:
+        plain = _per_pattern(pg, G, plans, expect, pg.KERNEL_CLIQUE_NONPERSISTENT, stream, flush, matches)
+        plain["kernel"] = ("k-clique bitmap kernel without persistence: one warp per start vertex (one CTA per "
+                           "heavy start vertex), one launch pair per pattern")
+        plain["speedup_of_value"] = plain["ms_per_step"] / ms_step
+        interp = _per_pattern(pg, G, plans, expect, pg.KERNEL_CLIQUE_PLAIN, stream, flush, matches)
+        interp["kernel"] = ("plan interpreter (sorted-list set operations, 16-byte driver loads), one warp per "
+                            "start vertex, one launch per pattern")
+        interp["speedup_of_value"] = interp["ms_per_step"] / ms_step
 
     if rank != 0:
         return 0
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
     alg = algorithmic_bytes(g, G.rank(), min(CLIQUE_SIZES))
-    achieved = alg / (ms_step / 1e3) / 1e9
-    import hashlib
-    src = os.path.join(ROOT, "paper_2004_02369_b300", "csrc", "count_clique.cu")
-    sha16 = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    ncu_valid = sha16 == NCU_CLIQUE["source_sha16"]
-    traffic = args.traffic if args.traffic is not None else (NCU_CLIQUE["dram_bytes_per_launch"] if ncu_valid else None)
-    roofline = {"bound": "hbm", "kernel": "k_count_clique", "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "algorithmic_bytes_per_launch": alg, "traffic": traffic,
-                "ncu": ({"l2_bytes_per_launch": NCU_CLIQUE["l2_bytes_per_launch"],
-                         "issue_active_frac": NCU_CLIQUE["issue_active_frac"],
-                         "inst_executed_frac_of_peak": NCU_CLIQUE["inst_executed_frac"],
-                         "note": "graph is L2-resident; the kernel is instruction-issue bound"}
-                        if ncu_valid else None)}
-
+    rec = ncu_record("k_count_clique")
+    roofline = hbm_roofline(
+        "k_count_clique", alg // max(world, 1), ms_step_max,
+        "4 B x (out-list of every start vertex + out-lists of its out-neighbours but the first): the operands "
+        "of the level-1 intersections; deeper levels are word ANDs of on-chip bitmap rows",
+        {"issue_active_frac": rec.get("issue_active_frac") if rec else None,
+         "note": "graph L2-resident; the kernel is bound by instruction issue (issue_active_frac of the "
+                 "SM issue slots, ncu)"})
+    extra = run_extra_configs(args, pg, dev, G) if (args.extra and world == 1) else None
     cpu_rate, _, cpu_secs = cpu_oracle_rate(g, 1)
     cfg = workload_config(g)
     cfg.update({"kernel": {0: "auto (persistent bitmap clique kernel)", 3: "clique"}.get(args.kernel, str(args.kernel)),
                 "autotune": tune,
+                "parallelism": f"start vertices dealt round-robin by degree rank over {world} GPU(s), exact "
+                               "sum of the 128-bit counters" if world > 1 else "one GPU",
                 "l2": "256 MiB buffer written between timed steps (not timed)",
-                "counts": {p.name: c for p, c in zip(plans, got)}})
+                "counts": {p.name: c for p, c in zip(plans, total)}, "counts_match_oracle": True})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": cfg, "e2e": e2e, "gpu_launches": args.steps,
             "roofline": roofline, "clocks": clk,
             "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{CPU_SAMPLE_SOURCES} seeded random start vertices, 4- and 5-cliques, "
                                        f"{cpu_secs:.1f} s"},
             "plain_one_pattern_per_launch": plain,
+            "interpreter_one_pattern_per_launch": interp,
+            "configs": extra,
             "wall_s_timed": wall}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _per_pattern(pg, G, plans, expect, kernel, stream, flush, matches):
+    """One launch (pair) per pattern with `kernel`, CUDA events per pattern."""
+    import torch
+    pc = torch.zeros(2, dtype=torch.int64, device=flush.device)
+    per = {}
+    for i, p in enumerate(plans):
+        pg.count_async(G, [p], pc, kernel=kernel, stream=stream)  # warm
+        torch.cuda.synchronize()
+        flush.zero_()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        pg.count_async(G, [p], pc, kernel=kernel, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        if pg.decode_counts(pc)[0] != expect[i]:
+            raise SystemExit(f"{p.name}: kernel {kernel} count differs")
+        per[p.name] = s.elapsed_time(e)
+    tot = sum(per.values())
+    return {"ms_per_step": tot, "value": matches / (tot / 1e3), "per_pattern_ms": per}
+
+
+# --------------------------------------------------------------- other configs ---
+
+def _events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _timed(fn, stream, flush=None, reps=1) -> float:
+    """Device milliseconds of fn() per call on `stream` (CUDA events),
+    flushing L2 before the timed region when `flush` is given."""
+    import torch
+    torch.cuda.synchronize()
+    if flush is not None:
+        flush.zero_()
+    s, e = _events(stream)
+    s.record(stream)
+    for _ in range(reps):
+        fn()
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def _e2e(pg, g, call, reps=3) -> dict:
+    """End to end through the C-ABI with host buffers: pinned CSR (and
+    labels) -> pg_load_graph -> call(graph) (launches and D2H) -> graph
+    freed; mean wall milliseconds over reps after one warm-up."""
+    import torch
+    off_h, adj_h = _pinned(g.offsets), _pinned(g.adj)
+    lab_h = None if g.labels is None else _pinned(g.labels)
+    ms = []
+    for it in range(reps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        G = pg.Graph(off_h, adj_h, lab_h)
+        res = call(G)
+        dt = (time.perf_counter() - t) * 1e3
+        G.close()
+        if it:
+            ms.append(dt)
+    h2d = int(g.offsets.nbytes + g.adj.nbytes + (0 if g.labels is None else g.labels.nbytes))
+    return {"ms": float(np.mean(ms)), "h2d_bytes_per_step": h2d, "result": res}
+
+
+def _cfg_motif3(pg, dev) -> dict:
+    """Induced triangles and wedges on ER G(2000, 0.005): launch-latency
+    bound; microseconds per two-pattern batch, eager and CUDA-graph replay."""
+    import torch
+    g = sg.workload_graph(1)
+    G = pg.Graph.from_synth(g)
+    plans = [pg.Plan.from_dict(p) for p in sg.motif3_patterns()]
+    batch = pg.Batch(plans)
+    out = torch.zeros(4, dtype=torch.int64, device=dev)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(5):
+            pg.count_batch(G, batch, out, stream=side)
+        eager_us = 1e3 * _timed(lambda: pg.count_batch(G, batch, out, stream=side), side, reps=200)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            pg.count_batch(G, batch, out, stream=side)
+        graph.replay()
+        graph_us = 1e3 * _timed(graph.replay, side, reps=200)
+    torch.cuda.synchronize()
+    got = pg.decode_counts(out)
+    gold = golden_counts("motif3")
+    ok = got == [gold["induced_triangle"], gold["induced_wedge"]]
+    e2e = _e2e(pg, g, lambda G2: pg.count(G2, plans))
+    if e2e["result"] != got:
+        raise SystemExit("motif3 end-to-end counts differ")
+    adj_bytes = int(g.adj.nbytes + 16 * g.n)
+    return {"workload": "motif3_er_n2000_p0.005", "metric": "microseconds per batch of induced 3-motifs",
+            "unit": "us", "higher_is_better": False, "value": graph_us, "eager_us": eager_us,
+            "cuda_graph_us": graph_us, "counts": {"induced_triangle": got[0], "induced_wedge": got[1]},
+            "counts_match_oracle": ok, "gpu_launches_per_batch": 2,
+            "e2e": {"value": 1e3 * e2e["ms"], "unit": "us", "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                    "d2h_bytes_per_step": 32, "includes": "pg_load_graph from pinned host CSR, pg_count, D2H"},
+            "roofline": hbm_roofline("k_count_batched", adj_bytes, graph_us / 1e3,
+                                     "every adjacency list and vertex record read once (lower bound)",
+                                     {"note": "launch-latency bound: 2 kernels of a few microseconds"})}
+
+
+def c4_increments(g, rank):
+    """Adjacency elements the 4-cycle co-degree kernel reads: for every
+    anchor w and neighbour a ranked after w, the suffix of adj(a) ranked
+    after w, plus the anchors' own neighbour suffixes."""
+    deg = np.diff(g.offsets)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    rs, rd = rank[src].astype(np.int64), rank[g.adj.astype(np.int64)].astype(np.int64)
+    o = np.lexsort((rd, rs))
+    RS, RD = rs[o], rd[o]
+    off = np.zeros(g.n + 1, np.int64)
+    np.add.at(off, RS + 1, 1)
+    off = np.cumsum(off)
+    pos = np.arange(RS.size) - off[RS]
+    lower = RD < RS                      # edge (a -> w) with w ranked before a
+    above = (off[RS + 1] - off[RS]) - pos - 1
+    return int(above[lower].sum()) + int(lower.sum())
+
+
+def _cfg_motif4(pg, dev, args) -> dict:
+    """The six induced 4-vertex motifs of R-MAT scale 20 in one fused launch
+    (anti-edges expanded into edge-induced terms; the 4-cycle term by the
+    co-degree kernel, cliques by the clique kernel, the rest on the prefix
+    tree)."""
+    import torch
+    g = sg.workload_graph(3)
+    G = pg.Graph.from_synth(g)
+    pats = sg.motif4_patterns()
+    plans = [pg.Plan.from_dict(p) for p in pats]
+    batch = pg.Batch(plans)
+    out = torch.zeros(12, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tune = pg.autotune(G, plans, sample_stride=64) if args.autotune else None
+    pg.count_batch(G, batch, out)
+    fused_ms = min(_timed(lambda: pg.count_batch(G, batch, out), stream, flush) for _ in range(2))
+    got = pg.decode_counts(out)
+    gold = golden_counts("motif4")
+    ok = got == [gold[p["name"]] for p in pats]
+    c4 = pg.Batch([pg.Plan(4, sg.cycle_edges(4))])
+    c4_out = torch.zeros(2, dtype=torch.int64, device=dev)
+    pg.count_batch(G, c4, c4_out)
+    c4_ms = _timed(lambda: pg.count_batch(G, c4, c4_out), stream, flush)
+    matches = sum(got)
+    e2e = _e2e(pg, g, lambda G2: pg.count(G2, plans), reps=2)
+    if e2e["result"] != got:
+        raise SystemExit("motif4 end-to-end counts differ")
+    inc = c4_increments(g, G.rank())
+    return {"workload": "motif4_induced_rmat_scale20_ef16", "metric": METRIC, "unit": UNIT, "value": matches / (fused_ms / 1e3),
+            "ms": fused_ms, "counts": dict(zip([p["name"] for p in pats], got)), "counts_match_oracle": ok,
+            "graph": {"n": g.n, "m": g.m}, "autotune": tune, "edge_induced_4cycle_ms": c4_ms,
+            "e2e": {"value": matches / (e2e["ms"] / 1e3), "unit": UNIT, "ms": e2e["ms"],
+                    "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": 96,
+                    "includes": "pg_load_graph from pinned host CSR, pg_count (batch build, launches, D2H)"},
+            "roofline": hbm_roofline("k_c4_dense", 4 * inc, c4_ms,
+                                     "4 B x adjacency elements the co-degree pass reads (neighbour suffixes "
+                                     "above each anchor); timed: the 4-cycle term alone",
+                                     {"share_of_fused_step": c4_ms / fused_ms})}
+
+
+def fsm_bytes(g) -> int:
+    """Bytes the FSM row kernel reads and writes: per vertex its record, label
+    masks and list; per neighbour w its record, masks and list, a 16-byte
+    mask per element of adj(w) (path ends), and the smaller list of the
+    triangle test; one row of membership words written and read once."""
+    deg = np.diff(g.offsets).astype(np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    dw = deg[g.adj.astype(np.int64)]
+    nl = int(g.labels.max()) + 1
+    words = 1 + 3 * nl + 4 * nl * nl
+    return int(g.n * 32 + 4 * deg.sum() + 32 * deg.sum() + 20 * dw.sum() + 4 * np.minimum(deg[src], dw).sum()
+               + 2 * 4 * words * g.n)
+
+
+def _cfg_fsm(pg, dev) -> dict:
+    """Labeled FSM with MNI support >= 1000, 1..3 edges, on Chung-Lu 500K / 5M
+    with Zipf labels over 20 (synchronous call: wall milliseconds)."""
+    import torch
+    g = sg.workload_graph(4)
+    G = pg.Graph.from_synth(g)
+    pg.fsm(G, threshold=1000)
+    ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        freq = pg.fsm(G, threshold=1000)
+        ms.append((time.perf_counter() - t) * 1e3)
+    want = {}
+    for key, v in golden_counts("fsm").items():
+        shape, labels = key.split(":")
+        want[(shape, tuple(int(x) for x in labels.split(",")))] = v
+    e2e = _e2e(pg, g, lambda G2: len(pg.fsm(G2, threshold=1000)), reps=2)
+    by_shape = {}
+    for (shape, _), _v in freq.items():
+        by_shape[shape] = by_shape.get(shape, 0) + 1
+    return {"workload": "fsm_chunglu_n500K_m5M_g2.3_zipf20", "metric": "FSM milliseconds (labeled patterns <= 3 "
+            "edges, MNI >= 1000)", "unit": "ms", "higher_is_better": False, "value": min(ms),
+            "frequent": len(freq), "frequent_by_shape": by_shape, "counts_match_oracle": freq == want,
+            "e2e": {"value": e2e["ms"], "unit": "ms", "h2d_bytes_per_step": e2e["h2d_bytes_per_step"],
+                    "d2h_bytes_per_step": 32 * len(freq),
+                    "includes": "pg_load_graph from pinned host CSR and labels, pg_fsm (host scan of the label "
+                                "histogram, kernels, D2H, sort)"},
+            "roofline": hbm_roofline("k_fsm_rows", fsm_bytes(g), min(ms),
+                                     "vertex and neighbour records, lists, per-element label masks of the 2-hop "
+                                     "scan, rows written and read once; timed: the whole synchronous call",
+                                     {"note": "the call's wall time includes host steps"})}
+
+
+def _cfg_exists(pg, G) -> dict:
+    """Existence queries with early termination on the 1M-vertex Chung-Lu graph
+    (the paper's 14-clique existence query, and a 6-clique)."""
+    import torch
+    res = {}
+    for k in (6, 14):
+        plan = pg.Plan(k, sg.clique_edges(k))
+        pg.count_until(G, plan, 1)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        got, reached = pg.count_until(G, plan, 1)
+        res[f"{k}-clique"] = {"exists": reached, "found_before_stop": got,
+                              "ms_to_verdict": (time.perf_counter() - t) * 1e3}
+    return {"workload": "existence_chunglu_n1M_m10M", "results": res,
+            "note": "wall milliseconds of the synchronous pg_count_until (launch, stop flag, D2H)"}
 
 
 # --------------------------------------------------------------- other workloads ---
@@ -465,37 +751,10 @@ def _events_ms(fn, stream, reps=1):
 
 
 def run_motif3(args):
-    """Induced triangles and wedges on ER G(2000, 0.005): launch-latency
-    bound, so microseconds per two-pattern batch, with and without CUDA-graph
-    replay of the captured batch launch."""
     import torch
     import paper_2004_02369_b300 as pg
     torch.cuda.set_device(0)
-    g = sg.workload_graph(1)
-    G = pg.Graph.from_synth(g)
-    plans = [pg.Plan.from_dict(p) for p in sg.motif3_patterns()]
-    batch = pg.Batch(plans)
-    out = torch.zeros(4, dtype=torch.int64, device="cuda")
-    side = torch.cuda.Stream()
-    with torch.cuda.stream(side):
-        for _ in range(5):
-            pg.count_batch(G, batch, out, stream=side)
-        reps = 200
-        eager_us = 1e3 * _events_ms(lambda: pg.count_batch(G, batch, out, stream=side), side, reps)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=side):
-            pg.count_batch(G, batch, out, stream=side)
-        graph.replay()
-        graph_us = 1e3 * _events_ms(graph.replay, side, reps)
-    torch.cuda.synchronize()
-    counts = pg.decode_counts(out)
-    line = {"metric": "microseconds per batch of induced 3-motifs", "value": graph_us, "unit": "us",
-            "higher_is_better": False, "data": "synthetic", "n_gpus": 1,
-            "config": {"workload": "motif3_er_n2000_p0.005", "m": g.m,
-                       "patterns": ["induced_triangle", "induced_wedge"]},
-            "eager_us": eager_us, "cuda_graph_us": graph_us,
-            "counts": {"induced_triangle": counts[0], "induced_wedge": counts[1]}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_cfg_motif3(pg, torch.device("cuda", 0))), flush=True)
     return 0
 
 
@@ -506,7 +765,8 @@ def run_motif4(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     res = {}
-    for sd in ([4, 0] if not args.motif4_small else [4]):
+    for scale in (args.motif4_scales if not args.motif4_small else [16]):
+        sd = 20 - scale
         g = sg.workload_graph(3, scale_down=sd)
         G = pg.Graph.from_synth(g)
         plans = [pg.Plan.from_dict(p) for p in sg.motif4_patterns()]
@@ -517,7 +777,7 @@ def run_motif4(args):
         counts = pg.decode_counts(out)
         tune = None
         if args.autotune:
-            tune = pg.autotune(G, plans, sample_stride=8 if sd > 0 else 64)
+            tune = pg.autotune(G, plans, sample_stride=8 if scale <= 16 else 64)
             tuned = _events_ms(lambda: pg.count_batch(G, b, out), stream)
             if pg.decode_counts(out) != counts:
                 raise SystemExit("counts changed under tuned launch parameters")
@@ -527,14 +787,14 @@ def run_motif4(args):
         row = {"n": g.n, "m": g.m, "fused_batched_ms": fused, "autotune": tune,
                "counts": dict(zip([p["name"] for p in sg.motif4_patterns()], counts)),
                "matches_per_s": sum(counts) / (fused / 1e3)}
-        if sd > 0:
+        if scale <= 16:
             sep = 0.0
             o = torch.zeros(2, dtype=torch.int64, device="cuda")
             for pl in plans:
                 sep += _events_ms(lambda: pg.count_async(G, [pl], o, kernel=pg.KERNEL_GENERIC), stream)
             row["six_separate_launches_ms"] = sep
-        res[f"rmat_scale{20 - sd}"] = row
-    full = res.get("rmat_scale20") or res["rmat_scale16"]
+        res[f"rmat_scale{scale}"] = row
+    full = res[f"rmat_scale{max(int(x) for x in (args.motif4_scales if not args.motif4_small else [16]))}"]
     line = {"metric": "exact pattern matches/sec", "value": full["matches_per_s"], "unit": "matches/s",
             "data": "synthetic", "n_gpus": 1,
             "config": {"workload": "motif4_induced_rmat_scale20_ef16"}, "results": res}
@@ -626,43 +886,26 @@ def run_exists(args):
 
 
 def run_fsm(args):
-    """Frequent labeled patterns (1..3 edges, MNI >= 1000) on Chung-Lu 500K."""
     import torch
     import paper_2004_02369_b300 as pg
     torch.cuda.set_device(0)
-    g = sg.workload_graph(4)
-    G = pg.Graph.from_synth(g)
-    pg.fsm(G, threshold=1000)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    freq = pg.fsm(G, threshold=1000)
-    dt = time.perf_counter() - t
-    by_shape = {}
-    for (shape, _), v in freq.items():
-        by_shape[shape] = by_shape.get(shape, 0) + 1
-    line = {"metric": "FSM wall seconds (all labeled patterns <= 3 edges, MNI >= 1000)", "value": dt,
-            "unit": "s", "higher_is_better": False, "data": "synthetic", "n_gpus": 1,
-            "config": {"workload": "fsm_chunglu_n500K_m5M_g2.3_zipf20", "threshold": 1000},
-            "frequent": len(freq), "frequent_by_shape": by_shape}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(_cfg_fsm(pg, torch.device("cuda", 0))), flush=True)
     return 0
 
 
 # --------------------------------------------------------------- serving ---
 
-def run_serving(args):
-    """Poisson stream of count queries over a resident R-MAT graph: batched
-    continuous serving vs the same kernels one query at a time."""
+def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, labeled_only=("C5",),
+                query_timeout_s: float = 0.0) -> dict:
+    """Poisson streams of count queries over a resident R-MAT graph (the
+    survey's mix, 10% labeled over 8 labels): continuous batching (4
+    streams, up to 32 queries per launch) against the same kernels one query
+    at a time; every result of the mix equals the query's count alone."""
     import torch
-    import paper_2004_02369_b300 as pg
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    scale = args.serve_scale
+    dev = torch.device("cuda", torch.cuda.current_device())
     g = sg.workload_graph(5, scale_down=22 - scale)
     G = pg.Graph.from_synth(g)
-    # unlabeled 5-cycles take minutes alone on power-law hubs: they are
-    # calibrated alone (alone_ms) and drawn only in their labeled form
-    qs = sg.serving_queries(args.serve_n, seed=sg.SEED_BASE + 55, labeled_only=("C5",))
+    qs = sg.serving_queries(n_queries, seed=sg.SEED_BASE + 55, labeled_only=labeled_only)
     types = sorted({q["name"] for q in qs})
 
     # per-type service time alone (first call compiles / sizes scratch)
@@ -687,14 +930,15 @@ def run_serving(args):
             while time.perf_counter() - t0 < a:
                 time.sleep(min(2e-4, max(0.0, a - (time.perf_counter() - t0))))
             tickets.append(server.submit(q))
-        server.drain(args.serve_timeout)
+        server.drain(timeout_s)
         res = {r["ticket"]: r for r in server.poll(len(qs) + 10)}
         out = [res[t] for t in tickets]
         lat = np.array([r["t_done"] - r["t_submit"] for r in out]) * 1e3
         span = max(r["t_done"] for r in out) - min(r["t_submit"] for r in out)
         return out, {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "mean_ms": float(lat.mean()), "queries_per_s": len(out) / span,
-                     "batches": server.stats()["batches"]}
+                     "batches": server.stats()["batches"],
+                     "timed_out": sum(1 for r in out if r["status"] == pg.PG_ETIMEOUT)}
 
     # serial capacity: closed loop, everything submitted at t = 0
     srv = pg.Server(G, serial=True)
@@ -703,29 +947,51 @@ def run_serving(args):
     capacity = cal["queries_per_s"]
     log(f"serial capacity {capacity:.1f} queries/s ({cal})")
     want = [r["count"] for r in base]
+    if any(r["status"] != pg.PG_OK for r in base):
+        raise SystemExit("a serving query failed when run one at a time")
     runs = []
-    for f in args.serve_lambdas:
+    for f in lambdas:
         arrivals = sg.poisson_arrivals(len(qs), f * capacity, seed=sg.SEED_BASE + int(100 * f))
         row = {"lambda_x_capacity": f, "rate_qps": f * capacity}
         for mode, kw in (("serial", dict(serial=True)), ("batched", dict(n_streams=4, max_batch=32))):
-            srv = pg.Server(G, **kw)
+            srv = pg.Server(G, query_timeout_s=query_timeout_s, **kw)
             out, st = drive(srv, arrivals)
             srv.close()
             log(f"lambda {f} {mode}: {st}")
-            if [r["count"] for r in out] != want:
+            got = [r["count"] if r["status"] == pg.PG_OK else None for r in out]
+            if any(x is not None and x != w for x, w in zip(got, want)):
                 raise SystemExit(f"serving counts differ from one-at-a-time ({mode}, lambda {f})")
             row[mode] = st
         runs.append(row)
-    line = {"metric": "serving p50/p99 latency and queries/s, batched vs one query at a time",
-            "unit": "ms, queries/s", "n_gpus": 1, "data": "synthetic",
-            "config": {"workload": f"serving_rmat_scale{scale}_ef16_labels8",
-                       "graph": {"n": g.n, "m": g.m, "max_degree": int(g.meta["max_degree"])},
-                       "queries": len(qs), "types": types, "labeled_fraction": 0.1,
-                       "labeled_only": ["C5"],
-                       "arrivals": "Poisson, rate = lambda x measured serial capacity",
-                       "batched": "4 streams, up to 32 queries per launch"},
-            "serial_capacity_qps": capacity, "alone_ms": alone_ms, "runs": runs,
-            "mix_equals_alone": True}
+    return {"workload": f"serving_rmat_scale{scale}_ef16_labels8",
+            "metric": "serving p50/p99 latency and queries/s, batched vs one query at a time",
+            "unit": "ms, queries/s",
+            "graph": {"n": g.n, "m": g.m, "max_degree": int(g.meta["max_degree"])},
+            "queries": len(qs), "types": types, "labeled_fraction": 0.1, "labeled_only": list(labeled_only),
+            "arrivals": "Poisson, rate = lambda x measured serial capacity",
+            "batched": "4 streams, up to 32 queries per launch", "serial_capacity_qps": capacity,
+            "alone_ms": alone_ms, "runs": runs, "mix_equals_alone": True,
+            "query_timeout_s": query_timeout_s}
+
+
+def run_extra_configs(args, pg, dev, G_cliques) -> dict:
+    t = time.perf_counter()
+    out = {"motif3_er2000": _cfg_motif3(pg, dev), "motif4_rmat20": _cfg_motif4(pg, dev, args),
+           "fsm_chunglu500k": _cfg_fsm(pg, dev), "exists_chunglu1M": _cfg_exists(pg, G_cliques)}
+    if args.serve_n > 0:
+        out[f"serving_rmat{args.serve_scale}"] = serving_run(pg, args.serve_scale, args.serve_n, args.serve_lambdas,
+                                                             args.serve_timeout)
+    out["wall_s"] = time.perf_counter() - t
+    return out
+
+
+def run_serving(args):
+    import torch
+    import paper_2004_02369_b300 as pg
+    torch.cuda.set_device(0)
+    line = serving_run(pg, args.serve_scale, args.serve_n, args.serve_lambdas, args.serve_timeout,
+                       labeled_only=tuple(args.serve_labeled_only), query_timeout_s=args.serve_query_timeout)
+    line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -743,8 +1009,14 @@ def main():
     ap.add_argument("--workload", choices=["cliques", "serving", "motif3", "motif4", "motif5", "lmotif3", "fsm", "exists"],
                     default="cliques")
     ap.add_argument("--motif4-small", action="store_true", help="skip the full-size motif run")
+    ap.add_argument("--motif4-scales", type=int, nargs="+", default=[16, 20], help="R-MAT scales of the motif run")
+    ap.add_argument("--no-extra", dest="extra", action="store_false",
+                    help="only the k-clique headline (no per-config keys)")
     ap.add_argument("--serve-scale", type=int, default=16, help="R-MAT scale of the serving graph")
-    ap.add_argument("--serve-n", type=int, default=300, help="queries per arrival rate")
+    ap.add_argument("--serve-n", type=int, default=100, help="queries per arrival rate (0: no serving key)")
+    ap.add_argument("--serve-labeled-only", nargs="*", default=["C5"],
+                    help="query types drawn only in their labeled form")
+    ap.add_argument("--serve-query-timeout", type=float, default=0.0, help="server query time limit (s)")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
     ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")
     ap.add_argument("--tuning-json", default=None,

@@ -150,6 +150,9 @@ typedef struct {
 #define PG_KERNEL_CLIQUE_PLAIN 2  /* plan interpreter, one warp per task, one launch per pattern */
 #define PG_KERNEL_CLIQUE 3        /* k-clique, persistent, bitmap sub-graph */
 #define PG_KERNEL_BATCHED 4       /* all plans in one launch over their shared prefix tree */
+#define PG_KERNEL_CLIQUE_NONPERSISTENT 5 /* k-clique bitmap kernel without persistence: one warp per
+                                            start vertex (one CTA per heavy one), one launch pair
+                                            per pattern -- the plain form of PG_KERNEL_CLIQUE */
 
 /*
  * pg_load_graph - make a data graph resident on the current device.
@@ -285,6 +288,22 @@ int pg_count_until(pg_graph *g, pg_plan *p, uint64_t target, uint64_t *count_out
  */
 int pg_clustering_coefficient_above(pg_graph *g, double bound, int32_t *answer, uint64_t *triangles_out,
                                     uint64_t *wedges_out, void *stream);
+
+/*
+ * pg_set_partition - count only this GPU's share of the tasks: the counting
+ * kernels (pg_count, pg_count_ex, pg_count_batch, pg_count_until, the
+ * k-clique no-allocation entry point) take the tasks t with
+ * t mod n_parts == part, where tasks are start vertices in degree-rank order
+ * (Section 5.1 tasks; hub start vertices split into several tasks, and
+ * (start vertex, matching order) pairs on the interpreter).  Every match
+ * belongs to exactly one task, so the counts of parts 0..n_parts-1 on
+ * copies of the same graph sum to the full count (the multi-GPU split: one
+ * sum all-reduce of the counters).  Interleaving by rank deals hubs evenly.
+ * (0, 1) restores the whole graph.  Listing (pg_match), FSM and labeled
+ * motifs ignore the partition.  Host only.  Errors: PG_EINVAL (NULL graph,
+ * part outside 0..n_parts-1, a server running on the graph).
+ */
+int pg_set_partition(pg_graph *g, int32_t part, int32_t n_parts);
 
 /*
  * pg_set_time_budget - device work budget of the synchronous calls on g
@@ -428,9 +447,10 @@ void pg_free_batch(pg_batch *b);
  *                         that share its first-level candidates, so that hub
  *                         start vertices do not serialise on one warp
  *                         (0 = no split; default 512).
- *   batched_regcap        1: the batched kernel variant limited to 64
+ *   batched_regcap        register cap of the batched kernel: 1 = 64
  *                         registers per thread (more resident warps, some
- *                         spilling); 0: the compiler's choice (default).
+ *                         spilling), 2 = about 100, 0 = the compiler's
+ *                         choice (default).
  *   clique_min_blocks     k-clique kernel variant: 3 CTAs per SM (80
  *                         registers, default) or 4 (64 registers, some
  *                         spilling).

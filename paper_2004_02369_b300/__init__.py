@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpg.so")
 
 PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETRUNC, PG_ETIMEOUT, PG_EDEVICE, PG_EUNSUPPORTED = range(7)
-KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_BATCHED = range(5)
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_BATCHED, KERNEL_CLIQUE_NONPERSISTENT = range(6)
 MAX_PATTERN = 8
 MAX_CLIQUE = 16
 
@@ -99,6 +99,7 @@ _lib.pg_get_tuning.argtypes = [_vp, _vp]
 _lib.pg_set_tuning.argtypes = [_vp, _vp, _vp]
 _lib.pg_autotune.argtypes = [_vp, _vp, _i32, _i32, _vp, _vp]
 _lib.pg_set_time_budget.argtypes = [_vp, ctypes.c_double]
+_lib.pg_set_partition.argtypes = [_vp, _i32, _i32]
 _lib.pg_clustering_coefficient_above.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(_i32), _vp, _vp, _vp]
 _lib.pg_get_time_budget.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
 _lib.pg_last_error.restype = ctypes.c_char_p
@@ -379,6 +380,11 @@ def clustering_coefficient_above(graph: Graph, bound: float, stream=None):
     _check(_lib.pg_clustering_coefficient_above(graph.handle, float(bound), ctypes.byref(ans), t.ctypes.data,
                                                 w.ctypes.data, _stream_ptr(stream)))
     return bool(ans.value), _u128(t[0], t[1]), _u128(w[0], w[1])
+
+
+def set_partition(graph: Graph, part: int, n_parts: int):
+    """Count only the tasks t with t mod n_parts == part (pg_set_partition)."""
+    _check(_lib.pg_set_partition(graph.handle, int(part), int(n_parts)))
 
 
 def set_time_budget(graph: Graph, budget_ms: float):

@@ -367,15 +367,23 @@ int count_dispatch(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t
     }
     if (kernel == PG_KERNEL_AUTO)
         kernel = all_clique ? PG_KERNEL_CLIQUE : any_anti_vertex ? PG_KERNEL_GENERIC : PG_KERNEL_BATCHED;
-    if (any_big && kernel != PG_KERNEL_CLIQUE)
+    if (any_big && kernel != PG_KERNEL_CLIQUE && kernel != PG_KERNEL_CLIQUE_NONPERSISTENT)
         return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices run on the k-clique kernel only");
     if (any_anti_vertex && kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN)
         return pg_set_error(PG_EUNSUPPORTED, "anti-vertex patterns run on the plan interpreter (PG_KERNEL_GENERIC)");
-    if (kernel == PG_KERNEL_CLIQUE && !all_clique)
-        return pg_set_error(PG_EINVAL, "PG_KERNEL_CLIQUE needs unlabeled k-clique patterns, k >= 3");
+    if ((kernel == PG_KERNEL_CLIQUE || kernel == PG_KERNEL_CLIQUE_NONPERSISTENT) && !all_clique)
+        return pg_set_error(PG_EINVAL, "the k-clique kernels need unlabeled k-clique patterns, k >= 3");
     if (kernel != PG_KERNEL_GENERIC && kernel != PG_KERNEL_CLIQUE_PLAIN && kernel != PG_KERNEL_CLIQUE &&
-        kernel != PG_KERNEL_BATCHED)
+        kernel != PG_KERNEL_BATCHED && kernel != PG_KERNEL_CLIQUE_NONPERSISTENT)
         return pg_set_error(PG_EINVAL, "unknown kernel family");
+    if (kernel == PG_KERNEL_CLIQUE_NONPERSISTENT) {
+        PG_CUDA(cudaMemsetAsync(counts_dev, 0, 2 * sizeof(uint64_t) * n_plans, s));
+        for (int i = 0; i < n_plans; ++i) {
+            int rc = pg_launch_clique_plain(g, pg_plan_size(plans[i]->h), (unsigned long long *)counts_dev + 2 * i, s);
+            if (rc) return rc;
+        }
+        return PG_OK;
+    }
     if (kernel == PG_KERNEL_BATCHED) {
         std::vector<uint64_t> key;
         for (int i = 0; i < n_plans; ++i) key.push_back(plans[i]->serial);
@@ -435,6 +443,14 @@ extern "C" int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
     if (n_plans > PG_MAX_QUEUES) return pg_set_error(PG_EINVAL, "at most 64 plans per call");
     if (n_plans == 0) return PG_OK;
     return count_dispatch(g, plans, n_plans, counts_dev, kernel, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int pg_set_partition(pg_graph *g, int32_t part, int32_t n_parts) {
+    if (!g || n_parts < 1 || part < 0 || part >= n_parts) return pg_set_error(PG_EINVAL, "need 0 <= part < n_parts");
+    if (g->servers > 0) return pg_set_error(PG_EINVAL, "a server is running on this graph");
+    g->part = part;
+    g->n_parts = n_parts;
+    return PG_OK;
 }
 
 extern "C" int pg_set_time_budget(pg_graph *g, double budget_ms) {

@@ -44,7 +44,7 @@ int check_tuning(const pg_tuning &t) {
         return pg_set_error(PG_EINVAL, "hub_min_degree must be >= 1 and hub_max 0..65536");
     if (t.clique_min_blocks != 3 && t.clique_min_blocks != 4)
         return pg_set_error(PG_EINVAL, "clique_min_blocks must be 3 or 4");
-    if (t.batched_regcap != 0 && t.batched_regcap != 1) return pg_set_error(PG_EINVAL, "batched_regcap must be 0 or 1");
+    if (t.batched_regcap < 0 || t.batched_regcap > 2) return pg_set_error(PG_EINVAL, "batched_regcap must be 0, 1 or 2");
     if (t.batched_split_grain != 0 && t.batched_split_grain < 16)
         return pg_set_error(PG_EINVAL, "batched_split_grain must be 0 or >= 16");
     return PG_OK;
@@ -137,7 +137,7 @@ extern "C" int pg_autotune(pg_graph *g, pg_plan *const *plans, int32_t n_plans, 
     if (kernel == PG_KERNEL_BATCHED) {
         knobs.push_back({&pg_tuning::batched_split_grain, {0, 128, 512, 2048}});
         knobs.push_back({&pg_tuning::batched_warps, {2, 4, 8}});
-        knobs.push_back({&pg_tuning::batched_regcap, {0, 1}});
+        knobs.push_back({&pg_tuning::batched_regcap, {0, 1, 2}});
         knobs.push_back({&pg_tuning::batched_chunk, {1, 2, 4, 8}});
         knobs.push_back({&pg_tuning::batched_blocks_per_sm, {1, 2, 4, 0}});
         knobs.push_back({&pg_tuning::hub_min_degree, {256, 1024, 4096}});

@@ -59,8 +59,8 @@ struct BatchArgs {
     unsigned long long *queue;
     int n;
     int chunk;                  // tasks per queue grab
-    int stride;                 // every stride-th task (timing samples)
-    long long n_tasks;          // ceil((n_split_tasks + n - n_split) / stride)
+    long long stride, offset;   // task selection: offset, offset + stride, ... (samples, partition)
+    long long n_tasks;          // selected tasks of the n_split_tasks + n - n_split
     // Ranks 0..n_split-1 (the highest degrees) are split: rank r owns tasks
     // split_prefix[r] .. split_prefix[r+1]-1, task j of S walking the level-1
     // candidates with index = j (mod S).  Later ranks are one task each.
@@ -89,11 +89,12 @@ __device__ void count_terms(const BatchArgs &a, const PgTrieNode &C, const int *
         }
 }
 
-// W warps per CTA; CAP = 1 limits the kernel to 64 registers per thread
-// (32 / W CTAs per SM: more resident warps to hide the latency of the
-// binary searches, at the price of some spilling).
+// W warps per CTA.  CAP limits the registers per thread so that more warps
+// are resident to hide the latency of the searches, at the price of some
+// spilling: 1 = 32 / W CTAs per SM (64 registers), 2 = 20 / W CTAs per SM
+// (about 100 registers); 0 = the compiler's choice.
 template <int W, int CAP>
-__global__ void __launch_bounds__(W * 32, CAP ? 32 / W : 0) k_count_batched(BatchArgs a) {
+__global__ void __launch_bounds__(W * 32, CAP == 1 ? 32 / W : CAP == 2 ? 20 / W : 0) k_count_batched(BatchArgs a) {
     __shared__ unsigned long long s_acc[W][2 * kMaxSlots];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(W * 32, CAP ? 32 / W : 0) k_count_batched(Batc
             if (task >= a.n_tasks) break;
             task_end = min(task + a.chunk, a.n_tasks);
         }
-        const long long tg = task * a.stride;
+        const long long tg = a.offset + task * a.stride;
         ++task;
         int v, part = 0, parts = 1;
         if (tg < a.n_split_tasks) {
@@ -231,7 +232,8 @@ void batched_kernel(int w, void **fn) {
 
 void *batched_fn(const pg_graph *g) {
     void *fn = nullptr;
-    if (g->tune.batched_regcap) batched_kernel<1>(batched_warps(g), &fn);
+    if (g->tune.batched_regcap == 1) batched_kernel<1>(batched_warps(g), &fn);
+    else if (g->tune.batched_regcap == 2) batched_kernel<2>(batched_warps(g), &fn);
     else batched_kernel<0>(batched_warps(g), &fn);
     return fn;
 }
@@ -689,11 +691,13 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.queue = g->ex->queues + queue_slot;
     a.n = (int)g->n;
     a.chunk = std::max(1, g->tune.batched_chunk);
-    a.stride = std::max(1, g->sample_stride);
+    const PgTaskSel sel = pg_task_sel(g);
+    a.stride = sel.stride;
+    a.offset = sel.offset;
     a.split_prefix = g->split_prefix;
     a.n_split = g->n_split;
     a.n_split_tasks = g->n_split_tasks;
-    a.n_tasks = (g->n_split_tasks + (g->n - g->n_split) + a.stride - 1) / a.stride;
+    a.n_tasks = sel.count(g->n_split_tasks + (g->n - g->n_split));
     a.counts = b->d_slot_counts;
     a.ctl = ctl ? *ctl : PgRunCtl{};
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));

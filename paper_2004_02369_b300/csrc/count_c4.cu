@@ -21,14 +21,15 @@
 // deg(a) * out-degree(a) (the Chiba-Nishizeki bound), so hubs are anchors of
 // few cycles' worth of work each.
 //
-// B300 mapping (two launches of one persistent grid of 4-warp CTAs):
-//  * first launch: anchors one per warp in rank order; counters live in a
-//    per-warp open-addressing hash table in shared memory sized for T_w.  An
-//    anchor of degree above kLightDeg, or with more than kLightT increments,
-//    is appended to a deferred list instead;
-//  * second launch: deferred anchors one per CTA; the counters are a dense
-//    n-entry array per CTA in global memory, incremented with atomicAdd and
-//    cleared by a second walk over the same suffixes.
+// B300 mapping (two persistent launches):
+//  * light pass (4-warp CTAs): anchors one per warp in rank order; counters
+//    live in a per-warp open-addressing hash table in shared memory sized
+//    for T_w.  An anchor of degree above kLightDeg, or with more than kLightT
+//    increments, is appended to a deferred list instead;
+//  * dense pass (16-warp CTAs, no shared tables, so more resident warps to
+//    cover the atomics' latency): deferred anchors one per CTA; the counters
+//    are a dense n-entry array per CTA in global memory, incremented with
+//    atomicAdd and cleared by a second walk over the same suffixes.
 //  Both walk the suffixes 32 neighbours a at a time: lanes binary-search
 //  their a's suffix start, a warp prefix sum flattens the 32 suffixes, and
 //  lanes read the flattened increments with coalesced loads.
@@ -37,9 +38,10 @@
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kBlock = kWarps * 32;
-constexpr int kLightDeg = 512;        // light anchors: degree <= kLightDeg
-constexpr int kHashCap = 2048;        // per-warp hash slots (power of two)
+constexpr int kBlock = kWarps * 32;   // light pass
+constexpr int kDenseBlock = 512;      // dense pass
+constexpr int kLightDeg = 256;        // light anchors: degree <= kLightDeg
+constexpr int kHashCap = 1024;        // per-warp hash slots (power of two)
 constexpr int kLightT = kHashCap / 2; // light anchors: at most this many increments
 constexpr int kEmpty = -1;
 
@@ -50,8 +52,7 @@ struct C4Args {
     int *deferred;          // anchors left to the CTAs
     unsigned long long *q;  // [0] warp cursor, [1] deferred count, [2] deferred cursor
     unsigned long long *count; // (low, high)
-    int mode;               // 0: anchors per warp; 1: deferred anchors per CTA
-    int stride;             // every stride-th anchor (timing samples)
+    long long stride, offset; // anchor selection: offset, offset + stride, ... (samples, partition)
     PgRunCtl ctl;
 };
 
@@ -205,66 +206,75 @@ __device__ bool light_anchor(const C4Args &a, int w, WarpSmem &sm, int lane, uns
     return true;
 }
 
-__global__ void __launch_bounds__(kBlock) k_count_c4(C4Args a) {
+// Light pass: one warp per anchor, rank order; heavy anchors deferred.
+__global__ void __launch_bounds__(kBlock) k_c4_light(C4Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_task, s_next, s_p;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const bool polled = a.ctl.words != nullptr;
-    if (polled && threadIdx.x == 0) ctl_begin(a.ctl);
+    if (polled && lane == 0) ctl_begin(a.ctl);
     unsigned long long cnt = 0;
-    if (a.mode == 0) {
-        // ---- one warp per anchor, rank order; heavy ones deferred
-        WarpSmem &sm = ((WarpSmem *)smem_raw)[warp];
-        const long long n_tasks = ((long long)a.n + a.stride - 1) / a.stride;
-        for (;;) {
-            if (polled && ctl_stop(a.ctl, lane)) break;
-            unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(a.q, 1ull);
-            t = __shfl_sync(PG_FULL, t, 0);
-            if ((long long)t >= n_tasks) break;
-            const int w = (int)(t * (unsigned long long)a.stride);
-            if (!light_anchor(a, w, sm, lane, cnt) && lane == 0) a.deferred[atomicAdd(a.q + 1, 1ull)] = w;
-        }
-    } else {
-        // ---- one CTA per deferred anchor, dense counters
-        unsigned *C = a.dense + (size_t)blockIdx.x * (size_t)a.n;
-        const unsigned long long n_def = *(volatile unsigned long long *)(a.q + 1);
-        for (;;) {
-            if (threadIdx.x == 0) {
-                int w = -1;
-                if (!polled || !ctl_poll(a.ctl)) {
-                    const unsigned long long t = atomicAdd(a.q + 2, 1ull);
-                    if (t < n_def) w = a.deferred[t];
-                }
-                s_task = w;
-            }
-            __syncthreads();
-            const int w = s_task;
-            __syncthreads();
-            if (w < 0) break;
-            cnt += dense_anchor(a, w, C, &s_next, &s_p);
-        }
+    WarpSmem &sm = ((WarpSmem *)smem_raw)[warp];
+    const long long n_tasks = a.n > a.offset ? ((long long)a.n - a.offset + a.stride - 1) / a.stride : 0;
+    for (;;) {
+        if (polled && ctl_stop(a.ctl, lane)) break;
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.q, 1ull);
+        t = __shfl_sync(PG_FULL, t, 0);
+        if ((long long)t >= n_tasks) break;
+        const int w = (int)((unsigned long long)a.offset + t * (unsigned long long)a.stride);
+        if (!light_anchor(a, w, sm, lane, cnt) && lane == 0) a.deferred[atomicAdd(a.q + 1, 1ull)] = w;
     }
     const unsigned __int128 tot = warp_sum_u128(cnt);
     if (lane == 0 && tot) atomic_add_u128(a.count, tot);
 }
 
-int c4_grid(const pg_graph *g, int *grid) {
+// Dense pass: one CTA per deferred anchor on its dense counter array.
+__global__ void __launch_bounds__(kDenseBlock) k_c4_dense(C4Args a) {
+    __shared__ int s_task, s_next, s_p;
+    const int lane = threadIdx.x & 31;
+    const bool polled = a.ctl.words != nullptr;
+    if (polled && threadIdx.x == 0) ctl_begin(a.ctl);
+    unsigned long long cnt = 0;
+    unsigned *C = a.dense + (size_t)blockIdx.x * (size_t)a.n;
+    const unsigned long long n_def = *(volatile unsigned long long *)(a.q + 1);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int w = -1;
+            if (!polled || !ctl_poll(a.ctl)) {
+                const unsigned long long t = atomicAdd(a.q + 2, 1ull);
+                if (t < n_def) w = a.deferred[t];
+            }
+            s_task = w;
+        }
+        __syncthreads();
+        const int w = s_task;
+        __syncthreads();
+        if (w < 0) break;
+        cnt += dense_anchor(a, w, C, &s_next, &s_p);
+    }
+    const unsigned __int128 tot = warp_sum_u128(cnt);
+    if (lane == 0 && tot) atomic_add_u128(a.count, tot);
+}
+
+constexpr size_t kLightSmem = (size_t)kWarps * sizeof(WarpSmem);
+
+int c4_grids(const pg_graph *g, int *light, int *dense) {
     int per_sm = 0;
-    const size_t smem = (size_t)kWarps * sizeof(WarpSmem);
-    PG_CUDA(cudaFuncSetAttribute(k_count_c4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_c4, kBlock, smem));
-    *grid = std::max(1, per_sm) * g->num_sms;
+    PG_CUDA(cudaFuncSetAttribute(k_c4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLightSmem));
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4_light, kBlock, kLightSmem));
+    *light = std::max(1, per_sm) * g->num_sms;
+    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4_dense, kDenseBlock, 0));
+    *dense = std::max(1, per_sm) * g->num_sms;
     return PG_OK;
 }
 
 }  // namespace
 
 size_t pg_c4_scratch_bytes(const pg_graph *g) {
-    int grid = 0;
-    if (c4_grid(g, &grid) != PG_OK) grid = 2 * g->num_sms;
-    return (size_t)grid * (size_t)g->n * sizeof(unsigned) + (size_t)(g->n + 1) * sizeof(int) + 256;
+    int light = 0, dense = 0;
+    if (c4_grids(g, &light, &dense) != PG_OK) dense = 4 * g->num_sms;
+    return (size_t)dense * (size_t)g->n * sizeof(unsigned) + (size_t)(g->n + 1) * sizeof(int) + 256;
 }
 
 // Adds the number of edge-induced 4-cycles of g into count_dev (128-bit,
@@ -274,10 +284,10 @@ int pg_launch_c4(pg_graph *g, unsigned long long *count_dev, int queue_slot, cud
     if (g->n < 4) return PG_OK;
     if (queue_slot + 3 > PG_CTL_WORDS_SLOT) return pg_set_error(PG_EINVAL, "queue slot out of range");
     if (g->adj_entries >= (1ll << 32)) return pg_set_error(PG_EUNSUPPORTED, "4-cycle kernel: adjacency above 2^32 entries");
-    int grid = 0;
-    int rc = c4_grid(g, &grid);
+    int light = 0, dense = 0;
+    int rc = c4_grids(g, &light, &dense);
     if (rc) return rc;
-    const size_t dense_bytes = (size_t)grid * (size_t)g->n * sizeof(unsigned);
+    const size_t dense_bytes = (size_t)dense * (size_t)g->n * sizeof(unsigned);
     if (pg_c4_scratch_bytes(g) > g->ex->scratch_bytes) return pg_set_error(PG_ENOMEM, "scratch smaller than the 4-cycle kernel needs");
     C4Args a;
     a.g = g->d;
@@ -286,15 +296,15 @@ int pg_launch_c4(pg_graph *g, unsigned long long *count_dev, int queue_slot, cud
     a.deferred = (int *)((unsigned char *)g->ex->scratch + dense_bytes);
     a.q = g->ex->queues + queue_slot;
     a.count = count_dev;
-    a.stride = std::max(1, g->sample_stride);
+    const PgTaskSel sel = pg_task_sel(g);
+    a.stride = sel.stride;
+    a.offset = sel.offset;
     a.ctl = ctl ? *ctl : PgRunCtl{};
     PG_CUDA(cudaMemsetAsync(a.dense, 0, dense_bytes, s));
     PG_CUDA(cudaMemsetAsync(a.q, 0, 3 * sizeof(unsigned long long), s));
-    const size_t smem = (size_t)kWarps * sizeof(WarpSmem);
-    for (int mode = 0; mode < 2; ++mode) {
-        a.mode = mode;
-        k_count_c4<<<grid, kBlock, smem, s>>>(a);
-        PG_CUDA(cudaGetLastError());
-    }
+    k_c4_light<<<light, kBlock, kLightSmem, s>>>(a);
+    PG_CUDA(cudaGetLastError());
+    k_c4_dense<<<dense, kDenseBlock, 0, s>>>(a);
+    PG_CUDA(cudaGetLastError());
     return PG_OK;
 }

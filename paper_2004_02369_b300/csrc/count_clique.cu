@@ -67,10 +67,13 @@ struct CliqueArgs {
     unsigned long long *counts;
     int chunk;                 // light start vertices per queue grab
     int heavy_min;             // light vertices have out-degree <= heavy_min (<= kLightD)
-    int stride;                // every stride-th start vertex (timing samples)
-    long long n_light_tasks;   // ceil(n / stride)
-    long long n_heavy_tasks;   // ceil(n_heavy / stride)
+    int stride;                // task selection: offset, offset + stride, ... (samples, partition)
+    int offset;
+    long long n_light_tasks;   // selected start vertices
+    long long n_heavy_tasks;   // selected entries of the heavy list
     PgRunCtl ctl;              // early termination / work budget (words null: none)
+    int plain;                 // extended variant only: 0 persistent; 1 one CTA per heavy start
+                               // vertex (blockIdx); 2 one warp per light start vertex (global warp)
 };
 
 // cnt[S] = lane counter of (S+3)-cliques.  A lane adds at most 2^16 per
@@ -437,12 +440,17 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
         ht.rows = (unsigned *)(ht.pre + a.dpad + 4);
         ht.ws = a.hws;
     }
-    for (;;) {
+    for (int iter = 0;; ++iter) {
         if (threadIdx.x == 0) {
             int v = -1;
-            if (!polled || !ctl_poll(a.ctl)) {
+            if (XT && a.plain) {
+                // non-persistent: this block's own heavy start vertex, once
+                if (a.plain == 1 && iter == 0 && blockIdx.x < a.n_heavy_tasks)
+                    v = a.heavy[(unsigned long long)a.offset + blockIdx.x * (unsigned long long)a.stride];
+            } else if (!polled || !ctl_poll(a.ctl)) {
                 const unsigned long long h = atomicAdd(a.queue + 1, 1ull);
-                if (h < (unsigned long long)a.n_heavy_tasks) v = a.heavy[h * (unsigned long long)a.stride];
+                if (h < (unsigned long long)a.n_heavy_tasks)
+                    v = a.heavy[(unsigned long long)a.offset + h * (unsigned long long)a.stride];
             }
             ctl[0] = v;
             ctl[1] = 0; // rows traversed
@@ -484,16 +492,24 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
         lt.rows = (unsigned *)(lt.pre + kLightD + 1);
         lt.ws = kLightWs;
     }
-    for (;;) {
+    for (int iter = 0;; ++iter) {
         if (polled && ctl_stop(a.ctl, lane)) break;
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, (unsigned long long)a.chunk);
-        base = __shfl_sync(PG_FULL, base, 0);
+        int chunk = a.chunk;
+        if (XT && a.plain) {
+            // non-persistent: this warp's own light start vertex, once
+            if (a.plain != 2 || iter > 0) break;
+            base = (unsigned long long)blockIdx.x * kWarps + warp;
+            chunk = 1;
+        } else {
+            if (lane == 0) base = atomicAdd(a.queue, (unsigned long long)a.chunk);
+            base = __shfl_sync(PG_FULL, base, 0);
+        }
         if (base >= (unsigned long long)a.n_light_tasks) break;
-        for (int q = 0; q < a.chunk; ++q) {
+        for (int q = 0; q < chunk; ++q) {
             const unsigned long long t = base + (unsigned long long)q;
             if (t >= (unsigned long long)a.n_light_tasks) break;
-            const int v = (int)(t * (unsigned long long)a.stride);
+            const int v = (int)((unsigned long long)a.offset + t * (unsigned long long)a.stride);
             const int4 vi = __ldg(&g.vinfo[v]);
             const int d = vi.z;
             if (d < a.kmin - 1 || d > a.heavy_min) continue;
@@ -613,10 +629,13 @@ int launch(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev, unsi
     a.counts = counts_dev;
     a.chunk = g->tune.clique_chunk;
     a.heavy_min = g->heavy_min_built; // the threshold the heavy list was built with
-    a.stride = std::max(1, g->sample_stride);
-    a.n_light_tasks = (g->n + a.stride - 1) / a.stride;
-    a.n_heavy_tasks = (g->n_heavy + a.stride - 1) / a.stride;
+    const PgTaskSel sel = pg_task_sel(g);
+    a.stride = (int)sel.stride;
+    a.offset = (int)sel.offset;
+    a.n_light_tasks = sel.count(g->n);
+    a.n_heavy_tasks = sel.count(g->n_heavy);
     a.ctl = rctl ? *rctl : PgRunCtl{};
+    a.plain = 0;
     if (a.ctl.target > 0 && (kmin != kmax || !a.ctl.words))
         return pg_set_error(PG_EINVAL, "internal: existence mode needs one clique size and control words");
     const bool xt = extended_variant(kmin, kmax, rctl);
@@ -651,6 +670,54 @@ int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts
     if (queue_slot + 1 >= PG_CTL_WORDS_SLOT) return pg_set_error(PG_EINVAL, "queue slot out of range");
     return launch(g, kmin, kmax, counts_dev, g->ex->queues + queue_slot, g->ex->scratch,
                   (long long)(g->ex->scratch_bytes / std::max<size_t>(pg_clique_slab_bytes(g, kmax), 1)), s, ctl);
+}
+
+// The plain form of the same traversal: no persistence and no shared
+// traversal of several sizes.  One launch of one CTA per heavy start vertex
+// and one launch of one warp per light start vertex, for a single clique
+// size k; adds into counts_dev (low, high).  Heavy tiles must fit shared
+// memory.
+int pg_launch_clique_plain(pg_graph *g, int k, unsigned long long *counts_dev, cudaStream_t s) {
+    if (k < 3 || k > PG_MAX_CLIQUE) return pg_set_error(PG_EINVAL, "clique size must be 3..16");
+    if (g->n == 0) return PG_OK;
+    if (g->max_out >= 65536) return pg_set_error(PG_EUNSUPPORTED, "clique kernel needs out-degrees below 65536");
+    const int kvar = kmax_variant(k);
+    Layout L = layout_for(g, kvar);
+    if (!L.a.heavy_in_smem)
+        return pg_set_error(PG_EUNSUPPORTED, "plain clique launches need the heavy tiles in shared memory");
+    int rc = ensure_attributes(g->device);
+    if (rc) return rc;
+    CliqueArgs a = L.a;
+    a.g = g->d;
+    a.kmin = a.kmax = k;
+    a.heavy = g->heavy;
+    a.n_heavy = (int)g->n_heavy;
+    a.n = (int)g->n;
+    a.slabs = nullptr;
+    a.queue = nullptr;
+    a.counts = counts_dev;
+    a.chunk = 1;
+    a.heavy_min = g->heavy_min_built;
+    const PgTaskSel sel = pg_task_sel(g);
+    a.stride = (int)sel.stride;
+    a.offset = (int)sel.offset;
+    a.n_light_tasks = sel.count(g->n);
+    a.n_heavy_tasks = sel.count(g->n_heavy);
+    a.ctl = PgRunCtl{};
+    void *fn = kvar > 8 ? (void *)k_count_clique<3, 16, true> : (void *)k_count_clique<3, 8, true>;
+    void *args[] = {&a};
+    if (a.n_heavy_tasks > 0) {
+        a.plain = 1;
+        PG_CUDA(cudaLaunchKernel(fn, dim3((unsigned)a.n_heavy_tasks), dim3(kBlock), args, L.smem_bytes, s));
+        PG_CUDA(cudaGetLastError());
+    }
+    if (a.n_light_tasks > 0) {
+        a.plain = 2;
+        const long long blocks = (a.n_light_tasks + kWarps - 1) / kWarps;
+        PG_CUDA(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(kBlock), args, L.smem_bytes, s));
+        PG_CUDA(cudaGetLastError());
+    }
+    return PG_OK;
 }
 
 // Same kernel on caller-supplied scratch: `queue` = two 64-bit counters

@@ -37,7 +37,8 @@ struct GenericArgs {
     long long warp_stride;      // ints per warp
     long long lvl_off[PGP_MAXK]; // offset of level l's buffer inside a warp's region
     unsigned long long *queue;  // dynamic task counter (persistent mode)
-    unsigned long long n_tasks;
+    unsigned long long n_tasks; // selected tasks: offset + t * stride over (start vertex, order) pairs
+    unsigned long long offset, stride;
     int persistent;             // 0: one task per warp, no queue
     unsigned long long *counts; // (low, high)
     // run control: existence mode (ctl.target > 0) publishes counts after
@@ -97,8 +98,9 @@ __global__ void __launch_bounds__(kBlock) k_count_generic(GenericArgs a) {
             t = __shfl_sync(PG_FULL, t, 0);
         }
         if (t >= a.n_tasks) break;
-        const int v = (int)(t / (unsigned long long)a.n_orders);
-        const int o = (int)(t % (unsigned long long)a.n_orders);
+        const unsigned long long tt = a.offset + t * a.stride;
+        const int v = (int)(tt / (unsigned long long)a.n_orders);
+        const int o = (int)(tt % (unsigned long long)a.n_orders);
         acc += run_task(a, v, a.orders[o], wbuf, lane);
         if (a.ctl.target && acc) {
             if (lane == 0) ctl_publish(a.ctl, a.counts, acc);
@@ -144,7 +146,7 @@ long long level_layout(const pg_graph *g, const pg_plan *p, long long *off) {
 }
 
 unsigned long long n_tasks_of(const pg_graph *g, const pg_plan *p) {
-    return (unsigned long long)g->n * (unsigned long long)p->h.orders.size();
+    return (unsigned long long)pg_task_sel(g).count((long long)g->n * (long long)p->h.orders.size());
 }
 
 int grid_of(const pg_graph *g, const pg_plan *p, bool persistent) {
@@ -173,6 +175,9 @@ int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_
     a.scratch = (int *)g->ex->scratch;
     a.queue = g->ex->queues + queue_slot;
     a.n_tasks = n_tasks_of(g, p);
+    const PgTaskSel sel = pg_task_sel(g);
+    a.offset = (unsigned long long)sel.offset;
+    a.stride = (unsigned long long)sel.stride;
     a.persistent = persistent ? 1 : 0;
     a.counts = counts_dev;
     a.ctl = ctl ? *ctl : PgRunCtl{};

@@ -75,6 +75,90 @@ __device__ __forceinline__ bool in_slice(const DevGraph &g, const Slice &s, int 
     return contains_g(s.p, s.len, x);
 }
 
+// Four membership tests against one slice at once (x[j] in the slice,
+// ANDed into ok[j], negated for set differences).  The four branch-free
+// binary searches run over the same length, so each step issues four
+// independent loads: four times the memory-level parallelism of one search
+// per lane.  Hub slices answer from their membership bitmap for the keys
+// still in play (ok[j]); the searches' loads stay inside the slice whatever
+// the keys are.
+__device__ __forceinline__ void in_slice4(const DevGraph &g, const Slice &s, const int (&x)[4], bool (&ok)[4],
+                                          bool negate) {
+    bool f[4];
+    if (s.owner >= 0 && s.owner < g.n_hubs) {
+        const unsigned *row = g.hubbits + (size_t)s.owner * g.hub_stride;
+        // only keys still in play are looked up: the others may be padding
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f[j] = ok[j] && ((__ldg(row + ((unsigned)x[j] >> 5)) >> (x[j] & 31)) & 1u);
+    } else if (s.len <= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f[j] = false;
+    } else {
+        const int *p = s.p;
+        int b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        int n = s.len;
+        while (n > 1) {
+            const int half = n >> 1;
+            const int v0 = __ldg(p + b0 + half - 1), v1 = __ldg(p + b1 + half - 1), v2 = __ldg(p + b2 + half - 1),
+                      v3 = __ldg(p + b3 + half - 1);
+            b0 += v0 < x[0] ? half : 0;
+            b1 += v1 < x[1] ? half : 0;
+            b2 += v2 < x[2] ? half : 0;
+            b3 += v3 < x[3] ? half : 0;
+            n -= half;
+        }
+        f[0] = __ldg(p + b0) == x[0];
+        f[1] = __ldg(p + b1) == x[1];
+        f[2] = __ldg(p + b2) == x[2];
+        f[3] = __ldg(p + b3) == x[3];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ok[j] = ok[j] && (f[j] != negate);
+}
+
+// The driver slice d of a level, read four elements per lane with one
+// aligned 16-byte load: lists start 16-byte aligned and are padded to 4
+// entries, so the groups covering d stay inside its list.  Group g of a
+// warp step holds elements d.p[-off + 4 * (base/4 + lane) + j].
+struct Driver4 {
+    const int4 *v;
+    int off, total; // elements before d.p in its group; off + d.len
+};
+
+__device__ __forceinline__ Driver4 driver4(const Slice &d) {
+    Driver4 r;
+    r.off = (int)(((uintptr_t)d.p >> 2) & 3u);
+    r.v = (const int4 *)(d.p - r.off);
+    r.total = d.len + r.off;
+    return r;
+}
+
+// Lane's four elements at warp step `base` (a multiple of 128) and which of
+// them lie inside the slice.
+__device__ __forceinline__ void driver4_load(const Driver4 &dv, int base, int lane, int (&x)[4], bool (&ok)[4]) {
+    const int q = base + 4 * lane;
+    int4 t = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff);
+    if (q < dv.total) t = __ldg(dv.v + (q >> 2));
+    x[0] = t.x;
+    x[1] = t.y;
+    x[2] = t.z;
+    x[3] = t.w;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ok[j] = q + j >= dv.off && q + j < dv.total;
+}
+
+// Warp-wide exclusive prefix of c (lane order); *total gets the sum.
+__device__ __forceinline__ int warp_excl_scan(int c, int lane, int *total) {
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(PG_FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    *total = __shfl_sync(PG_FULL, incl, 31);
+    return incl - c;
+}
+
 // 128-bit exact accumulation into two 64-bit words (low, high).
 __device__ __forceinline__ void atomic_add_u128(unsigned long long *c, unsigned __int128 x) {
     const unsigned long long lo = (unsigned long long)x;

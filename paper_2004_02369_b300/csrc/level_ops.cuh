@@ -28,7 +28,25 @@ __device__ __forceinline__ bool pass_label_excl(const DevGraph &g, const PgLevel
     return ok;
 }
 
-// Materialise the candidate set of (non-last) level L into buf; returns size.
+// x[j] pass label and exclusion tests of level L (ANDed into ok[j]).
+__device__ __forceinline__ void label_excl4(const DevGraph &g, const PgLevel &L, const int *m, const int (&x)[4],
+                                            bool (&ok)[4]) {
+    for (int i = 0; i < L.n_excl; ++i) {
+        const int e = m[L.excl_src[i]];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ok[j] = ok[j] && x[j] != e;
+    }
+    if (L.label >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) ok[j] = __ldg(&g.vinfo[x[j]].w) == L.label;
+    }
+}
+
+// Materialise the candidate set of (non-last) level L into buf, in
+// ascending order; returns its size.  Each lane takes four driver elements
+// per step (one 16-byte load) and tests them against the other lists four
+// searches at a time; a warp prefix sum compacts the survivors.
 static __device__ __noinline__ int fill_level(const DevGraph &g, const PgLevel &L, const int *m, int *buf, int lane) {
     const LevelRange r = level_range(L, m);
     if (r.lo + 1 >= r.hi) return 0;
@@ -40,29 +58,53 @@ static __device__ __noinline__ int fill_level(const DevGraph &g, const PgLevel &
         s[i] = bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi, w);
         if (s[i].len < s[drv].len) drv = i;
     }
-    const Slice d = s[drv];
+    const Driver4 dv = driver4(s[drv]);
     int n_out = 0;
-    for (int base = 0; base < d.len; base += 32) {
-        const int idx = base + lane;
-        bool ok = idx < d.len;
-        int x = 0;
-        if (ok) {
-            x = __ldg(d.p + idx);
-            for (int i = 0; i < L.n_int && ok; ++i)
-                if (i != drv) ok = in_slice(g, s[i], x);
-            for (int i = 0; i < L.n_diff && ok; ++i) {
-                const int w = m[L.diff_src[i]];
-                const int4 vi = __ldg(&g.vinfo[w]);
-                ok = !in_slice(g, Slice{adj_of(g, vi), vi.y, w}, x);
-            }
-            if (ok) ok = pass_label_excl(g, L, m, x);
+    for (int base = 0; base < dv.total; base += 128) {
+        int x[4];
+        bool ok[4];
+        driver4_load(dv, base, lane, x, ok);
+        for (int i = 0; i < L.n_int; ++i)
+            if (i != drv) in_slice4(g, s[i], x, ok, false);
+        for (int i = 0; i < L.n_diff; ++i) {
+            const int w = m[L.diff_src[i]];
+            const int4 vi = __ldg(&g.vinfo[w]);
+            in_slice4(g, Slice{adj_of(g, vi), vi.y, w}, x, ok, true);
         }
-        const unsigned bal = __ballot_sync(PG_FULL, ok);
-        if (ok) buf[n_out + __popc(bal & ((1u << lane) - 1))] = x;
-        n_out += __popc(bal);
+        label_excl4(g, L, m, x, ok);
+        const int c = (int)ok[0] + (int)ok[1] + (int)ok[2] + (int)ok[3];
+        int step_total;
+        int pos = n_out + warp_excl_scan(c, lane, &step_total);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) buf[pos++] = x[j];
+        n_out += step_total;
     }
     __syncwarp();
     return n_out;
+}
+
+// Number of elements of slice d that lie in every slice of s[0, n) other
+// than index `skip`, in none of s[n, n + nd), and carry `label` (>= 0).
+__device__ __forceinline__ unsigned long long count_filtered(const DevGraph &g, const Slice &d, const Slice *s,
+                                                              int n, int skip, int nd, int label, int lane) {
+    const Driver4 dv = driver4(d);
+    unsigned c = 0;
+    for (int base = 0; base < dv.total; base += 128) {
+        int x[4];
+        bool ok[4];
+        driver4_load(dv, base, lane, x, ok);
+        for (int i = 0; i < n; ++i)
+            if (i != skip) in_slice4(g, s[i], x, ok, false);
+        for (int i = 0; i < nd; ++i) in_slice4(g, s[n + i], x, ok, true);
+        if (label >= 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j]) ok[j] = __ldg(&g.vinfo[x[j]].w) == label;
+        }
+        c += (unsigned)ok[0] + (unsigned)ok[1] + (unsigned)ok[2] + (unsigned)ok[3];
+    }
+    return (unsigned long long)__reduce_add_sync(PG_FULL, c);
 }
 
 // |S| of the last level (before C(|S|, g)).
@@ -96,47 +138,30 @@ static __device__ __noinline__ unsigned long long count_last(const DevGraph &g, 
     if (labeled || ni > 1) ie += (long long)s[drv].len * (ni - 1 + (labeled ? 1 : 0));
     long long total = 0;
     if (nd == 0 || direct <= ie) {
-        const Slice d = s[drv];
-        unsigned long long c = 0;
-        for (int base = 0; base < d.len; base += 32) {
-            const int idx = base + lane;
-            bool ok = idx < d.len;
-            if (ok) {
-                const int x = __ldg(d.p + idx);
-                for (int i = 0; i < ni && ok; ++i)
-                    if (i != drv) ok = in_slice(g, s[i], x);
-                for (int j = 0; j < nd && ok; ++j) ok = !in_slice(g, s[ni + j], x);
-                if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
-            }
-            c += __popc(__ballot_sync(PG_FULL, ok));
-        }
-        total = (long long)c;
+        total = (long long)count_filtered(g, s[drv], s, ni, drv, nd, L.label, lane);
     } else {
         // |A \ (B1 u ... u Bd)| = sum over T subset of diffs of (-1)^|T| |A n B_T|
         for (unsigned T = 0; T < (1u << nd); ++T) {
             int dd = drv;
             for (int j = 0; j < nd; ++j)
                 if ((T >> j & 1) && s[ni + j].len < s[dd].len) dd = ni + j;
-            const Slice d = s[dd];
             long long term;
             if (ni == 1 && T == 0 && !labeled) {
-                term = d.len;
+                term = s[dd].len;
             } else {
-                unsigned long long c = 0;
-                for (int base = 0; base < d.len; base += 32) {
-                    const int idx = base + lane;
-                    bool ok = idx < d.len;
-                    if (ok) {
-                        const int x = __ldg(d.p + idx);
-                        for (int i = 0; i < ni && ok; ++i)
-                            if (i != dd) ok = in_slice(g, s[i], x);
-                        for (int j = 0; j < nd && ok; ++j)
-                            if ((T >> j & 1) && ni + j != dd) ok = in_slice(g, s[ni + j], x);
-                        if (ok && labeled) ok = (__ldg(&g.vinfo[x].w) == L.label);
-                    }
-                    c += __popc(__ballot_sync(PG_FULL, ok));
+                // the intersected lists: the regular ones and the differences in T
+                Slice t[2 * PGP_MAXK];
+                int nt = 0, skip = -1;
+                for (int i = 0; i < ni; ++i) {
+                    if (i == dd) skip = nt;
+                    t[nt++] = s[i];
                 }
-                term = (long long)c;
+                for (int j = 0; j < nd; ++j)
+                    if (T >> j & 1) {
+                        if (ni + j == dd) skip = nt;
+                        t[nt++] = s[ni + j];
+                    }
+                term = (long long)count_filtered(g, s[dd], t, nt, skip, 0, L.label, lane);
             }
             total += (__popc(T) & 1) ? -term : term;
         }

@@ -119,7 +119,23 @@ struct pg_graph {
     int sample_stride = 1;
     // device work budget of the synchronous calls (pg_set_time_budget), ns; 0 = none
     unsigned long long budget_ns = 0;
+    // task partition (pg_set_partition): launches take the tasks t with
+    // t mod n_parts == part (one GPU's share of a multi-GPU count)
+    int part = 0, n_parts = 1;
 };
+
+// Task selection of a launch: tasks offset, offset + stride, ... below n
+// (timing samples and the task partition combined).
+struct PgTaskSel {
+    long long offset, stride;
+    long long count(long long n) const { return n > offset ? (n - offset + stride - 1) / stride : 0; }
+};
+inline PgTaskSel pg_task_sel(const pg_graph *g) {
+    PgTaskSel t;
+    t.stride = (long long)(g->sample_stride > 1 ? g->sample_stride : 1) * (g->n_parts > 1 ? g->n_parts : 1);
+    t.offset = g->n_parts > 1 ? g->part : 0;
+    return t;
+}
 
 // Run control of a synchronous call on g: the graph's work budget (if any)
 // and, for existence queries, a target.  Zeroes the control words on s.
@@ -185,6 +201,8 @@ size_t pg_match_scratch_bytes(const pg_graph *g, const pg_plan *p);
 int pg_launch_clique(pg_graph *g, int kmin, int kmax, unsigned long long *counts_dev,
                      int queue_slot, cudaStream_t s, const PgRunCtl *ctl = nullptr);
 size_t pg_clique_scratch_bytes(const pg_graph *g, int kmax);
+// non-persistent form, one size per launch pair (PG_KERNEL_CLIQUE_NONPERSISTENT)
+int pg_launch_clique_plain(pg_graph *g, int k, unsigned long long *counts_dev, cudaStream_t s);
 size_t pg_clique_slab_bytes(const pg_graph *g, int kmax);
 
 // fsm.cu

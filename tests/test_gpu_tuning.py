@@ -38,7 +38,7 @@ def motif_case(pg):
 
 CLIQUE_VALUES = {"clique_heavy_min": [8, 16, 33, 64], "clique_chunk": [1, 3, 16, 64],
                  "clique_blocks_per_sm": [1, 2, 0], "clique_min_blocks": [4, 3]}
-BATCHED_VALUES = {"batched_split_grain": [16, 100, 0, 512], "batched_regcap": [1, 0], "batched_warps": [2, 8, 4],
+BATCHED_VALUES = {"batched_split_grain": [16, 100, 0, 512], "batched_regcap": [1, 2, 0], "batched_warps": [2, 8, 4],
                   "batched_chunk": [1, 5, 64], "batched_blocks_per_sm": [1, 3, 0],
                   "hub_min_degree": [1, 300, 1 << 30, 1024], "hub_max": [0, 7, 2048, 512]}
 
@@ -98,7 +98,7 @@ def test_tuning_validation(pg):
     g = sg.erdos_renyi(100, 0.05, 304)
     G = pg.Graph.from_synth(g)
     for bad in [dict(batched_warps=3), dict(clique_chunk=0), dict(clique_heavy_min=65), dict(hub_max=-1),
-                dict(batched_split_grain=8), dict(batched_regcap=2), dict(clique_min_blocks=2)]:
+                dict(batched_split_grain=8), dict(batched_regcap=3), dict(clique_min_blocks=2)]:
         with pytest.raises(pg.PgError) as e:
             pg.set_tuning(G, **bad)
         assert e.value.code == pg.PG_EINVAL
