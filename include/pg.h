@@ -45,6 +45,7 @@ extern "C" {
 #define PG_ETIMEOUT 4  /* a kernel's work budget ran out; partial results discarded */
 #define PG_EDEVICE 5   /* CUDA runtime error (launch failure, no device, ...) */
 #define PG_EUNSUPPORTED 6 /* valid request that this build does not implement */
+#define PG_ECANCELED 7 /* the query was cancelled (pg_server_cancel) */
 
 #define PG_MAX_PATTERN 8 /* pattern vertices, regular plus anti-vertices */
 #define PG_MAX_CLIQUE 16 /* k-cliques (unlabeled complete patterns) up to this size */
@@ -548,6 +549,38 @@ int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *o
            int64_t *n_frequent, void *stream);
 
 /*
+ * pg_fsm_general - labeled frequent subgraph mining for any number of edges
+ * (Section 3.2 FSM program: match, keep the patterns whose MNI support
+ * (Section 2.1) is >= threshold, extendByEdge the survivors with label
+ * discovery (Section 3.2.1), repeat; MNI is anti-monotone, so candidates
+ * with an infrequent connected sub-pattern are never matched).  Domains are
+ * decided vertex by vertex on the GPU: for each candidate and each orbit of
+ * its automorphism group, one warp per data vertex with the orbit's label
+ * searches for one match that binds the orbit's vertex to it and stops at
+ * the first (Section 5.5 domains; a candidate leaves as soon as one of its
+ * domains is below the threshold).  Supports are exact.
+ *   max_edges  1..PG_FSM_MAX_EDGES (patterns up to 8 vertices).
+ *   out        host array of `capacity` records, sorted by edge count then
+ *              canonical form: vertices 0..k-1 with their labels, edges as
+ *              pairs u < v, and the MNI support.  *n_frequent = size of the
+ *              frequent set (exact even when capacity is short).
+ * For max_edges <= 3 the frequent set equals pg_fsm's (a second,
+ * independent GPU path).  Needs a labeled graph.  Synchronous; allocates
+ * its buffers.  Errors: PG_EINVAL (unlabeled graph, max_edges or threshold
+ * out of range), PG_ETRUNC, PG_ENOMEM, PG_EDEVICE.
+ */
+#define PG_FSM_MAX_EDGES 7
+typedef struct {
+    int32_t k;        /* pattern vertices */
+    int32_t n_edges;
+    int32_t edges[2 * PG_FSM_MAX_EDGES];
+    int32_t labels[PG_MAX_PATTERN]; /* -1 past k */
+    uint64_t support;
+} pg_fsm_general_pattern;
+int pg_fsm_general(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_general_pattern *out,
+                   int64_t capacity, int64_t *n_frequent, void *stream);
+
+/*
  * pg_labeled_motif3 - labeled 3-motifs with label discovery (the paper's
  * labeled motif workload, Section 6; labels discovered from the matches,
  * Section 3.2.1): the number of vertex-induced matches of every labeled
@@ -629,6 +662,15 @@ int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_server **out);
 int pg_server_submit(pg_server *s, const pg_pattern_desc *q, uint64_t *ticket);
 /* pg_server_poll - move up to max_results finished results into out (host). */
 int pg_server_poll(pg_server *s, pg_query_result *out, int32_t max_results, int32_t *n_out);
+/* pg_server_cancel - withdraw a query.  A query still waiting gets a
+ * PG_ECANCELED result at once.  A query being counted stops its launch: the
+ * launch's stop flag is raised from a separate stream, the kernels leave at
+ * their next poll (between tasks and between first-level candidates), the
+ * query gets PG_ECANCELED and the other queries of that launch go back to
+ * the front of the queue (they are counted again, results unchanged).  A
+ * query that already has a result is left alone.  Errors: PG_EINVAL (NULL
+ * server, ticket never issued or already finished). */
+int pg_server_cancel(pg_server *s, uint64_t ticket);
 /* pg_server_drain - wait until every submitted query has a result, or
  * PG_ETIMEOUT after timeout_s seconds. */
 int pg_server_drain(pg_server *s, double timeout_s);

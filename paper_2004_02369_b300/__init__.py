@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpg.so")
 
-PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETRUNC, PG_ETIMEOUT, PG_EDEVICE, PG_EUNSUPPORTED = range(7)
+PG_OK, PG_EINVAL, PG_ENOMEM, PG_ETRUNC, PG_ETIMEOUT, PG_EDEVICE, PG_EUNSUPPORTED, PG_ECANCELED = range(8)
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_CLIQUE_PLAIN, KERNEL_CLIQUE, KERNEL_BATCHED, KERNEL_CLIQUE_NONPERSISTENT = range(6)
 MAX_PATTERN = 8
 MAX_CLIQUE = 16
@@ -75,6 +75,7 @@ _lib.pg_server_create.argtypes = [_vp, _vp, ctypes.POINTER(_vp)]
 _lib.pg_server_submit.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_uint64)]
 _lib.pg_server_poll.argtypes = [_vp, _vp, _i32, ctypes.POINTER(_i32)]
 _lib.pg_server_drain.argtypes = [_vp, ctypes.c_double]
+_lib.pg_server_cancel.argtypes = [_vp, ctypes.c_uint64]
 _lib.pg_server_get_stats.argtypes = [_vp, _vp]
 _lib.pg_server_free.argtypes = [_vp]
 _lib.pg_server_free.restype = None
@@ -91,6 +92,7 @@ _lib.pg_patterns_size.argtypes = [_vp, ctypes.POINTER(_i64)]
 _lib.pg_patterns_get.argtypes = [_vp, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp, ctypes.POINTER(_i32)]
 _lib.pg_free_patterns.argtypes = [_vp]
 _lib.pg_free_patterns.restype = None
+_lib.pg_fsm_general.argtypes = [_vp, _i32, ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_labeled_motif3.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_count_until.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.POINTER(_i32), _vp]
 _lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
@@ -526,6 +528,28 @@ def fsm(graph: Graph, threshold: int, max_edges: int = 3, stream=None) -> dict:
     return out
 
 
+class FsmGeneralPattern(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.c_int32 * 14),
+                ("labels", ctypes.c_int32 * 8), ("support", ctypes.c_uint64)]
+
+
+def fsm_general(graph: Graph, threshold: int, max_edges: int = 4, stream=None) -> list[dict]:
+    """pg_fsm_general: every frequent labeled pattern with 1..max_edges
+    edges as dicts (k, edges, labels, support), sorted by edge count."""
+    n = _i64()
+    rc = _lib.pg_fsm_general(graph.handle, max_edges, threshold, None, 0, ctypes.byref(n), _stream_ptr(stream))
+    if rc not in (PG_OK, PG_ETRUNC):
+        _check(rc)
+    arr = (FsmGeneralPattern * max(1, n.value))()
+    _check(_lib.pg_fsm_general(graph.handle, max_edges, threshold, arr, n.value, ctypes.byref(n),
+                               _stream_ptr(stream)))
+    out = []
+    for r in arr[:n.value]:
+        out.append(dict(k=int(r.k), edges=[(int(r.edges[2 * i]), int(r.edges[2 * i + 1])) for i in range(r.n_edges)],
+                        labels=[int(r.labels[i]) for i in range(r.k)], support=int(r.support)))
+    return out
+
+
 class LabeledCount(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int32), ("labels", ctypes.c_int32 * 3),
                 ("count_lo", ctypes.c_uint64), ("count_hi", ctypes.c_uint64)]
@@ -598,6 +622,10 @@ class Server:
         return [dict(ticket=int(r.ticket), status=int(r.status), count=_u128(r.count_lo, r.count_hi),
                      t_submit=r.t_submit, t_start=r.t_start, t_done=r.t_done, batch_size=int(r.batch_size))
                 for r in arr[:n.value]]
+
+    def cancel(self, ticket: int):
+        """Withdraw a query (pg_server_cancel); its result reports PG_ECANCELED."""
+        _check(_lib.pg_server_cancel(self._h, ticket))
 
     def drain(self, timeout_s: float = 600.0):
         _check(_lib.pg_server_drain(self._h, timeout_s))

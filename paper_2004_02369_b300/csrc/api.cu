@@ -323,9 +323,9 @@ int pg_plan_upload(pg_plan *pl) {
 
 // ---------------------------------------------------------------- count ----
 
-int pg_run_ctl(pg_graph *g, unsigned long long target, cudaStream_t s, PgRunCtl *out) {
+int pg_run_ctl(pg_graph *g, unsigned long long target, cudaStream_t s, PgRunCtl *out, bool force) {
     *out = PgRunCtl{};
-    if (!target && !g->budget_ns) return PG_OK;
+    if (!target && !g->budget_ns && !force) return PG_OK;
     out->words = g->ex->queues + PG_CTL_WORDS_SLOT;
     out->target = target;
     out->budget_ns = g->budget_ns;
@@ -624,6 +624,12 @@ extern "C" int pg_labeled_motif3(pg_graph *g, pg_labeled_count *out, int64_t cap
                                  void *stream) {
     if (!g || !n_out || (capacity > 0 && !out) || capacity < 0) return pg_set_error(PG_EINVAL, "bad argument");
     return pg_labeled_motif3_run(g, out, capacity, n_out, (cudaStream_t)stream);
+}
+
+extern "C" int pg_fsm_general(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_general_pattern *out,
+                              int64_t capacity, int64_t *n_frequent, void *stream) {
+    if (!g || !n_frequent || (capacity > 0 && !out) || capacity < 0) return pg_set_error(PG_EINVAL, "bad argument");
+    return pg_fsm_general_run(g, max_edges, threshold, out, capacity, n_frequent, (cudaStream_t)stream);
 }
 
 extern "C" int pg_fsm(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_pattern *out, int64_t capacity,

@@ -33,6 +33,8 @@
 //  Both walk the suffixes 32 neighbours a at a time: lanes binary-search
 //  their a's suffix start, a warp prefix sum flattens the 32 suffixes, and
 //  lanes read the flattened increments with coalesced loads.
+#include <mutex>
+
 #include "device_sets.cuh"
 
 namespace {
@@ -259,13 +261,33 @@ __global__ void __launch_bounds__(kDenseBlock) k_c4_dense(C4Args a) {
 
 constexpr size_t kLightSmem = (size_t)kWarps * sizeof(WarpSmem);
 
+// Grids per device, computed once (the shared-memory attribute is a
+// per-device setting): launches then only enqueue work, as stream capture
+// requires.
+constexpr int kMaxDevices = 64;
+std::once_flag g_once[kMaxDevices];
+cudaError_t g_err[kMaxDevices];
+int g_light_per_sm[kMaxDevices], g_dense_per_sm[kMaxDevices];
+
 int c4_grids(const pg_graph *g, int *light, int *dense) {
-    int per_sm = 0;
-    PG_CUDA(cudaFuncSetAttribute(k_c4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLightSmem));
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4_light, kBlock, kLightSmem));
-    *light = std::max(1, per_sm) * g->num_sms;
-    PG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4_dense, kDenseBlock, 0));
-    *dense = std::max(1, per_sm) * g->num_sms;
+    const int dev = g->device;
+    if (dev < 0 || dev >= kMaxDevices) return pg_set_error(PG_EINVAL, "device index out of range");
+    std::call_once(g_once[dev], [dev] {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaError_t e = cudaSetDevice(dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_c4_light, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLightSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_light_per_sm[dev], k_c4_light, kBlock, kLightSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_dense_per_sm[dev], k_c4_dense, kDenseBlock, 0);
+        cudaSetDevice(prev);
+        g_err[dev] = e;
+    });
+    if (g_err[dev] != cudaSuccess) return pg_cuda_error(g_err[dev], "4-cycle kernel set-up");
+    *light = std::max(1, g_light_per_sm[dev]) * g->num_sms;
+    *dense = std::max(1, g_dense_per_sm[dev]) * g->num_sms;
     return PG_OK;
 }
 

@@ -139,7 +139,9 @@ inline PgTaskSel pg_task_sel(const pg_graph *g) {
 
 // Run control of a synchronous call on g: the graph's work budget (if any)
 // and, for existence queries, a target.  Zeroes the control words on s.
-int pg_run_ctl(pg_graph *g, unsigned long long target, cudaStream_t s, PgRunCtl *out);
+// force: control words even without a target or budget (launches that may be
+// stopped from the host)
+int pg_run_ctl(pg_graph *g, unsigned long long target, cudaStream_t s, PgRunCtl *out, bool force = false);
 // PG_ETIMEOUT if the launch behind ctl ran out of budget (synchronises s).
 int pg_run_ctl_check(const PgRunCtl &ctl, cudaStream_t s);
 
@@ -208,6 +210,10 @@ size_t pg_clique_slab_bytes(const pg_graph *g, int kmax);
 // fsm.cu
 int pg_fsm_run(pg_graph *g, int max_edges, unsigned long long threshold, pg_fsm_pattern *out, int64_t capacity,
                int64_t *n_frequent, cudaStream_t s);
+
+// fsm_general.cu
+int pg_fsm_general_run(pg_graph *g, int max_edges, unsigned long long threshold, pg_fsm_general_pattern *out,
+                       int64_t capacity, int64_t *n_frequent, cudaStream_t s);
 
 // labeled_motifs.cu
 int pg_labeled_motif3_run(pg_graph *g, pg_labeled_count *out, int64_t capacity, int64_t *n_out, cudaStream_t s);

@@ -55,6 +55,7 @@ struct Slot {
     double t_start = 0;
     bool busy = false;
     bool dead = false;     // retired after a device error
+    std::vector<uint64_t> cancelled; // cancelled queries of the launch in flight
     PgRunCtl ctl;          // run control of the launch in flight
 };
 
@@ -78,6 +79,9 @@ struct pg_server {
     int device = 0;
     uint64_t next_ticket = 1;
     std::atomic<int64_t> batches{0}, launched_queries{0};
+    std::vector<uint64_t> cancelled;     // tickets to cancel (worker applies them)
+    cudaStream_t ctl_stream = nullptr;   // raises stop words of running launches
+    unsigned long long *d_one = nullptr; // device word holding 1 (source of those copies)
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -154,7 +158,7 @@ int launch_alone(pg_server *S, Slot &s, const ServerQuery &q) {
     int rc = pg_plan_upload(q.plan);
     if (rc == PG_OK && pg_generic_scratch_bytes(&s.view, q.plan, true) > s.ex.scratch_bytes) rc = PG_ENOMEM;
     if (rc == PG_OK && cudaMemsetAsync(s.d_counts, 0, 2 * sizeof(uint64_t), s.stream) != cudaSuccess) rc = PG_EDEVICE;
-    if (rc == PG_OK) rc = pg_run_ctl(&s.view, 0, s.stream, &s.ctl);
+    if (rc == PG_OK) rc = pg_run_ctl(&s.view, 0, s.stream, &s.ctl, true);
     if (rc == PG_OK) {
         s.t_start = S->now();
         rc = pg_launch_generic(&s.view, q.plan, (unsigned long long *)s.d_counts, 0, true, s.stream, &s.ctl);
@@ -198,7 +202,7 @@ int launch_batch(pg_server *S, Slot &s, std::vector<ServerQuery> qs) {
                     return 0;
                 }
                 rc = pg_batch_stage(b, s.d_area, s.h_area, s.area_bytes, s.stream);
-                if (rc == PG_OK) rc = pg_run_ctl(&s.view, 0, s.stream, &s.ctl);
+                if (rc == PG_OK) rc = pg_run_ctl(&s.view, 0, s.stream, &s.ctl, true);
                 if (rc == PG_OK) {
                     s.t_start = S->now();
                     rc = pg_launch_batched(&s.view, b, (unsigned long long *)s.d_counts, 0, s.stream, &s.ctl);
@@ -246,11 +250,45 @@ void fail_pending(pg_server *S, int status) {
     S->outstanding -= (int64_t)qs.size();
 }
 
+// Cancellations: waiting queries leave the queue with PG_ECANCELED; a
+// running launch that holds a cancelled query gets its stop word raised.
+void apply_cancels(pg_server *S) {
+    std::vector<uint64_t> todo;
+    std::deque<ServerQuery> gone;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        todo.swap(S->cancelled);
+        for (uint64_t t : todo)
+            for (auto it = S->pending.begin(); it != S->pending.end(); ++it)
+                if (it->ticket == t) {
+                    gone.push_back(*it);
+                    S->pending.erase(it);
+                    break;
+                }
+    }
+    const double now = S->now();
+    for (auto &q : gone) emit(S, q, PG_ECANCELED, nullptr, now, now, 0);
+    S->outstanding -= (int64_t)gone.size();
+    for (uint64_t t : todo)
+        for (Slot &s : S->slots) {
+            if (!s.busy || !s.ctl.words) continue;
+            bool mine = false;
+            for (auto &q : s.qs) mine |= q.ticket == t;
+            if (!mine) continue;
+            if (s.cancelled.empty())
+                cudaMemcpyAsync(s.ctl.words, S->d_one, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                S->ctl_stream);
+            s.cancelled.push_back(t);
+        }
+    // a ticket found nowhere already has its result: nothing to do
+}
+
 void worker_loop(pg_server *S) {
     cudaSetDevice(S->device);
     const int max_batch = S->cfg.serial ? 1 : std::max(1, std::min(S->cfg.max_batch, (int)PG_MAX_QUEUES));
     while (!S->stop.load()) {
         bool progress = false;
+        apply_cancels(S);
         for (Slot &s : S->slots) {
             if (!s.busy) continue;
             const cudaError_t e = cudaEventQuery(s.done);
@@ -262,6 +300,33 @@ void worker_loop(pg_server *S) {
                 cudaGetLastError();
                 for (auto &q : s.qs) emit(S, q, PG_EDEVICE, nullptr, s.t_start, t, (int)s.qs.size());
                 s.dead = true;
+            } else if (!s.cancelled.empty()) {
+                // the launch was stopped: its cancelled queries end here, the
+                // others go back to the front of the queue
+                std::vector<ServerQuery> again;
+                int64_t ended = 0;
+                for (auto &q : s.qs) {
+                    bool c = false;
+                    for (uint64_t x : s.cancelled) c |= x == q.ticket;
+                    if (c) {
+                        emit(S, q, PG_ECANCELED, nullptr, s.t_start, t, (int)s.qs.size());
+                        ++ended;
+                    } else {
+                        again.push_back(q);
+                    }
+                }
+                {
+                    std::lock_guard<std::mutex> lock(S->mu);
+                    for (size_t i = again.size(); i-- > 0;) S->pending.push_front(again[i]);
+                }
+                S->outstanding -= ended;
+                pg_batch_free(s.batch);
+                s.batch = nullptr;
+                s.qs.clear();
+                s.cancelled.clear();
+                s.busy = false;
+                progress = true;
+                continue;
             } else {
                 const bool timed_out = *(const unsigned long long *)(s.h_counts + 2 * PG_MAX_QUEUES) != 0;
                 for (size_t i = 0; i < s.qs.size(); ++i)
@@ -318,6 +383,20 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
     if (e != cudaSuccess) {
         delete S;
         return pg_cuda_error(e, "cudaGetDevice");
+    }
+    if ((e = cudaStreamCreateWithFlags(&S->ctl_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMalloc(&S->d_one, sizeof(unsigned long long))) != cudaSuccess) {
+        rc = pg_cuda_error(e, "server control stream");
+        pg_server_free(S);
+        return rc;
+    }
+    {
+        const unsigned long long one = 1;
+        if ((e = cudaMemcpy(S->d_one, &one, sizeof(one), cudaMemcpyHostToDevice)) != cudaSuccess) {
+            rc = pg_cuda_error(e, "server control word");
+            pg_server_free(S);
+            return rc;
+        }
     }
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -432,6 +511,19 @@ extern "C" void pg_server_free(pg_server *S) {
         pg_exec_release(&s.ex);
     }
     for (auto &kv : S->plans) pg_free_plan(kv.second);
+    if (S->ctl_stream) {
+        cudaStreamSynchronize(S->ctl_stream);
+        cudaStreamDestroy(S->ctl_stream);
+    }
+    if (S->d_one) cudaFree(S->d_one);
     if (S->g) S->g->servers--;
     delete S;
+}
+
+extern "C" int pg_server_cancel(pg_server *S, uint64_t ticket) {
+    if (!S) return pg_set_error(PG_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (ticket == 0 || ticket >= S->next_ticket) return pg_set_error(PG_EINVAL, "no such ticket");
+    S->cancelled.push_back(ticket);
+    return PG_OK;
 }

@@ -105,3 +105,36 @@ def test_memory_admission(pg, graph):
     got, _ = _serve(pg, G, qs, n_streams=2, max_batch=8, memory_budget=4096)
     assert all(r["status"] == pg.PG_ENOMEM for r in got if r["status"] != 0)
     assert any(r["status"] == pg.PG_ENOMEM for r in got)
+
+
+def test_cancel_waiting_and_running_queries(pg):
+    """A running query (unlabeled 5-cycles on R-MAT 16: far longer than the
+    test allows) is cancelled mid-launch and a waiting one before it starts;
+    both report PG_ECANCELED, and the queries around them come back with
+    their counts alone.  No device fault is involved: the launch sees its
+    stop word and returns."""
+    import time
+    g = sg.workload_graph(5, scale_down=6)
+    G = pg.Graph.from_synth(g)
+    fast = [sg.pattern(3, sg.clique_edges(3)), sg.pattern(3, sg.star_edges(3)), sg.pattern(4, sg.clique_edges(4))]
+    want = [pg.count(G, [pg.Plan.from_dict(q)])[0] for q in fast]
+    srv = pg.Server(G, n_streams=1, max_batch=1)
+    slow = srv.submit(sg.pattern(5, sg.cycle_edges(5)))
+    time.sleep(0.5)
+    waiting = srv.submit(sg.pattern(4, sg.chain_edges(4)))
+    tickets = [srv.submit(q) for q in fast]
+    srv.cancel(waiting)
+    srv.cancel(slow)
+    t = time.perf_counter()
+    srv.drain(120)
+    took = time.perf_counter() - t
+    res = {r["ticket"]: r for r in srv.poll()}
+    srv.close()
+    assert res[slow]["status"] == pg.PG_ECANCELED and res[waiting]["status"] == pg.PG_ECANCELED
+    assert [res[x]["status"] for x in tickets] == [pg.PG_OK] * 3
+    assert [res[x]["count"] for x in tickets] == want
+    assert took < 60
+    srv = pg.Server(G, n_streams=1, memory_budget=1 << 28)
+    with pytest.raises(pg.PgError):
+        srv.cancel(10 ** 9)
+    srv.close()
