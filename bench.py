@@ -225,6 +225,11 @@ def algorithmic_bytes(g, rank: np.ndarray, kmin: int) -> int:
     return 4 * total + 16 * g.n
 
 
+def log(msg: str):
+    """Progress on stderr (the JSON line stays alone on stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def ncu_record(kernel: str):
     """The ncu figures of `kernel` if they were taken on its current source
     (sha256 prefix of the .cu file named in the record), else None."""
@@ -370,6 +375,7 @@ def run_ours(args):
     import paper_2004_02369_b300 as pg
 
     g = sg.workload_graph(2)
+    log("graph generated")
     stream = torch.cuda.current_stream(dev)
     G = pg.Graph.from_synth(g, stream=stream)
     if world > 1:
@@ -390,6 +396,7 @@ def run_ours(args):
     else:
         tune = pg.autotune(G, plans, stream=stream) if args.autotune and args.kernel == 0 else None
 
+    log(f"tuned: {tune['chosen'] if tune else None}")
     clocks = ClockSampler(local)  # running before the timed region starts
     clocks.start()
     for _ in range(args.warmup):
@@ -431,6 +438,7 @@ def run_ours(args):
             print(json.dumps({"only_kernel": True, "ms_per_step": ms_step, "counts": got}), flush=True)
         return 0
 
+    log(f"timed steps: {ms_step:.3f} ms")
     # ---- end to end through the C-ABI with host buffers: pinned CSR ->
     # pg_load_graph (the library's own H2D, validation, degree relabel) ->
     # pg_count (launch, D2H) -> exact sum over ranks
@@ -459,6 +467,7 @@ def run_ours(args):
            "includes": "pg_load_graph from pinned host CSR (H2D, validation, degree relabel), "
                        "launch-parameter copy, pg_count (count, D2H), sum over ranks"}
 
+    log(f"e2e: {e2e['ms_per_step']:.2f} ms")
     # ---- plain one-pattern-per-launch forms on the same GPU --------------
     plain = interp = None
     if args.compare_plain and rank == 0 and world == 1:
@@ -466,7 +475,9 @@ def run_ours(args):
         plain["kernel"] = ("k-clique bitmap kernel without persistence: one warp per start vertex (one CTA per "
                            "heavy start vertex), one launch pair per pattern")
         plain["speedup_of_value"] = plain["ms_per_step"] / ms_step
+        log(f"plain non-persistent: {plain['ms_per_step']:.2f} ms")
         interp = _per_pattern(pg, G, plans, expect, pg.KERNEL_CLIQUE_PLAIN, stream, flush, matches)
+        log(f"interpreter per pattern: {interp['ms_per_step']:.2f} ms")
         interp["kernel"] = ("plan interpreter (sorted-list set operations, 16-byte driver loads), one warp per "
                             "start vertex, one launch per pattern")
         interp["speedup_of_value"] = interp["ms_per_step"] / ms_step
@@ -718,21 +729,33 @@ def _cfg_fsm(pg, dev) -> dict:
                                      {"note": "the call's wall time includes host steps"})}
 
 
-def _cfg_exists(pg, G) -> dict:
+def _cfg_exists(pg, G, budget_ms: float = 30000.0) -> dict:
     """Existence queries with early termination on the 1M-vertex Chung-Lu graph
-    (the paper's 14-clique existence query, and a 6-clique)."""
+    (the paper's 14-clique existence query, and 6- and 10-cliques), each
+    under a device work budget: a query that neither finds a match nor
+    exhausts the search within it is reported as undetermined."""
     import torch
     res = {}
-    for k in (6, 14):
-        plan = pg.Plan(k, sg.clique_edges(k))
-        pg.count_until(G, plan, 1)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        got, reached = pg.count_until(G, plan, 1)
-        res[f"{k}-clique"] = {"exists": reached, "found_before_stop": got,
-                              "ms_to_verdict": (time.perf_counter() - t) * 1e3}
-    return {"workload": "existence_chunglu_n1M_m10M", "results": res,
-            "note": "wall milliseconds of the synchronous pg_count_until (launch, stop flag, D2H)"}
+    pg.set_time_budget(G, budget_ms)
+    try:
+        for k in (6, 10, 14):
+            plan = pg.Plan(k, sg.clique_edges(k))
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            try:
+                got, reached = pg.count_until(G, plan, 1)
+                res[f"{k}-clique"] = {"exists": reached, "found_before_stop": got,
+                                      "ms_to_verdict": (time.perf_counter() - t) * 1e3}
+            except pg.PgError as e:
+                if e.code != pg.PG_ETIMEOUT:
+                    raise
+                res[f"{k}-clique"] = {"exists": None, "undetermined_within_ms": budget_ms}
+            log(f"exists {k}-clique: {res[f'{k}-clique']}")
+    finally:
+        pg.set_time_budget(G, 0)
+    return {"workload": "existence_chunglu_n1M_m10M", "results": res, "budget_ms": budget_ms,
+            "note": "wall milliseconds of the synchronous pg_count_until (launch, stop flag, D2H); "
+                    "cliques run on the k-clique kernel with cardinality pruning"}
 
 
 # --------------------------------------------------------------- other workloads ---
@@ -793,6 +816,15 @@ def run_motif4(args):
             for pl in plans:
                 sep += _events_ms(lambda: pg.count_async(G, [pl], o, kernel=pg.KERNEL_GENERIC), stream)
             row["six_separate_launches_ms"] = sep
+        if args.motif4_terms:
+            # the edge-induced terms the induced motifs expand into, each alone
+            terms = {}
+            o = torch.zeros(2, dtype=torch.int64, device="cuda")
+            for name, edges in sg.MOTIF4_SHAPES.items():
+                tb = pg.Batch([pg.Plan(4, edges)])
+                pg.count_batch(G, tb, o)
+                terms[name] = _events_ms(lambda: pg.count_batch(G, tb, o), stream)
+            row["edge_induced_terms_ms"] = terms
         res[f"rmat_scale{scale}"] = row
     full = res[f"rmat_scale{max(int(x) for x in (args.motif4_scales if not args.motif4_small else [16]))}"]
     line = {"metric": "exact pattern matches/sec", "value": full["matches_per_s"], "unit": "matches/s",
@@ -976,8 +1008,12 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
 
 def run_extra_configs(args, pg, dev, G_cliques) -> dict:
     t = time.perf_counter()
-    out = {"motif3_er2000": _cfg_motif3(pg, dev), "motif4_rmat20": _cfg_motif4(pg, dev, args),
-           "fsm_chunglu500k": _cfg_fsm(pg, dev), "exists_chunglu1M": _cfg_exists(pg, G_cliques)}
+    out = {}
+    for name, fn in (("motif3_er2000", lambda: _cfg_motif3(pg, dev)), ("motif4_rmat20", lambda: _cfg_motif4(pg, dev, args)),
+                     ("fsm_chunglu500k", lambda: _cfg_fsm(pg, dev)), ("exists_chunglu1M", lambda: _cfg_exists(pg, G_cliques))):
+        log(f"config {name} ...")
+        out[name] = fn()
+        log(f"config {name} done")
     if args.serve_n > 0:
         out[f"serving_rmat{args.serve_scale}"] = serving_run(pg, args.serve_scale, args.serve_n, args.serve_lambdas,
                                                              args.serve_timeout)
@@ -1010,6 +1046,7 @@ def main():
                     default="cliques")
     ap.add_argument("--motif4-small", action="store_true", help="skip the full-size motif run")
     ap.add_argument("--motif4-scales", type=int, nargs="+", default=[16, 20], help="R-MAT scales of the motif run")
+    ap.add_argument("--motif4-terms", action="store_true", help="also time each edge-induced 4-vertex term alone")
     ap.add_argument("--no-extra", dest="extra", action="store_false",
                     help="only the k-clique headline (no per-config keys)")
     ap.add_argument("--serve-scale", type=int, default=16, help="R-MAT scale of the serving graph")

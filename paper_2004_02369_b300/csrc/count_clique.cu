@@ -121,6 +121,10 @@ struct Walker {
     int kmin;       // smallest size counted (cardinality pruning)
 };
 
+// Run control of the extended variant, copied to shared memory once per CTA
+// so the traversal can poll it without carrying it in registers.
+__shared__ PgRunCtl s_run_ctl;
+
 // Group-wide barrier: the CTA for heavy vertices, the warp for light ones.
 template <bool CTA>
 __device__ __forceinline__ void group_sync() {
@@ -260,6 +264,11 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
         for (int w = 0; w < nw; ++w) {
             unsigned x = C[w];
             while (x) {
+                if constexpr (XT && P <= 2) {
+                    // long traversals (large k in dense regions) stop soon
+                    // after the launch's stop flag or work budget says so
+                    if (s_run_ctl.words && ctl_stop(s_run_ctl, lane)) return;
+                }
                 const int l = w * 32 + __ffs(x) - 1;
                 x &= x - 1;
                 const unsigned *rl = t.rows + (size_t)l * t.ws;
@@ -424,6 +433,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     wk.m = 0;
     wk.used = 0;
     wk.kmin = a.kmin;
+    if constexpr (XT) {
+        if (threadIdx.x == 0) s_run_ctl = a.ctl;
+        __syncthreads();
+    }
 
     unsigned long long cnt[KMAX];
 #pragma unroll 1

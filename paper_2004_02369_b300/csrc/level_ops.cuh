@@ -137,7 +137,11 @@ static __device__ __noinline__ unsigned long long count_last(const DevGraph &g, 
     }
     if (labeled || ni > 1) ie += (long long)s[drv].len * (ni - 1 + (labeled ? 1 : 0));
     long long total = 0;
-    if (nd == 0 || direct <= ie) {
+    if (ni == 1 && nd == 0 && !labeled) {
+        // a plain bounded slice of one list: its length (the excluded
+        // images inside it are removed below), no pass over its elements
+        total = s[0].len;
+    } else if (nd == 0 || direct <= ie) {
         total = (long long)count_filtered(g, s[drv], s, ni, drv, nd, L.label, lane);
     } else {
         // |A \ (B1 u ... u Bd)| = sum over T subset of diffs of (-1)^|T| |A n B_T|
