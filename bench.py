@@ -928,7 +928,7 @@ def run_fsm(args):
 # --------------------------------------------------------------- serving ---
 
 def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, labeled_only=("C5",),
-                query_timeout_s: float = 0.0) -> dict:
+                query_timeout_s: float = 0.0, alone_only: bool = False) -> dict:
     """Poisson streams of count queries over a resident R-MAT graph (the
     survey's mix, 10% labeled over 8 labels): continuous batching (4
     streams, up to 32 queries per launch) against the same kernels one query
@@ -954,6 +954,9 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
         print(f"[serving {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
     log(f"graph n={g.n} m={g.m}; {len(qs)} queries; per-type alone ms {alone_ms}")
+    if alone_only:
+        return {"workload": f"serving_rmat_scale{scale}_ef16_labels8", "graph": {"n": g.n, "m": g.m},
+                "alone_ms": alone_ms, "mix_mean_alone_ms": float(np.mean([alone_ms[q["name"]] for q in qs]))}
 
     def drive(server, arrivals):
         t0 = time.perf_counter()
@@ -1026,7 +1029,8 @@ def run_serving(args):
     import paper_2004_02369_b300 as pg
     torch.cuda.set_device(0)
     line = serving_run(pg, args.serve_scale, args.serve_n, args.serve_lambdas, args.serve_timeout,
-                       labeled_only=tuple(args.serve_labeled_only), query_timeout_s=args.serve_query_timeout)
+                       labeled_only=tuple(args.serve_labeled_only), query_timeout_s=args.serve_query_timeout,
+                       alone_only=args.serve_alone_only)
     line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
@@ -1054,6 +1058,7 @@ def main():
     ap.add_argument("--serve-labeled-only", nargs="*", default=["C5"],
                     help="query types drawn only in their labeled form")
     ap.add_argument("--serve-query-timeout", type=float, default=0.0, help="server query time limit (s)")
+    ap.add_argument("--serve-alone-only", action="store_true", help="only each query type's time alone")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
     ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")
     ap.add_argument("--tuning-json", default=None,

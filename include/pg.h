@@ -602,6 +602,45 @@ typedef struct {
 int pg_labeled_motif3(pg_graph *g, pg_labeled_count *out, int64_t capacity, int64_t *n_out, void *stream);
 
 /*
+ * pg_labeled_motif4 - labeled 4-motifs with label discovery (Section 6
+ * labeled motifs; Section 3.2.1 label discovery): the number of
+ * vertex-induced matches of every labeled connected 4-vertex pattern present
+ * in the graph.  The labeled 3-motifs present (pg_labeled_motif3) discover the
+ * candidates: a labeled 4-motif is counted only if each of its connected
+ * induced 3-vertex sub-patterns, with its labels, occurs (it cannot occur
+ * otherwise); candidates are counted exactly in fused batches of
+ * vertex-induced labeled plans.
+ *   out    host array of `capacity` records: shape PG_MOTIF4_*, labels of
+ *          pattern vertices 0..3 (the smallest tuple over the shape's
+ *          automorphisms), count as a 128-bit (low, high) pair; only
+ *          nonzero counts, in no particular order.
+ *   n_out  host: number of records (exact even when capacity is short).
+ * Shapes and vertex numbering:
+ *   PG_MOTIF4_PATH     path 0-1-2-3
+ *   PG_MOTIF4_STAR     centre 0, leaves 1, 2, 3
+ *   PG_MOTIF4_CYCLE    0-1-2-3-0
+ *   PG_MOTIF4_TAILED   triangle 0-1-2, tail 3 at 0
+ *   PG_MOTIF4_DIAMOND  cycle 0-1-2-3-0 with chord 1-3
+ *   PG_MOTIF4_CLIQUE   all six pairs
+ * Needs a labeled graph with labels 0..31.  Synchronous; allocates its
+ * tables.  Errors: PG_EINVAL (unlabeled graph), PG_EUNSUPPORTED (a label
+ * above 31), PG_ETRUNC, PG_ENOMEM, PG_EDEVICE.
+ */
+#define PG_MOTIF4_PATH 1
+#define PG_MOTIF4_STAR 2
+#define PG_MOTIF4_CYCLE 3
+#define PG_MOTIF4_TAILED 4
+#define PG_MOTIF4_DIAMOND 5
+#define PG_MOTIF4_CLIQUE 6
+typedef struct {
+    int32_t shape;
+    int32_t labels[4];
+    int32_t pad;
+    uint64_t count_lo, count_hi;
+} pg_labeled_count4;
+int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int64_t *n_out, void *stream);
+
+/*
  * Serving: a request loop over a resident graph.  Queries are submitted at
  * any time from any host thread; a worker thread admits waiting queries into
  * batches whenever one of n_streams streams is free and the batch's scratch

@@ -92,6 +92,7 @@ _lib.pg_patterns_size.argtypes = [_vp, ctypes.POINTER(_i64)]
 _lib.pg_patterns_get.argtypes = [_vp, _i64, ctypes.POINTER(_i32), ctypes.POINTER(_i32), _vp, ctypes.POINTER(_i32)]
 _lib.pg_free_patterns.argtypes = [_vp]
 _lib.pg_free_patterns.restype = None
+_lib.pg_labeled_motif4.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_fsm_general.argtypes = [_vp, _i32, ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_labeled_motif3.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_count_until.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.POINTER(_i32), _vp]
@@ -531,6 +532,27 @@ def fsm(graph: Graph, threshold: int, max_edges: int = 3, stream=None) -> dict:
 class FsmGeneralPattern(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("n_edges", ctypes.c_int32), ("edges", ctypes.c_int32 * 14),
                 ("labels", ctypes.c_int32 * 8), ("support", ctypes.c_uint64)]
+
+
+class LabeledCount4(ctypes.Structure):
+    _fields_ = [("shape", ctypes.c_int32), ("labels", ctypes.c_int32 * 4), ("pad", ctypes.c_int32),
+                ("count_lo", ctypes.c_uint64), ("count_hi", ctypes.c_uint64)]
+
+
+MOTIF4_SHAPE_NAMES = {1: "path", 2: "star", 3: "cycle", 4: "tailed_triangle", 5: "diamond", 6: "clique"}
+
+
+def labeled_motif4(graph: Graph, stream=None) -> dict:
+    """pg_labeled_motif4: {(shape name, (l0, l1, l2, l3)): vertex-induced count}
+    for every labeled connected 4-vertex pattern present."""
+    n = _i64()
+    rc = _lib.pg_labeled_motif4(graph.handle, None, 0, ctypes.byref(n), _stream_ptr(stream))
+    if rc not in (PG_OK, PG_ETRUNC):
+        _check(rc)
+    arr = (LabeledCount4 * max(1, n.value))()
+    _check(_lib.pg_labeled_motif4(graph.handle, arr, n.value, ctypes.byref(n), _stream_ptr(stream)))
+    return {(MOTIF4_SHAPE_NAMES[r.shape], tuple(int(x) for x in r.labels)): _u128(r.count_lo, r.count_hi)
+            for r in arr[:n.value]}
 
 
 def fsm_general(graph: Graph, threshold: int, max_edges: int = 4, stream=None) -> list[dict]:

@@ -626,6 +626,12 @@ extern "C" int pg_labeled_motif3(pg_graph *g, pg_labeled_count *out, int64_t cap
     return pg_labeled_motif3_run(g, out, capacity, n_out, (cudaStream_t)stream);
 }
 
+extern "C" int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int64_t *n_out,
+                                 void *stream) {
+    if (!g || !n_out || (capacity > 0 && !out) || capacity < 0) return pg_set_error(PG_EINVAL, "bad argument");
+    return pg_labeled_motif4_run(g, out, capacity, n_out, (cudaStream_t)stream);
+}
+
 extern "C" int pg_fsm_general(pg_graph *g, int32_t max_edges, uint64_t threshold, pg_fsm_general_pattern *out,
                               int64_t capacity, int64_t *n_frequent, void *stream) {
     if (!g || !n_frequent || (capacity > 0 && !out) || capacity < 0) return pg_set_error(PG_EINVAL, "bad argument");

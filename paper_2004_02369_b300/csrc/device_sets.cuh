@@ -116,6 +116,33 @@ __device__ __forceinline__ void in_slice4(const DevGraph &g, const Slice &s, con
     for (int j = 0; j < 4; ++j) ok[j] = ok[j] && (f[j] != negate);
 }
 
+// Four lower bounds at once: pos[j] = first index i of a[0, len) with
+// a[i] >= x[j] (len for none).  Branch-free searches over the same length,
+// so each step issues four independent loads.  RO: read-only path (lists);
+// else coherent loads (scratch written earlier by this warp).  Every load
+// stays inside a[0, len).
+template <bool RO>
+__device__ __forceinline__ void lower_bound4(const int *a, int len, const int (&x)[4], int (&pos)[4]) {
+    if (len <= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pos[j] = 0;
+        return;
+    }
+    int b[4] = {0, 0, 0, 0};
+    int n = len;
+    while (n > 1) {
+        const int half = n >> 1;
+        int v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = RO ? __ldg(a + b[j] + half - 1) : a[b[j] + half - 1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] += v[j] < x[j] ? half : 0;
+        n -= half;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) pos[j] = b[j] + ((RO ? __ldg(a + b[j]) : a[b[j]]) < x[j] ? 1 : 0);
+}
+
 // The driver slice d of a level, read four elements per lane with one
 // aligned 16-byte load: lists start 16-byte aligned and are padded to 4
 // entries, so the groups covering d stay inside its list.  Group g of a

@@ -306,29 +306,53 @@ static __device__ __noinline__ unsigned long long count_joint(const DevGraph &g,
     } else {
         qs = Slice{bufB, fill_level(g, Q, m, bufB, lane), -1};
     }
-    // side: count Q elements greater than e, or smaller than e
+    // side: count Q elements greater than e, or smaller than e.  Lanes take
+    // four elements of I per step (one 16-byte load; a list slice may start
+    // mid-group, a scratch set starts aligned) and run four searches at once.
     const bool greater = (iterX && rel > 0) || (!iterX && rel < 0);
+    const int off = islice ? (int)(((uintptr_t)is.p >> 2) & 3u) : 0;
+    const int4 *v4 = (const int4 *)(is.p - off);
+    const int total = is.len + off;
     unsigned long long acc = 0;
-    for (int base = 0; base < is.len; base += 32) {
-        const int idx = base + lane;
-        if (idx < is.len) {
-            const int e = islice ? __ldg(is.p + idx) : is.p[idx];
-            bool skip = false;
-            if (islice)
-                for (int i = 0; i < I.n_excl; ++i) skip |= e == m[I.excl_src[i]];
-            if (!skip) {
-                if (rel == 0) {
-                    bool in = qslice ? contains_g(qs.p, qs.len, e) : contains_s(qs.p, qs.len, e);
-                    for (int i = 0; i < nqx; ++i) in &= e != qx[i];
-                    acc += in ? 1 : 0;
-                } else {
-                    // elements < e
-                    const int pos = qslice ? lower_bound_g(qs.p, qs.len, e) : lower_bound_s(qs.p, qs.len, e);
-                    const bool has = pos < qs.len && (qslice ? __ldg(qs.p + pos) : qs.p[pos]) == e;
-                    long long c = greater ? (long long)(qs.len - pos - (has ? 1 : 0)) : (long long)pos;
-                    for (int i = 0; i < nqx; ++i) c -= greater ? (qx[i] > e) : (qx[i] < e);
-                    acc += (unsigned long long)c;
-                }
+    for (int base = 0; base < total; base += 128) {
+        const int q = base + 4 * lane;
+        int4 t = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff);
+        if (q < total) t = islice ? __ldg(v4 + (q >> 2)) : v4[q >> 2];
+        const int e[4] = {t.x, t.y, t.z, t.w};
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ok[j] = q + j >= off && q + j < total;
+        if (islice)
+            for (int i = 0; i < I.n_excl; ++i) {
+                const int x = m[I.excl_src[i]];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) ok[j] = ok[j] && e[j] != x;
+            }
+        if (rel == 0) {
+            bool in[4] = {ok[0], ok[1], ok[2], ok[3]};
+            if (qslice) {
+                in_slice4(g, qs, e, in, false);
+            } else {
+                int pos[4];
+                lower_bound4<false>(qs.p, qs.len, e, pos);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) in[j] = in[j] && pos[j] < qs.len && qs.p[pos[j]] == e[j];
+            }
+            for (int i = 0; i < nqx; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) in[j] = in[j] && e[j] != qx[i];
+            acc += (unsigned)in[0] + (unsigned)in[1] + (unsigned)in[2] + (unsigned)in[3];
+        } else {
+            int pos[4];
+            if (qslice) lower_bound4<true>(qs.p, qs.len, e, pos);
+            else lower_bound4<false>(qs.p, qs.len, e, pos);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!ok[j]) continue;
+                const bool has = pos[j] < qs.len && (qslice ? __ldg(qs.p + pos[j]) : qs.p[pos[j]]) == e[j];
+                long long c = greater ? (long long)(qs.len - pos[j] - (has ? 1 : 0)) : (long long)pos[j];
+                for (int i = 0; i < nqx; ++i) c -= greater ? (qx[i] > e[j]) : (qx[i] < e[j]);
+                acc += (unsigned long long)c;
             }
         }
     }

@@ -217,6 +217,8 @@ int pg_fsm_general_run(pg_graph *g, int max_edges, unsigned long long threshold,
 
 // labeled_motifs.cu
 int pg_labeled_motif3_run(pg_graph *g, pg_labeled_count *out, int64_t capacity, int64_t *n_out, cudaStream_t s);
+// labeled_motifs4.cpp
+int pg_labeled_motif4_run(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int64_t *n_out, cudaStream_t s);
 
 // count_batched.cu: many plans, one launch over a shared prefix tree
 int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out);

@@ -74,3 +74,29 @@ def test_labeled_motif3_errors(pg):
     with pytest.raises(pg.PgError) as e:
         pg.labeled_motif3(pg.Graph.from_synth(g))
     assert e.value.code == pg.PG_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("case", range(2))
+def test_labeled_motif4_discovery(pg, case):
+    """Labeled 4-motifs with label discovery: every labeling of every shape is
+    checked against the oracle's vertex-induced labeled count (absent =
+    zero), and per shape the labeled counts sum to the unlabeled induced
+    count of the motif linear system."""
+    import itertools
+    g = [sg.erdos_renyi(120, 0.08, 1401), sg.chung_lu(300, 1200, 2.1, 40.0, 1402)][case]
+    nl = 3
+    g.labels = sg.uniform_labels(g.n, nl, 1410 + case)
+    G = pg.Graph.from_synth(g)
+    got = pg.labeled_motif4(G)
+    assert all(v > 0 for v in got.values())
+    ind = oracle.motif4_induced(g)
+    for shape, edges in sg.MOTIF4_SHAPES.items():
+        assert sum(v for (sh, _), v in got.items() if sh == shape) == ind[shape], shape
+        seen = set()
+        for lab in itertools.product(range(nl), repeat=4):
+            want = oracle.count(g, sg.pattern(4, edges, labels=list(lab), vertex_induced=True))
+            key = (shape, lab)
+            if key in got:
+                assert got[key] == want, key
+                seen.add(key)
+        assert seen == {k for k in got if k[0] == shape}
