@@ -156,10 +156,9 @@ __global__ void __launch_bounds__(W * 32, CAP == 1 ? 32 / W : CAP == 2 ? 20 / W 
                         continue;
                     }
                 }
-                if (l == 1 && ch[l] == 0 && polled && ctl_stop(a.ctl, lane)) {
-                    l = 0;
-                    break;
-                }
+                // poll at each new candidate of the first three levels, so a
+                // stop or a spent budget ends even a hub's long task soon
+                if (polled && ch[l] == 0 && l >= 1 && l <= 3 && ctl_stop(a.ctl, lane)) break;
                 if (l > 0) m[l] = wbuf[a.lvl_off[l] + ci[l]];
                 const int child = N.first_child + ch[l];
                 const PgTrieNode &C = a.nodes[child];

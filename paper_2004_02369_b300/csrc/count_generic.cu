@@ -76,7 +76,7 @@ __device__ unsigned __int128 run_task(const GenericArgs &a, int v, const PgOrder
         // advance to the next unexplored candidate
         while (l >= 1 && (l == L - 1 || idx[l] >= sz[l])) --l;
         if (l < 1) break;
-        if (l == 1 && a.ctl.words && ctl_stop(a.ctl, lane)) break;
+        if (l <= 3 && a.ctl.words && ctl_stop(a.ctl, lane)) break;
         m[l] = wbuf[a.lvl_off[l] + idx[l]];
         ++idx[l];
         ++l;

@@ -237,6 +237,26 @@ static __device__ __noinline__ int filter_anti(const DevGraph &g, const PgOrder 
     return kept;
 }
 
+// x lies in the candidate set of level spec L (bounds, lists, differences,
+// label, excluded images): one lane's test.
+__device__ __forceinline__ bool in_level_set(const DevGraph &g, const PgLevel &L, const int *m, int x) {
+    const LevelRange r = level_range(L, m);
+    if (!(x > r.lo && x < r.hi)) return false;
+    for (int i = 0; i < L.n_excl; ++i)
+        if (x == m[L.excl_src[i]]) return false;
+    for (int i = 0; i < L.n_int; ++i) {
+        const int w = m[L.int_src[i]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        if (!in_slice(g, Slice{adj_of(g, vi), vi.y, w}, x)) return false;
+    }
+    for (int i = 0; i < L.n_diff; ++i) {
+        const int w = m[L.diff_src[i]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        if (in_slice(g, Slice{adj_of(g, vi), vi.y, w}, x)) return false;
+    }
+    return L.label < 0 || __ldg(&g.vinfo[x].w) == L.label;
+}
+
 // A set given by a level spec is a plain bounded slice of one adjacency list
 // (minus excluded images) when it has one intersected list, no differences
 // and no label: its elements and ranks are read off the list directly.
@@ -283,6 +303,23 @@ static __device__ __noinline__ unsigned long long count_joint(const DevGraph &g,
     const unsigned long long nY = count_last(g, Yp, m, lane);
     if (nY == 0) return 0;
     if (rel == 0 && !excl_xy) return nX * nY;
+    if (rel == 0) {
+        // one set inside the other's list: when A is a plain unbounded slice
+        // of adj(w) and B intersects adj(w) too, B lies in adj(w), so
+        // |A n B| = |B| minus A's excluded images that lie in B
+        auto sub = [&](const PgLevel &A, const PgLevel &B, unsigned long long nB, unsigned long long *inter) {
+            if (!(is_slice(A) && A.n_lo == 0 && A.n_hi == 0)) return false;
+            bool in_b = false;
+            for (int i = 0; i < B.n_int; ++i) in_b |= B.int_src[i] == A.int_src[0];
+            if (!in_b) return false;
+            bool hit = false;
+            if (lane < A.n_excl) hit = in_level_set(g, B, m, m[A.excl_src[lane]]);
+            *inter = nB - (unsigned long long)__popc(__ballot_sync(PG_FULL, hit));
+            return true;
+        };
+        unsigned long long inter;
+        if (sub(X, Yp, nY, &inter) || sub(Yp, X, nX, &inter)) return nX * nY - inter;
+    }
     const bool iterX = nX <= nY;
     const PgLevel &I = iterX ? X : Yp;
     const PgLevel &Q = iterX ? Yp : X;

@@ -82,7 +82,7 @@ __device__ void list_task(const MatchArgs &a, int v, const PgOrder &ord, int *wb
         if (l == L - 1) emit(a, ord, l, m, buf, sz[l], lane);
         while (l >= 1 && (l == L - 1 || idx[l] >= sz[l])) --l;
         if (l < 1) break;
-        if (l == 1 && a.ctl.words && ctl_stop(a.ctl, lane)) break;
+        if (l <= 3 && a.ctl.words && ctl_stop(a.ctl, lane)) break;
         m[l] = wbuf[a.lvl_off[l] + idx[l]];
         ++idx[l];
         ++l;

@@ -390,15 +390,40 @@ int pg_plan_compile(const PgPattern &in, bool vertex_induced, PgPlanHost &out, s
         std::sort(codes.begin(), codes.end());
         out.aut = (uint64_t)(std::unique(codes.begin(), codes.end()) - codes.begin());
     }
+    // Which symmetric vertex to order first is free (Grochow-Kellis; any
+    // choice gives the same count).  Ordering a vertex that every minimum
+    // connected vertex cover contains puts the order on core vertices, where
+    // it halves the enumerated core matches, and leaves the non-core
+    // vertices unordered, where their completion needs only membership tests
+    // (e.g. the path 0-1-2-3 orders 1 < 2 instead of 0 < 3).
+    uint32_t in_every_cover = reg;
+    {
+        int min_size = 0;
+        for (int size = 1; size <= popcount(reg) && !min_size; ++size)
+            for (uint32_t mask = 1; mask < (1u << k); ++mask) {
+                if ((mask & ~reg) || popcount(mask) != size) continue;
+                bool covers = true;
+                for (int u = 0; u < k && covers; ++u)
+                    for (int w = u + 1; w < k && covers; ++w)
+                        if ((reg >> u & 1) && (reg >> w & 1) && p.rel[u][w] && !(mask >> u & 1) && !(mask >> w & 1))
+                            covers = false;
+                if (!covers || !connected_by_edges(p, mask)) continue;
+                min_size = size;
+                in_every_cover &= mask;
+            }
+        if (popcount(reg) == 1) in_every_cover = reg;
+    }
     for (;;) {
         int v = -1;
         uint32_t orbit = 0;
-        for (int u = 0; u < k && v < 0; ++u) {
-            if (!(reg >> u & 1)) continue;
-            uint32_t o = 0;
-            for (auto &s : group) o |= 1u << s[u];
-            if (popcount(o) > 1) { v = u; orbit = o; }
-        }
+        for (int pass = 0; pass < 2 && v < 0; ++pass)
+            for (int u = 0; u < k && v < 0; ++u) {
+                if (!(reg >> u & 1)) continue;
+                if (pass == 0 && !(in_every_cover >> u & 1)) continue;
+                uint32_t o = 0;
+                for (auto &s : group) o |= 1u << s[u];
+                if (popcount(o) > 1) { v = u; orbit = o; }
+            }
         if (v < 0) break;
         for (int w = 0; w < k; ++w)
             if (w != v && (orbit >> w & 1)) out.po.push_back({v, w});
