@@ -928,7 +928,8 @@ def run_fsm(args):
 # --------------------------------------------------------------- serving ---
 
 def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, labeled_only=("C5",),
-                query_timeout_s: float = 0.0, alone_only: bool = False) -> dict:
+                query_timeout_s: float = 0.0, alone_only: bool = False, alone_budget_ms: float = 0.0,
+                types=None) -> dict:
     """Poisson streams of count queries over a resident R-MAT graph (the
     survey's mix, 10% labeled over 8 labels): continuous batching (4
     streams, up to 32 queries per launch) against the same kernels one query
@@ -937,26 +938,38 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
     dev = torch.device("cuda", torch.cuda.current_device())
     g = sg.workload_graph(5, scale_down=22 - scale)
     G = pg.Graph.from_synth(g)
-    qs = sg.serving_queries(n_queries, seed=sg.SEED_BASE + 55, labeled_only=labeled_only)
+    qs = sg.serving_queries(n_queries, seed=sg.SEED_BASE + 55, labeled_only=labeled_only, types=types)
     types = sorted({q["name"] for q in qs})
-
-    # per-type service time alone (first call compiles / sizes scratch)
-    alone_ms = {}
-    for name in types:
-        q = next(x for x in qs if x["name"] == name)
-        plan = pg.Plan.from_dict(q)
-        pg.count(G, [plan])
-        t = time.perf_counter()
-        pg.count(G, [plan])
-        alone_ms[name] = (time.perf_counter() - t) * 1e3
 
     def log(msg):
         print(f"[serving {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
+    # per-type service time alone (first call compiles / sizes scratch);
+    # with alone_budget_ms a type that runs longer is reported as over it
+    alone_ms = {}
+    if alone_budget_ms:
+        pg.set_time_budget(G, alone_budget_ms)
+    for name in types:
+        q = next(x for x in qs if x["name"] == name)
+        plan = pg.Plan.from_dict(q)
+        try:
+            pg.count(G, [plan])
+            t = time.perf_counter()
+            pg.count(G, [plan])
+            alone_ms[name] = (time.perf_counter() - t) * 1e3
+        except pg.PgError as e:
+            if e.code != pg.PG_ETIMEOUT:
+                raise
+            alone_ms[name] = f"> {alone_budget_ms:.0f}"
+        log(f"alone {name}: {alone_ms[name]}")
+    pg.set_time_budget(G, 0)
+
     log(f"graph n={g.n} m={g.m}; {len(qs)} queries; per-type alone ms {alone_ms}")
     if alone_only:
+        done = [alone_ms[q["name"]] for q in qs if not isinstance(alone_ms[q["name"]], str)]
         return {"workload": f"serving_rmat_scale{scale}_ef16_labels8", "graph": {"n": g.n, "m": g.m},
-                "alone_ms": alone_ms, "mix_mean_alone_ms": float(np.mean([alone_ms[q["name"]] for q in qs]))}
+                "alone_ms": alone_ms, "alone_budget_ms": alone_budget_ms,
+                "mix_mean_alone_ms_of_measured": float(np.mean(done)) if done else None}
 
     def drive(server, arrivals):
         t0 = time.perf_counter()
@@ -1030,7 +1043,8 @@ def run_serving(args):
     torch.cuda.set_device(0)
     line = serving_run(pg, args.serve_scale, args.serve_n, args.serve_lambdas, args.serve_timeout,
                        labeled_only=tuple(args.serve_labeled_only), query_timeout_s=args.serve_query_timeout,
-                       alone_only=args.serve_alone_only)
+                       alone_only=args.serve_alone_only, alone_budget_ms=args.serve_alone_budget_ms,
+                       types=args.serve_types)
     line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
@@ -1059,6 +1073,9 @@ def main():
                     help="query types drawn only in their labeled form")
     ap.add_argument("--serve-query-timeout", type=float, default=0.0, help="server query time limit (s)")
     ap.add_argument("--serve-alone-only", action="store_true", help="only each query type's time alone")
+    ap.add_argument("--serve-alone-budget-ms", type=float, default=0.0,
+                    help="device work budget of each alone measurement (0: none)")
+    ap.add_argument("--serve-types", nargs="*", default=None, help="query types of the mix (default: all)")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
     ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")
     ap.add_argument("--tuning-json", default=None,

@@ -28,8 +28,12 @@
 //    increments, is appended to a deferred list instead;
 //  * dense pass (16-warp CTAs, no shared tables, so more resident warps to
 //    cover the atomics' latency): deferred anchors one per CTA; the counters
-//    are a dense n-entry array per CTA in global memory, incremented with
-//    atomicAdd and cleared by a second walk over the same suffixes.
+//    are a dense n-entry array per CTA in global memory.  Each entry holds a
+//    12-bit anchor epoch and a 20-bit count; an increment from a newer epoch
+//    restarts the count (compare-and-swap), so no pass clears the counters
+//    between anchors (the array is cleared once when a CTA's epochs wrap).
+//    Graphs with a vertex of degree 2^20 or more use plain atomicAdd counters
+//    cleared by a second walk.
 //  Both walk the suffixes 32 neighbours a at a time: lanes binary-search
 //  their a's suffix start, a warp prefix sum flattens the 32 suffixes, and
 //  lanes read the flattened increments with coalesced loads.
@@ -50,6 +54,7 @@ constexpr int kEmpty = -1;
 struct C4Args {
     DevGraph g;
     int n;
+    int epochs;             // 1: epoch-tagged dense counters (all degrees below 2^20)
     unsigned *dense;        // per-CTA counter arrays of n entries, all zero between anchors
     int *deferred;          // anchors left to the CTAs
     unsigned long long *q;  // [0] warp cursor, [1] deferred count, [2] deferred cursor
@@ -112,9 +117,22 @@ __device__ __forceinline__ void walk_chunk(const DevGraph &g, unsigned my_start,
     }
 }
 
-// Heavy anchor w by the whole CTA on the dense counters C.  Returns this
-// thread's share of the anchored count.
-__device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, int *s_next, int *s_p) {
+// Counter x of the current epoch ep (1..4095): raise it, return its count
+// before (0 when it held an older epoch).
+__device__ __forceinline__ unsigned epoch_inc(unsigned *c, unsigned ep) {
+    unsigned cur = *(volatile unsigned *)c;
+    for (;;) {
+        const bool mine = (cur >> 20) == ep;
+        const unsigned nv = mine ? cur + 1u : (ep << 20) | 1u;
+        const unsigned prev = atomicCAS(c, cur, nv);
+        if (prev == cur) return mine ? (cur & 0xFFFFFu) : 0u;
+        cur = prev; // another increment got there first: retry on its value
+    }
+}
+
+// Heavy anchor w by the whole CTA on the dense counters C (epoch ep when
+// a.epochs).  Returns this thread's share of the anchored count.
+__device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, int *s_next, int *s_p, unsigned ep) {
     const DevGraph &g = a.g;
     const int lane = threadIdx.x & 31;
     const int4 wi = __ldg(&g.vinfo[w]);
@@ -126,7 +144,8 @@ __device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, 
     __syncthreads();
     const int p = *s_p, na = wi.y - p;
     unsigned long long cnt = 0;
-    for (int pass = 0; pass < 2; ++pass) {
+    const int passes = a.epochs ? 1 : 2;
+    for (int pass = 0; pass < passes; ++pass) {
         for (;;) {
             int c = 0;
             if (lane == 0) c = atomicAdd(s_next, 32);
@@ -135,7 +154,9 @@ __device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, 
             unsigned st = 0;
             int ln = 0;
             if (c + lane < na) suffix_of(g, __ldg(aw + p + c + lane), w, &st, &ln);
-            if (pass == 0)
+            if (a.epochs)
+                walk_chunk(g, st, ln, lane, [&](int x) { cnt += epoch_inc(C + x, ep); });
+            else if (pass == 0)
                 walk_chunk(g, st, ln, lane, [&](int x) { cnt += atomicAdd(C + x, 1u); });
             else
                 walk_chunk(g, st, ln, lane, [&](int x) { C[x] = 0u; });
@@ -240,6 +261,7 @@ __global__ void __launch_bounds__(kDenseBlock) k_c4_dense(C4Args a) {
     unsigned long long cnt = 0;
     unsigned *C = a.dense + (size_t)blockIdx.x * (size_t)a.n;
     const unsigned long long n_def = *(volatile unsigned long long *)(a.q + 1);
+    unsigned ep = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             int w = -1;
@@ -253,7 +275,13 @@ __global__ void __launch_bounds__(kDenseBlock) k_c4_dense(C4Args a) {
         const int w = s_task;
         __syncthreads();
         if (w < 0) break;
-        cnt += dense_anchor(a, w, C, &s_next, &s_p);
+        if (a.epochs && ++ep == 4096) {
+            // epochs wrap: clear this CTA's counters once
+            for (int i = threadIdx.x; i < a.n; i += blockDim.x) C[i] = 0u;
+            __syncthreads();
+            ep = 1;
+        }
+        cnt += dense_anchor(a, w, C, &s_next, &s_p, ep);
     }
     const unsigned __int128 tot = warp_sum_u128(cnt);
     if (lane == 0 && tot) atomic_add_u128(a.count, tot);
@@ -314,6 +342,7 @@ int pg_launch_c4(pg_graph *g, unsigned long long *count_dev, int queue_slot, cud
     C4Args a;
     a.g = g->d;
     a.n = (int)g->n;
+    a.epochs = g->max_deg < (1ll << 20) ? 1 : 0;
     a.dense = (unsigned *)g->ex->scratch;
     a.deferred = (int *)((unsigned char *)g->ex->scratch + dense_bytes);
     a.q = g->ex->queues + queue_slot;

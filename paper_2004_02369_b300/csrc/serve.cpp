@@ -81,7 +81,9 @@ struct pg_server {
     std::atomic<int64_t> batches{0}, launched_queries{0};
     std::vector<uint64_t> cancelled;     // tickets to cancel (worker applies them)
     cudaStream_t ctl_stream = nullptr;   // raises stop words of running launches
-    unsigned long long *d_one = nullptr; // device word holding 1 (source of those copies)
+    unsigned long long *h_one = nullptr; // pinned host word holding 1: the source of those
+                                         // copies (host-to-device, done by a copy engine
+                                         // while the running kernel holds every SM)
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -276,7 +278,7 @@ void apply_cancels(pg_server *S) {
             for (auto &q : s.qs) mine |= q.ticket == t;
             if (!mine) continue;
             if (s.cancelled.empty())
-                cudaMemcpyAsync(s.ctl.words, S->d_one, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                cudaMemcpyAsync(s.ctl.words, S->h_one, sizeof(unsigned long long), cudaMemcpyHostToDevice,
                                 S->ctl_stream);
             s.cancelled.push_back(t);
         }
@@ -385,19 +387,12 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
         return pg_cuda_error(e, "cudaGetDevice");
     }
     if ((e = cudaStreamCreateWithFlags(&S->ctl_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaMalloc(&S->d_one, sizeof(unsigned long long))) != cudaSuccess) {
+        (e = cudaMallocHost(&S->h_one, sizeof(unsigned long long))) != cudaSuccess) {
         rc = pg_cuda_error(e, "server control stream");
         pg_server_free(S);
         return rc;
     }
-    {
-        const unsigned long long one = 1;
-        if ((e = cudaMemcpy(S->d_one, &one, sizeof(one), cudaMemcpyHostToDevice)) != cudaSuccess) {
-            rc = pg_cuda_error(e, "server control word");
-            pg_server_free(S);
-            return rc;
-        }
-    }
+    *S->h_one = 1;
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     size_t budget = cfg->memory_budget > 0 ? (size_t)cfg->memory_budget : std::min<size_t>(free_b / 5 * 2, 64ull << 30);
@@ -515,7 +510,7 @@ extern "C" void pg_server_free(pg_server *S) {
         cudaStreamSynchronize(S->ctl_stream);
         cudaStreamDestroy(S->ctl_stream);
     }
-    if (S->d_one) cudaFree(S->d_one);
+    if (S->h_one) cudaFreeHost(S->h_one);
     if (S->g) S->g->servers--;
     delete S;
 }
