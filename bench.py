@@ -971,15 +971,19 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
                 "alone_ms": alone_ms, "alone_budget_ms": alone_budget_ms,
                 "mix_mean_alone_ms_of_measured": float(np.mean(done)) if done else None}
 
-    def drive(server, arrivals):
+    def drive(server, arrivals, closed=False):
+        # closed: each query is submitted when the previous one is done
         t0 = time.perf_counter()
-        tickets = []
+        tickets, res = [], {}
         for q, a in zip(qs, arrivals):
             while time.perf_counter() - t0 < a:
                 time.sleep(min(2e-4, max(0.0, a - (time.perf_counter() - t0))))
             tickets.append(server.submit(q))
+            if closed:
+                server.drain(timeout_s)
+                res.update({r["ticket"]: r for r in server.poll(10)})
         server.drain(timeout_s)
-        res = {r["ticket"]: r for r in server.poll(len(qs) + 10)}
+        res.update({r["ticket"]: r for r in server.poll(len(qs) + 10)})
         out = [res[t] for t in tickets]
         lat = np.array([r["t_done"] - r["t_submit"] for r in out]) * 1e3
         span = max(r["t_done"] for r in out) - min(r["t_submit"] for r in out)
@@ -988,15 +992,17 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
                      "batches": server.stats()["batches"],
                      "timed_out": sum(1 for r in out if r["status"] == pg.PG_ETIMEOUT)}
 
-    # serial capacity: closed loop, everything submitted at t = 0
-    srv = pg.Server(G, serial=True)
-    base, cal = drive(srv, np.zeros(len(qs)))
+    # serial capacity: closed loop, one query at a time (so that a query time
+    # limit counts only the query's own run)
+    srv = pg.Server(G, serial=True, query_timeout_s=query_timeout_s)
+    base, cal = drive(srv, np.zeros(len(qs)), closed=True)
     srv.close()
     capacity = cal["queries_per_s"]
     log(f"serial capacity {capacity:.1f} queries/s ({cal})")
-    want = [r["count"] for r in base]
-    if any(r["status"] != pg.PG_OK for r in base):
+    ok_status = (pg.PG_OK, pg.PG_ETIMEOUT) if query_timeout_s > 0 else (pg.PG_OK,)
+    if any(r["status"] not in ok_status for r in base):
         raise SystemExit("a serving query failed when run one at a time")
+    want = [r["count"] if r["status"] == pg.PG_OK else None for r in base]
     runs = []
     for f in lambdas:
         arrivals = sg.poisson_arrivals(len(qs), f * capacity, seed=sg.SEED_BASE + int(100 * f))
@@ -1007,8 +1013,9 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
             srv.close()
             log(f"lambda {f} {mode}: {st}")
             got = [r["count"] if r["status"] == pg.PG_OK else None for r in out]
-            if any(x is not None and x != w for x, w in zip(got, want)):
+            if any(x is not None and w is not None and x != w for x, w in zip(got, want)):
                 raise SystemExit(f"serving counts differ from one-at-a-time ({mode}, lambda {f})")
+            st["compared_with_alone"] = sum(1 for x, w in zip(got, want) if x is not None and w is not None)
             row[mode] = st
         runs.append(row)
     return {"workload": f"serving_rmat_scale{scale}_ef16_labels8",

@@ -673,8 +673,12 @@ typedef struct {
     double query_timeout_s; /* > 0: a query not done this long after its
                                submission fails with PG_ETIMEOUT (enforced as
                                the device work budget of its launch, see
-                               pg_set_time_budget; every query of that launch
-                               gets PG_ETIMEOUT); 0: no limit */
+                               pg_set_time_budget: a single query gets its
+                               time left, a batch half the least time left
+                               among its queries; when a batch runs out, its
+                               queries are launched again one by one with
+                               their own time left, so only the slow one
+                               fails); 0: no limit */
 } pg_server_config;
 
 typedef struct {

@@ -14,8 +14,12 @@
 //
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
-// the kernels stop when it runs out and every query of that launch gets
-// PG_ETIMEOUT, so one slow pattern cannot hold a stream indefinitely.  A
+// the kernels stop when it runs out, so one slow pattern cannot hold a
+// stream indefinitely.  A single query that runs out gets PG_ETIMEOUT.  A
+// batch gets half the least time left among its queries; if it runs out,
+// its queries (it is not known which one was slow) go back to the front of
+// the queue to be launched one by one with the time they have left, which
+// isolates the straggler.  A
 // stream whose launch fails with a device error is retired and its queries
 // get PG_EDEVICE; when no stream is left, waiting queries fail the same way.
 //
@@ -40,6 +44,7 @@ struct ServerQuery {
     uint64_t ticket;
     pg_plan *plan;
     double t_submit;
+    bool alone = false; // isolated after its batch ran out of time: launched by itself
 };
 
 struct Slot {
@@ -124,14 +129,33 @@ void emit(pg_server *S, const ServerQuery &q, int status, const uint64_t *cnt, d
     S->results.push_back(r);
 }
 
-// Work budget of a launch counting qs: the smallest remaining query time
-// (ns), 0 without a limit; false if some query has no time left (reported).
+// Queries of qs with no time left fail with PG_ETIMEOUT and leave qs.
+void drop_expired(pg_server *S, std::vector<ServerQuery> &qs) {
+    if (S->cfg.query_timeout_s <= 0) return;
+    const double now = S->now();
+    size_t k = 0;
+    for (auto &q : qs) {
+        if (S->cfg.query_timeout_s - (now - q.t_submit) > 0) {
+            qs[k++] = q;
+        } else {
+            emit(S, q, PG_ETIMEOUT, nullptr, now, now, 1);
+            S->outstanding--;
+        }
+    }
+    qs.resize(k);
+}
+
+// Work budget of a launch counting qs (ns), 0 without a limit: the smallest
+// remaining query time for a single query; half of it for a batch, so that
+// when a batch runs out every query still has at least half its time to run
+// alone.  False if some query has no time left (reported).
 bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
     s.view.budget_ns = 0;
     if (S->cfg.query_timeout_s <= 0) return true;
     const double now = S->now();
     double left = 1e300;
     for (auto &q : qs) left = std::min(left, S->cfg.query_timeout_s - (now - q.t_submit));
+    if (qs.size() > 1) left *= 0.5;
     if (left <= 0) {
         for (auto &q : qs) emit(S, q, PG_ETIMEOUT, nullptr, now, now, (int)qs.size());
         S->outstanding -= (int64_t)qs.size();
@@ -181,6 +205,7 @@ int launch_alone(pg_server *S, Slot &s, const ServerQuery &q) {
 
 // Try to launch up to `take` queries on slot s; returns queries launched.
 int launch_batch(pg_server *S, Slot &s, std::vector<ServerQuery> qs) {
+    drop_expired(S, qs);
     for (size_t i = 0; i < qs.size(); ++i) {
         if (!qs[i].plan->h.anti_vertices) continue;
         // the first anti-vertex query goes alone; the rest return to the queue front
@@ -331,6 +356,21 @@ void worker_loop(pg_server *S) {
                 continue;
             } else {
                 const bool timed_out = *(const unsigned long long *)(s.h_counts + 2 * PG_MAX_QUEUES) != 0;
+                if (timed_out && s.qs.size() > 1) {
+                    // isolate: every query of the batch runs again by itself
+                    std::lock_guard<std::mutex> lock(S->mu);
+                    for (size_t i = s.qs.size(); i-- > 0;) {
+                        ServerQuery q = s.qs[i];
+                        q.alone = true;
+                        S->pending.push_front(q);
+                    }
+                    pg_batch_free(s.batch);
+                    s.batch = nullptr;
+                    s.qs.clear();
+                    s.busy = false;
+                    progress = true;
+                    continue;
+                }
                 for (size_t i = 0; i < s.qs.size(); ++i)
                     emit(S, s.qs[i], timed_out ? PG_ETIMEOUT : PG_OK, timed_out ? nullptr : s.h_counts + 2 * i,
                          s.t_start, t, (int)s.qs.size());
@@ -350,8 +390,11 @@ void worker_loop(pg_server *S) {
             {
                 std::lock_guard<std::mutex> lock(S->mu);
                 while (!S->pending.empty() && (int)take.size() < max_batch) {
+                    // an isolated query goes alone; it also ends a batch in the making
+                    if (S->pending.front().alone && !take.empty()) break;
                     take.push_back(S->pending.front());
                     S->pending.pop_front();
+                    if (take.back().alone) break;
                 }
             }
             if (take.empty()) break;

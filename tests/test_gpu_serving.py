@@ -138,3 +138,29 @@ def test_cancel_waiting_and_running_queries(pg):
     with pytest.raises(pg.PgError):
         srv.cancel(10 ** 9)
     srv.close()
+
+
+def test_query_time_limit_isolates_the_slow_query(pg):
+    """With a query time limit, a batch that holds one slow query (unlabeled
+    5-cycles on R-MAT 16) runs out of its budget; its queries are launched
+    again one by one, so the fast ones still return their counts alone and
+    only the slow one reports PG_ETIMEOUT."""
+    import time
+    g = sg.workload_graph(5, scale_down=6)
+    G = pg.Graph.from_synth(g)
+    fast = [sg.pattern(3, sg.clique_edges(3)), sg.pattern(3, sg.star_edges(3)),
+            sg.pattern(4, sg.clique_edges(4)), sg.pattern(4, sg.cycle_edges(4))]
+    want = [pg.count(G, [pg.Plan.from_dict(q)])[0] for q in fast]
+    srv = pg.Server(G, n_streams=1, max_batch=8, query_timeout_s=4.0)
+    t = time.perf_counter()
+    tickets = [srv.submit(q) for q in fast]
+    slow = srv.submit(sg.pattern(5, sg.cycle_edges(5)))
+    more = [srv.submit(q) for q in fast]
+    srv.drain(120)
+    took = time.perf_counter() - t
+    res = {r["ticket"]: r for r in srv.poll()}
+    srv.close()
+    assert res[slow]["status"] == pg.PG_ETIMEOUT
+    assert [res[x]["status"] for x in tickets + more] == [pg.PG_OK] * (2 * len(fast))
+    assert [res[x]["count"] for x in tickets + more] == want + want
+    assert took < 30
