@@ -267,13 +267,34 @@ int pg_count_ex(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uint64_t *c
  * Unlabeled cliques (3..PG_MAX_CLIQUE vertices, e.g. the 14-clique existence
  * query of the paper's evaluation) run on the k-clique kernel, which
  * publishes its count after every first-level row of the start vertex's
- * sub-graph and cuts branches too small to reach k; other patterns run on
+ * sub-graph and, inside a row, at every candidate of the traversal's first
+ * three levels, and cuts branches too small to reach k; other patterns run on
  * the plan interpreter (PG_KERNEL_GENERIC).  Honours the graph's work budget
  * (PG_ETIMEOUT).  Synchronous.  Errors: PG_EINVAL (target 0, NULL argument,
  * labeled pattern on an unlabeled graph), PG_ENOMEM, PG_EDEVICE, PG_ETIMEOUT.
  */
 int pg_count_until(pg_graph *g, pg_plan *p, uint64_t target, uint64_t *count_out, int32_t *reached,
                    void *stream);
+
+/*
+ * pg_plan_operand_bytes - measurement aid: the algorithmic bytes of plan p
+ * on graph g, i.e. 4 bytes times the length of every operand of every set
+ * operation the plan's level program performs, each operand being an
+ * adjacency list cut to the level's partial-order range (Section 4.1
+ * bounds; Section 4.2 differences touch their lists too), summed over every
+ * (start vertex, matching order) task, every bound prefix and every level,
+ * the counted last level included (Section 5.1 processing model).  This is
+ * the work a sorted-list implementation of the plan must read, whatever a
+ * kernel does instead; a roofline divides it by a kernel's time.  Computed
+ * by a dedicated device walk over the same prefixes as the interpreter
+ * kernel (it counts no matches).  Honours pg_set_partition.
+ *   bytes_out  host uint64: the algorithmic bytes.
+ *   ops_out    host uint64: the number of set operations.
+ * Synchronous.  Errors: PG_EINVAL (NULL argument, labeled pattern on an
+ * unlabeled graph), PG_EUNSUPPORTED (cliques above 8 vertices), PG_ENOMEM,
+ * PG_EDEVICE.
+ */
+int pg_plan_operand_bytes(pg_graph *g, pg_plan *p, uint64_t *bytes_out, uint64_t *ops_out, void *stream);
 
 /*
  * pg_clustering_coefficient_above - the clustering-coefficient program of

@@ -96,6 +96,7 @@ _lib.pg_labeled_motif4.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_fsm_general.argtypes = [_vp, _i32, ctypes.c_uint64, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_labeled_motif3.argtypes = [_vp, _vp, _i64, ctypes.POINTER(_i64), _vp]
 _lib.pg_count_until.argtypes = [_vp, _vp, ctypes.c_uint64, _vp, ctypes.POINTER(_i32), _vp]
+_lib.pg_plan_operand_bytes.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_match.argtypes = [_vp, _vp, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_match_range.argtypes = [_vp, _vp, _i64, _i64, _vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), _vp]
 _lib.pg_get_tuning.argtypes = [_vp, _vp]
@@ -367,6 +368,17 @@ def count_until(graph: Graph, plan: Plan, target: int, stream=None):
     _check(_lib.pg_count_until(graph.handle, plan.handle, int(target), out.ctypes.data, ctypes.byref(reached),
                                _stream_ptr(stream)))
     return _u128(out[0], out[1]), bool(reached.value)
+
+
+def plan_operand_bytes(graph: Graph, plan: Plan, stream=None):
+    """pg_plan_operand_bytes: (algorithmic bytes, set operations) of the
+    plan's level program on the graph (4 B per element of every
+    partial-order-bounded operand slice of every set operation)."""
+    b = ctypes.c_uint64()
+    n = ctypes.c_uint64()
+    _check(_lib.pg_plan_operand_bytes(graph.handle, plan.handle, ctypes.byref(b), ctypes.byref(n),
+                                      _stream_ptr(stream)))
+    return int(b.value), int(n.value)
 
 
 def exists(graph: Graph, plan: Plan, stream=None) -> bool:

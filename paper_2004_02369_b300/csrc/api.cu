@@ -534,7 +534,7 @@ extern "C" int pg_count_until(pg_graph *g, pg_plan *pl, uint64_t target, uint64_
     PG_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
     PgRunCtl ctl;
     if ((rc = pg_run_ctl(g, target, s, &ctl)) != PG_OK) return rc;
-    // cliques: the bitmap kernel, publishing after every first-level row
+    // cliques: the bitmap kernel, publishing its count during traversals
     rc = clique ? pg_launch_clique(g, k, k, counts, 0, s, &ctl) : pg_launch_generic(g, pl, counts, 0, true, s, &ctl);
     if (rc) return rc;
     if ((rc = pg_run_ctl_check(ctl, s)) != PG_OK) return rc;
@@ -544,6 +544,22 @@ extern "C" int pg_count_until(pg_graph *g, pg_plan *pl, uint64_t target, uint64_
     count_out[0] = host[0];
     count_out[1] = host[1];
     *reached = (host[1] != 0 || host[0] >= target) ? 1 : 0;
+    return PG_OK;
+}
+
+extern "C" int pg_plan_operand_bytes(pg_graph *g, pg_plan *pl, uint64_t *bytes_out, uint64_t *ops_out, void *stream) {
+    if (!g || !pl || !bytes_out || !ops_out) return pg_set_error(PG_EINVAL, "NULL argument");
+    if (pl->h.labeled && !g->labeled) return pg_set_error(PG_EINVAL, "labeled pattern on an unlabeled graph");
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = pg_plan_upload(pl);
+    if (rc) return rc;
+    unsigned long long *d = g->ex->tmp_counts;
+    if ((rc = pg_launch_operand_bytes(g, pl, d, s)) != PG_OK) return rc;
+    unsigned long long h[2];
+    PG_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
+    *bytes_out = 4ull * h[0];
+    *ops_out = h[1];
     return PG_OK;
 }
 

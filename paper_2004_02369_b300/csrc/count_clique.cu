@@ -122,8 +122,21 @@ struct Walker {
 };
 
 // Run control of the extended variant, copied to shared memory once per CTA
-// so the traversal can poll it without carrying it in registers.
+// so the traversal can poll it without carrying it in registers (with the
+// count words that existence mode publishes to).
 __shared__ PgRunCtl s_run_ctl;
+__shared__ unsigned long long *s_counts;
+
+// Existence mode inside a traversal: publish the warp's kmax-clique count so
+// far (products still queued are published later), so that the first match
+// stops the launch without waiting for the end of its row.  Warp-uniform.
+__device__ __forceinline__ void publish_walk(unsigned long long *cnt, int kmax, int lane) {
+    const unsigned long long mine = cnt[kmax - 3];
+    if (!__any_sync(PG_FULL, mine != 0)) return;
+    cnt[kmax - 3] = 0;
+    const unsigned __int128 tot = warp_sum_u128(mine);
+    if (lane == 0) ctl_publish(s_run_ctl, s_counts, tot);
+}
 
 // Group-wide barrier: the CTA for heavy vertices, the warp for light ones.
 template <bool CTA>
@@ -267,7 +280,10 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
                 if constexpr (XT && P <= 2) {
                     // long traversals (large k in dense regions) stop soon
                     // after the launch's stop flag or work budget says so
-                    if (s_run_ctl.words && ctl_stop(s_run_ctl, lane)) return;
+                    if (s_run_ctl.words) {
+                        if (s_run_ctl.target) publish_walk(cnt, kmax, lane);
+                        if (ctl_stop(s_run_ctl, lane)) return;
+                    }
                 }
                 const int l = w * 32 + __ffs(x) - 1;
                 x &= x - 1;
@@ -434,7 +450,10 @@ __global__ void __launch_bounds__(kBlock, MINB) k_count_clique(CliqueArgs a) {
     wk.used = 0;
     wk.kmin = a.kmin;
     if constexpr (XT) {
-        if (threadIdx.x == 0) s_run_ctl = a.ctl;
+        if (threadIdx.x == 0) {
+            s_run_ctl = a.ctl;
+            s_counts = a.counts;
+        }
         __syncthreads();
     }
 

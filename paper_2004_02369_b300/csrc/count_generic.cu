@@ -111,6 +111,100 @@ __global__ void __launch_bounds__(kBlock) k_count_generic(GenericArgs a) {
     if (lane == 0 && acc) atomic_add_u128(a.counts, acc);
 }
 
+// ---- algorithmic operand bytes (measurement) --------------------------------
+//
+// The plan's set operations read, per level and bound prefix m, every
+// intersected and every subtracted list cut to the level's partial-order
+// range (lo, hi).  level_operand_elems gives the total length of those
+// slices; the walk below visits the same prefixes as run_task (every level
+// but the last materialised and enumerated) and sums it over every set
+// operation, the last level's for all candidates of the level before it in
+// parallel across lanes.
+
+__device__ __forceinline__ unsigned long long level_operand_elems(const DevGraph &g, const PgLevel &L, const int *m) {
+    const LevelRange r = level_range(L, m);
+    if (r.lo + 1 >= r.hi) return 0;
+    unsigned long long e = 0;
+    for (int i = 0; i < L.n_int + L.n_diff; ++i) {
+        const int w = m[i < L.n_int ? L.int_src[i] : L.diff_src[i - L.n_int]];
+        const int4 vi = __ldg(&g.vinfo[w]);
+        e += (unsigned long long)bound_slice(adj_of(g, vi), vi.y, r.lo, r.hi).len;
+    }
+    return e;
+}
+
+__device__ void operand_walk(const GenericArgs &a, int v, const PgOrder &ord, int *wbuf, int lane,
+                             unsigned long long &elems, unsigned long long &ops) {
+    const DevGraph &g = a.g;
+    const int L = ord.n_levels;
+    const int4 v0 = __ldg(&g.vinfo[v]);
+    if (ord.lv[0].label >= 0 && v0.w != ord.lv[0].label) return;
+    int m[PGP_MAXK];
+    int sz[PGP_MAXK], idx[PGP_MAXK];
+    m[0] = v;
+    if (ord.lv[0].n_anti && !checks_ok(g, ord, 0, m, lane)) return;
+    if (L == 1) return;
+    if (L == 2) {
+        if (lane == 0) {
+            elems += level_operand_elems(g, ord.lv[1], m);
+            ++ops;
+        }
+        return;
+    }
+    int l = 1;
+    for (;;) {
+        const PgLevel &lv = ord.lv[l];
+        if (lane == 0) {
+            elems += level_operand_elems(g, lv, m);
+            ++ops;
+        }
+        int *buf = wbuf + a.lvl_off[l];
+        sz[l] = fill_level(g, lv, m, buf, lane);
+        if (lv.n_anti) sz[l] = filter_anti(g, ord, l, m, buf, sz[l], lane);
+        idx[l] = 0;
+        if (l == L - 2) {
+            // the last level's operation for every candidate of this one
+            int mm[PGP_MAXK];
+            for (int i = 0; i < l; ++i) mm[i] = m[i];
+            for (int c = lane; c < sz[l]; c += 32) {
+                mm[l] = buf[c];
+                elems += level_operand_elems(g, ord.lv[L - 1], mm);
+                ++ops;
+            }
+            idx[l] = sz[l];
+        }
+        while (l >= 1 && idx[l] >= sz[l]) --l;
+        if (l < 1) break;
+        m[l] = wbuf[a.lvl_off[l] + idx[l]];
+        ++idx[l];
+        ++l;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_operand_bytes(GenericArgs a, unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    int *wbuf = a.scratch + gw * a.warp_stride;
+    unsigned long long elems = 0, ops = 0;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(a.queue, 1ull);
+        t = __shfl_sync(PG_FULL, t, 0);
+        if (t >= a.n_tasks) break;
+        const unsigned long long tt = a.offset + t * a.stride;
+        operand_walk(a, (int)(tt / (unsigned long long)a.n_orders), a.orders[tt % (unsigned long long)a.n_orders],
+                     wbuf, lane, elems, ops);
+    }
+    for (int o = 16; o; o >>= 1) {
+        elems += __shfl_down_sync(PG_FULL, elems, o);
+        ops += __shfl_down_sync(PG_FULL, ops, o);
+    }
+    if (lane == 0) {
+        atomicAdd(out, elems);
+        atomicAdd(out + 1, ops);
+    }
+}
+
 int generic_grid(const pg_graph *g) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_generic, kBlock, 0);
@@ -183,6 +277,36 @@ int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_
     a.ctl = ctl ? *ctl : PgRunCtl{};
     if (persistent) PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
     k_count_generic<<<grid_of(g, p, persistent), kBlock, 0, s>>>(a);
+    PG_CUDA(cudaGetLastError());
+    return PG_OK;
+}
+
+int pg_launch_operand_bytes(pg_graph *g, const pg_plan *p, unsigned long long *out_dev, cudaStream_t s) {
+    PG_CUDA(cudaMemsetAsync(out_dev, 0, 2 * sizeof(unsigned long long), s));
+    if (p->h.big_clique) return pg_set_error(PG_EUNSUPPORTED, "cliques above 8 vertices have no level program");
+    if (g->n == 0 || p->h.orders.empty()) return PG_OK;
+    GenericArgs a;
+    a.g = g->d;
+    a.orders = p->d_orders;
+    a.n_orders = (int)p->h.orders.size();
+    a.warp_stride = level_layout(g, p, a.lvl_off);
+    a.scratch = (int *)g->ex->scratch;
+    a.queue = g->ex->queues;
+    a.n_tasks = n_tasks_of(g, p);
+    const PgTaskSel sel = pg_task_sel(g);
+    a.offset = (unsigned long long)sel.offset;
+    a.stride = (unsigned long long)sel.stride;
+    a.persistent = 1;
+    a.counts = nullptr;
+    a.ctl = PgRunCtl{};
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_operand_bytes, kBlock, 0);
+    const int grid = std::max(1, per_sm) * g->num_sms;
+    const int rc = pg_ensure_scratch(g, (size_t)grid * kWarpsPerBlock * (size_t)a.warp_stride * sizeof(int), s);
+    if (rc) return rc;
+    a.scratch = (int *)g->ex->scratch; // the arena may have moved
+    PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
+    k_operand_bytes<<<grid, kBlock, 0, s>>>(a, out_dev);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }

@@ -188,6 +188,9 @@ int pg_plan_upload(pg_plan *p);
 int pg_launch_generic(pg_graph *g, const pg_plan *p, unsigned long long *counts_dev,
                       int queue_slot, bool persistent, cudaStream_t s, const PgRunCtl *ctl = nullptr);
 size_t pg_generic_scratch_bytes(const pg_graph *g, const pg_plan *p, bool persistent);
+// algorithmic operand elements of the plan's set operations and their number
+// into out_dev[0], out_dev[1] (reserves its own scratch)
+int pg_launch_operand_bytes(pg_graph *g, const pg_plan *p, unsigned long long *out_dev, cudaStream_t s);
 // per-warp level buffers of a level program (offsets per level, total ints)
 long long pg_level_layout(const pg_graph *g, const std::vector<PgOrder> &orders, bool listing, long long *off);
 

@@ -38,7 +38,36 @@ def lib():
         _lib = ctypes.CDLL(build())
         _lib.pe_count.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.POINTER(_Desc), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+        _lib.pe_operand_elems.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(_Desc), ctypes.c_void_p]
     return _lib
+
+
+def _desc(p: dict):
+    e = np.ascontiguousarray(np.asarray(p["edges"], dtype=np.int32).reshape(-1))
+    a = np.ascontiguousarray(np.asarray(p.get("anti_edges", []), dtype=np.int32).reshape(-1))
+    pl = None if p.get("labels") is None else np.ascontiguousarray(p["labels"], dtype=np.int32)
+    av = None if p.get("anti_vertex") is None else np.ascontiguousarray(p["anti_vertex"], dtype=np.uint8)
+    d = _Desc(p["k"], e.size // 2, e.ctypes.data if e.size else None, a.size // 2,
+              a.ctypes.data if a.size else None, None if pl is None else pl.ctypes.data,
+              None if av is None else av.ctypes.data, 1 if p.get("vertex_induced") else 0)
+    return d, (e, a, pl, av)
+
+
+def operand_elems(g, p: dict):
+    """(operand elements, set operations) of p's counting program on g:
+    the length of every partial-order-bounded operand list of every set
+    operation, summed over every task, prefix and level."""
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    adj = np.ascontiguousarray(g.adj, dtype=np.int32)
+    lab = None if g.labels is None else np.ascontiguousarray(g.labels, dtype=np.int32)
+    d, keep = _desc(p)
+    out = np.zeros(2, dtype=np.uint64)
+    rc = lib().pe_operand_elems(off.ctypes.data, g.n, adj.ctypes.data if adj.size else None,
+                                None if lab is None else lab.ctypes.data, ctypes.byref(d), out.ctypes.data)
+    if rc:
+        raise RuntimeError(f"plan compile error {rc}")
+    return int(out[0]), int(out[1])
 
 
 def count(g, p: dict, listing: bool = False):

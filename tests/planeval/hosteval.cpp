@@ -118,7 +118,72 @@ unsigned __int128 walk(const RankedGraph &g, const PgOrder &o, int l, int *m) {
     return t;
 }
 
+// Operand elements of level L at prefix m: every intersected and subtracted
+// list cut to the level's open range (lo, hi).
+uint64_t operand_elems(const RankedGraph &g, const PgLevel &L, const int *m) {
+    int lo = -1, hi = 0x7fffffff;
+    for (int i = 0; i < L.n_lo; ++i) lo = std::max(lo, m[L.lo_src[i]]);
+    for (int i = 0; i < L.n_hi; ++i) hi = std::min(hi, m[L.hi_src[i]]);
+    if (lo + 1 >= hi) return 0;
+    uint64_t e = 0;
+    for (int i = 0; i < L.n_int + L.n_diff; ++i) {
+        const int w = i < L.n_int ? m[L.int_src[i]] : m[L.diff_src[i - L.n_int]];
+        for (int64_t k = g.off[w]; k < g.off[w + 1]; ++k) e += (g.adj[k] > lo && g.adj[k] < hi) ? 1 : 0;
+    }
+    return e;
+}
+
+void walk_ops(const RankedGraph &g, const PgOrder &o, int l, int *m, uint64_t &elems, uint64_t &ops) {
+    const PgLevel &L = o.lv[l];
+    elems += operand_elems(g, L, m);
+    ++ops;
+    if (l == o.n_levels - 1) return;
+    std::vector<int> s = level_set(g, L, m);
+    for (int x : s) {
+        m[l] = x;
+        if (L.n_anti && !checks_ok(g, o, l, m)) continue;
+        walk_ops(g, o, l + 1, m, elems, ops);
+    }
+}
+
 }  // namespace
+
+// Operand elements and set operations of p's counting program on the graph
+// (every level of every task, the counted last level included).
+extern "C" int pe_operand_elems(const int64_t *off, int64_t n, const int32_t *adj, const int32_t *labels,
+                                const pg_pattern_desc *d, uint64_t *out2) {
+    PgPattern p;
+    p.k = d->k;
+    for (int i = 0; i < d->n_edges; ++i) {
+        int u = d->edges[2 * i], w = d->edges[2 * i + 1];
+        p.rel[u][w] = p.rel[w][u] = 1;
+    }
+    for (int i = 0; i < d->n_anti; ++i) {
+        int u = d->anti_edges[2 * i], w = d->anti_edges[2 * i + 1];
+        p.rel[u][w] = p.rel[w][u] = 2;
+    }
+    for (int u = 0; u < d->k; ++u) {
+        p.label[u] = d->labels ? d->labels[u] : -1;
+        p.anti_vertex[u] = d->anti_vertex ? d->anti_vertex[u] : 0;
+    }
+    PgPlanHost h;
+    std::string err;
+    int rc = pg_plan_compile(p, d->vertex_induced != 0, h, err);
+    if (rc) return rc;
+    RankedGraph g = rank_graph(off, n, adj, labels);
+    uint64_t elems = 0, ops = 0;
+    int m[PGP_MAXK];
+    for (const PgOrder &o : h.orders)
+        for (int v = 0; v < g.n; ++v) {
+            if (o.lv[0].label >= 0 && g.label[v] != o.lv[0].label) continue;
+            m[0] = v;
+            if (!checks_ok(g, o, 0, m)) continue;
+            if (o.n_levels > 1) walk_ops(g, o, 1, m, elems, ops);
+        }
+    out2[0] = elems;
+    out2[1] = ops;
+    return 0;
+}
 
 // Counts p on the graph by walking the compiled counting program (use_list =
 // 0) or the listing program (use_list = 1, every vertex enumerated).

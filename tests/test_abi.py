@@ -41,6 +41,7 @@ def test_null_arguments_rejected_without_a_device():
         lambda: L.pg_count(None, None, 1, None, None),
         lambda: L.pg_count_ex(None, None, 1, None, 0, None),
         lambda: L.pg_count_until(None, None, 1, None, ctypes.byref(i32), None),
+        lambda: L.pg_plan_operand_bytes(None, None, ctypes.byref(u64), ctypes.byref(u64), None),
         lambda: L.pg_match(None, None, None, 0, ctypes.byref(u64), None),
         lambda: L.pg_match_range(None, None, 0, 0, None, 0, ctypes.byref(u64), None),
         lambda: L.pg_fsm(None, 3, 1, None, 0, ctypes.byref(i64), None),

@@ -212,3 +212,36 @@ def test_every_generated_pattern_plans_match_oracle():
             assert got == want, (p, g.n)
             got, _ = planeval.count(g, p, listing=True)
             assert got == want, (p, g.n, "listing")
+
+
+def _ranked_out_degrees(g):
+    """Out-degree d+(r) of every degree rank r (rank = position in
+    (degree desc, id asc); out-neighbours = neighbours of smaller rank), and
+    the rank of every original vertex."""
+    deg = np.diff(g.offsets)
+    order = sorted(range(g.n), key=lambda v: (-deg[v], v))
+    rank = np.empty(g.n, dtype=np.int64)
+    rank[order] = np.arange(g.n)
+    dout = np.zeros(g.n, dtype=np.int64)
+    for v in range(g.n):
+        nb = rank[g.adj[g.offsets[v]:g.offsets[v + 1]]]
+        dout[rank[v]] = int((nb < rank[v]).sum())
+    return dout, rank
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_operand_elements_closed_forms(seed):
+    """The operand counter of the plan walk (the numerator of the set-operation
+    roofline) against closed forms.  Triangles: level 1 reads N+(v); level 2
+    reads N+(v) cut below u and N+(u) for every u in N+(v), so the elements
+    are sum d+(v) + sum C(d+(v), 2) + sum_v sum_{u in N+(v)} d+(u), and the
+    operations n + m.  The 3-star reads adj(v) once per start vertex."""
+    g = sg.chung_lu(300, 1500, 2.2, 40.0, seed)
+    dout, rank = _ranked_out_degrees(g)
+    second = 0
+    for v in range(g.n):
+        nb = rank[g.adj[g.offsets[v]:g.offsets[v + 1]]]
+        second += int(dout[nb[nb < rank[v]]].sum())
+    want = int(dout.sum() + (dout * (dout - 1) // 2).sum()) + second
+    assert planeval.operand_elems(g, sg.pattern(3, sg.clique_edges(3))) == (want, g.n + g.m)
+    assert planeval.operand_elems(g, sg.pattern(3, sg.star_edges(3))) == (2 * g.m, g.n)
