@@ -672,9 +672,13 @@ int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int
  * publishes per-query results with submit / start / completion times.
  * Batches on different streams overlap on the device, and queries arriving
  * while others run are admitted as soon as a stream frees up.  Plans are
- * compiled once per distinct pattern and kept.  An anti-vertex query is
- * launched alone on the plan interpreter (PG_KERNEL_GENERIC), since batches
- * do not take anti-vertex plans.  The paper runs one mining
+ * compiled once per distinct pattern and kept, with the pattern's measured
+ * service time: the first query of a pattern runs alone, and a pattern that
+ * took longer than batch_limit_ms alone keeps running alone, so batches
+ * gather the short queries (which overtake long ones waiting in the queue)
+ * and a long query never holds a batch of short ones.  An anti-vertex query
+ * is launched alone on the plan interpreter (PG_KERNEL_GENERIC), since
+ * batches do not take anti-vertex plans.  The paper runs one mining
  * program at a time (Section 5.1); this loop applies its processing model to
  * a stream of patterns.
  *   n_streams      concurrent batches (1..16); memory_budget: device bytes
@@ -699,7 +703,14 @@ typedef struct {
                                among its queries; when a batch runs out, its
                                queries are launched again one by one with
                                their own time left, so only the slow one
-                               fails); 0: no limit */
+                               fails).  The first (measuring) run of a
+                               pattern gets at most a quarter of the limit;
+                               if that runs out, the query goes to the back
+                               of the queue with the time it has left.
+                               0: no limit */
+    double batch_limit_ms;  /* > 0: a pattern whose query took longer than
+                               this alone is not batched again; 0: 20 ms;
+                               < 0: no measuring, any query may be batched */
 } pg_server_config;
 
 typedef struct {

@@ -12,6 +12,13 @@
 // up).  With serial = 1 the same kernels run one query per launch, one
 // launch at a time -- the one-query-at-a-time baseline.
 //
+// Admission by measured cost: the first query of a pattern runs alone and
+// its service time is kept with the cached plan; patterns that took longer
+// than the batch limit alone keep running alone.  A free stream takes the
+// oldest waiting query if it must run alone, else a batch of the waiting
+// short queries (which so overtake long ones), so a long query never holds
+// a batch of short ones and short queries are still fused into one launch.
+//
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
 // the kernels stop when it runs out, so one slow pattern cannot hold a
@@ -19,8 +26,10 @@
 // batch gets half the least time left among its queries; if it runs out,
 // its queries (it is not known which one was slow) go back to the front of
 // the queue to be launched one by one with the time they have left, which
-// isolates the straggler.  A
-// stream whose launch fails with a device error is retired and its queries
+// isolates the straggler.  The measuring run of a new pattern gets at most
+// a quarter of the limit; if it runs out, the query goes to the back of the
+// queue with the time it has left, so queries behind it are not held for
+// its whole limit.  A stream whose launch fails with a device error is retired and its queries
 // get PG_EDEVICE; when no stream is left, waiting queries fail the same way.
 //
 // Section 5.1 processing model (tasks = start vertices) applied to a stream
@@ -45,6 +54,14 @@ struct ServerQuery {
     pg_plan *plan;
     double t_submit;
     bool alone = false; // isolated after its batch ran out of time: launched by itself
+    double cap_s = 0;   // > 0: budget cap of a measuring run (re-queued if it runs out)
+    bool requeued = false;
+};
+
+// Measured service time of a pattern (worker thread only).
+struct PatternCost {
+    double alone_s = -1; // last time of a one-query launch; < 0: not measured
+    bool slow = false;   // longer than the batch limit alone, or ran out of time
 };
 
 struct Slot {
@@ -85,6 +102,8 @@ struct pg_server {
     uint64_t next_ticket = 1;
     std::atomic<int64_t> batches{0}, launched_queries{0};
     std::vector<uint64_t> cancelled;     // tickets to cancel (worker applies them)
+    std::unordered_map<const pg_plan *, PatternCost> cost; // worker thread only
+    double batch_limit_s = 0.02;         // < 0: batch everything
     cudaStream_t ctl_stream = nullptr;   // raises stop words of running launches
     unsigned long long *h_one = nullptr; // pinned host word holding 1: the source of those
                                          // copies (host-to-device, done by a copy engine
@@ -156,6 +175,7 @@ bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
     double left = 1e300;
     for (auto &q : qs) left = std::min(left, S->cfg.query_timeout_s - (now - q.t_submit));
     if (qs.size() > 1) left *= 0.5;
+    else if (qs[0].cap_s > 0 && left > 0) left = std::min(left, qs[0].cap_s);
     if (left <= 0) {
         for (auto &q : qs) emit(S, q, PG_ETIMEOUT, nullptr, now, now, (int)qs.size());
         S->outstanding -= (int64_t)qs.size();
@@ -310,6 +330,16 @@ void apply_cancels(pg_server *S) {
     // a ticket found nowhere already has its result: nothing to do
 }
 
+// Whether query q must be launched by itself: isolated after a batch ran
+// out of time, an anti-vertex pattern, or a pattern not yet measured or
+// measured longer than the batch limit.
+bool goes_alone(pg_server *S, const ServerQuery &q) {
+    if (q.alone || q.plan->h.anti_vertices) return true;
+    if (S->batch_limit_s < 0) return false;
+    auto it = S->cost.find(q.plan);
+    return it == S->cost.end() || it->second.slow;
+}
+
 void worker_loop(pg_server *S) {
     cudaSetDevice(S->device);
     const int max_batch = S->cfg.serial ? 1 : std::max(1, std::min(S->cfg.max_batch, (int)PG_MAX_QUEUES));
@@ -356,6 +386,30 @@ void worker_loop(pg_server *S) {
                 continue;
             } else {
                 const bool timed_out = *(const unsigned long long *)(s.h_counts + 2 * PG_MAX_QUEUES) != 0;
+                if (s.qs.size() == 1) {
+                    // a one-query launch measures its pattern
+                    PatternCost &c = S->cost[s.qs[0].plan];
+                    c.alone_s = t - s.t_start;
+                    c.slow = timed_out || (S->batch_limit_s >= 0 && c.alone_s > S->batch_limit_s);
+                    ServerQuery q = s.qs[0];
+                    if (timed_out && q.cap_s > 0 && S->cfg.query_timeout_s - (t - q.t_submit) > 0) {
+                        // the measuring run ran out of its cap: to the back
+                        // of the queue with the time it has left
+                        q.cap_s = 0;
+                        q.requeued = true;
+                        q.alone = true;
+                        {
+                            std::lock_guard<std::mutex> lock(S->mu);
+                            S->pending.push_back(q);
+                        }
+                        pg_batch_free(s.batch);
+                        s.batch = nullptr;
+                        s.qs.clear();
+                        s.busy = false;
+                        progress = true;
+                        continue;
+                    }
+                }
                 if (timed_out && s.qs.size() > 1) {
                     // isolate: every query of the batch runs again by itself
                     std::lock_guard<std::mutex> lock(S->mu);
@@ -389,12 +443,27 @@ void worker_loop(pg_server *S) {
             std::vector<ServerQuery> take;
             {
                 std::lock_guard<std::mutex> lock(S->mu);
-                while (!S->pending.empty() && (int)take.size() < max_batch) {
-                    // an isolated query goes alone; it also ends a batch in the making
-                    if (S->pending.front().alone && !take.empty()) break;
-                    take.push_back(S->pending.front());
-                    S->pending.pop_front();
-                    if (take.back().alone) break;
+                if (!S->pending.empty()) {
+                    ServerQuery &f = S->pending.front();
+                    if (max_batch == 1 || goes_alone(S, f)) {
+                        // the oldest query runs by itself: isolated, measuring
+                        // its pattern, known long, or anti-vertex
+                        if (!S->cfg.serial && S->cfg.query_timeout_s > 0 && !f.requeued && !f.alone &&
+                            !S->cost.count(f.plan))
+                            f.cap_s = 0.25 * S->cfg.query_timeout_s;
+                        take.push_back(f);
+                        S->pending.pop_front();
+                    } else {
+                        // a batch of the waiting short queries, oldest first
+                        for (auto it = S->pending.begin(); it != S->pending.end() && (int)take.size() < max_batch;) {
+                            if (goes_alone(S, *it)) {
+                                ++it;
+                            } else {
+                                take.push_back(*it);
+                                it = S->pending.erase(it);
+                            }
+                        }
+                    }
                 }
             }
             if (take.empty()) break;
@@ -415,12 +484,15 @@ void worker_loop(pg_server *S) {
 extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_server **out) {
     if (!g || !cfg || !out) return pg_set_error(PG_EINVAL, "NULL argument");
     if (!(cfg->query_timeout_s >= 0.0)) return pg_set_error(PG_EINVAL, "query_timeout_s must be >= 0");
+    if (cfg->batch_limit_ms != cfg->batch_limit_ms) return pg_set_error(PG_EINVAL, "batch_limit_ms is NaN");
     *out = nullptr;
     pg_server *S = new (std::nothrow) pg_server();
     if (!S) return pg_set_error(PG_ENOMEM, "host allocation failed");
     S->g = g;
     g->servers++; // views copy the graph's hub and heavy pointers: no retuning meanwhile
     S->cfg = *cfg;
+    if (cfg->batch_limit_ms > 0) S->batch_limit_s = cfg->batch_limit_ms * 1e-3;
+    if (cfg->batch_limit_ms < 0) S->batch_limit_s = -1;
     S->t0 = std::chrono::steady_clock::now();
     const int n_streams = cfg->serial ? 1 : std::max(1, std::min(cfg->n_streams, 16));
     int rc = PG_OK;

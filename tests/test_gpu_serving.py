@@ -140,18 +140,9 @@ def test_cancel_waiting_and_running_queries(pg):
     srv.close()
 
 
-def test_query_time_limit_isolates_the_slow_query(pg):
-    """With a query time limit, a batch that holds one slow query (unlabeled
-    5-cycles on R-MAT 16) runs out of its budget; its queries are launched
-    again one by one, so the fast ones still return their counts alone and
-    only the slow one reports PG_ETIMEOUT."""
+def _straggler_run(pg, G, fast, **kw):
     import time
-    g = sg.workload_graph(5, scale_down=6)
-    G = pg.Graph.from_synth(g)
-    fast = [sg.pattern(3, sg.clique_edges(3)), sg.pattern(3, sg.star_edges(3)),
-            sg.pattern(4, sg.clique_edges(4)), sg.pattern(4, sg.cycle_edges(4))]
-    want = [pg.count(G, [pg.Plan.from_dict(q)])[0] for q in fast]
-    srv = pg.Server(G, n_streams=1, max_batch=8, query_timeout_s=4.0)
+    srv = pg.Server(G, query_timeout_s=4.0, **kw)
     t = time.perf_counter()
     tickets = [srv.submit(q) for q in fast]
     slow = srv.submit(sg.pattern(5, sg.cycle_edges(5)))
@@ -160,7 +151,30 @@ def test_query_time_limit_isolates_the_slow_query(pg):
     took = time.perf_counter() - t
     res = {r["ticket"]: r for r in srv.poll()}
     srv.close()
+    return res, tickets + more, slow, took
+
+
+@pytest.mark.parametrize("mode", ["measured", "batch_everything"])
+def test_query_time_limit_fails_only_the_slow_query(pg, mode):
+    """A query time limit with one slow query (unlabeled 5-cycles on R-MAT
+    16, far longer than the limit) among short ones: only the slow one
+    reports PG_ETIMEOUT; the short ones return their counts alone.
+    measured: one stream; each pattern's first query runs alone with a
+    quarter of the limit, so the slow one goes to the back of the queue and
+    the short ones behind it run first.  batch_everything: no measuring, two
+    streams; the batch holding the slow query runs out of its budget (half
+    the time left) and its queries are launched again one by one."""
+    g = sg.workload_graph(5, scale_down=6)
+    G = pg.Graph.from_synth(g)
+    fast = [sg.pattern(3, sg.clique_edges(3)), sg.pattern(3, sg.star_edges(3)),
+            sg.pattern(4, sg.clique_edges(4)), sg.pattern(4, sg.cycle_edges(4))]
+    want = [pg.count(G, [pg.Plan.from_dict(q)])[0] for q in fast]
+    kw = dict(n_streams=1, max_batch=8) if mode == "measured" else dict(n_streams=2, max_batch=8, batch_limit_ms=-1)
+    res, ok, slow, took = _straggler_run(pg, G, fast, **kw)
     assert res[slow]["status"] == pg.PG_ETIMEOUT
-    assert [res[x]["status"] for x in tickets + more] == [pg.PG_OK] * (2 * len(fast))
-    assert [res[x]["count"] for x in tickets + more] == want + want
+    assert [res[x]["status"] for x in ok] == [pg.PG_OK] * len(ok)
+    assert [res[x]["count"] for x in ok] == want + want
     assert took < 30
+    if mode == "measured":
+        # the second round of short queries was fused into one launch
+        assert max(res[x]["batch_size"] for x in ok[len(fast):]) > 1
