@@ -707,7 +707,7 @@ def _cfg_motif4(pg, dev, args) -> dict:
             "e2e": {"value": matches / (e2e["ms"] / 1e3), "unit": UNIT, "ms": e2e["ms"],
                     "h2d_bytes_per_step": e2e["h2d_bytes_per_step"], "d2h_bytes_per_step": 96,
                     "includes": "pg_load_graph from pinned host CSR, pg_count (batch build, launches, D2H)"},
-            "roofline": hbm_roofline("k_c4_dense", 4 * inc, c4_ms,
+            "roofline": hbm_roofline("k_c4_tiled", 4 * inc, c4_ms,
                                      "4 B x adjacency elements the co-degree pass reads (neighbour suffixes "
                                      "above each anchor); timed: the 4-cycle term alone",
                                      {"share_of_fused_step": c4_ms / fused_ms})}

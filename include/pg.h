@@ -411,10 +411,13 @@ int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax, uint64_t *
                              void *stream);
 
 /*
- * pg_compile_batch - merge the matching-order programs of n_plans plans
- * (1..64) into one prefix tree for a single launch (shared start vertex and
- * shared candidate sets of identical level prefixes; Section 5.1 processing
- * model applied to several patterns at once).  Host object with a device
+ * pg_compile_batch - the matching-order programs of n_plans plans (1..64)
+ * for a single launch (Section 5.1 processing model applied to several
+ * patterns at once).  The programs of one counted pattern form a prefix
+ * tree (shared candidate sets of identical level prefixes); by default each
+ * counted pattern is a task group of its own, the launch's warps taking the
+ * (pattern, start vertex) tasks pattern by pattern, so that the warps on an
+ * SM mostly run one pattern's code at a time.  Host object with a device
  * copy on the current device; plans may be freed afterwards.
  *   flags  PG_BATCH_EXPAND_ANTI: count a plan with anti-edges (no
  *          anti-vertices, at most 6 anti-edges) as the signed sum over its
@@ -424,11 +427,15 @@ int pg_count_cliques_noalloc(pg_graph *g, int32_t kmin, int32_t kmax, uint64_t *
  *          Theorem of Section 3.1.3 it covers vertex-induced patterns);
  *          isomorphic terms of all plans are counted once.  0: anti-edges
  *          are applied as set differences inside each plan.
+ *          PG_BATCH_SHARE_PREFIXES: merge the programs of all counted
+ *          patterns into one prefix tree walked once per start vertex
+ *          (candidate sets of identical prefixes computed once for all).
  * At most 64 distinct counted patterns per batch after expansion.
  * Errors: PG_EINVAL, PG_EUNSUPPORTED (too many counted patterns),
  * PG_ENOMEM, PG_EDEVICE.
  */
 #define PG_BATCH_EXPAND_ANTI 1
+#define PG_BATCH_SHARE_PREFIXES 2
 int pg_compile_batch(pg_plan *const *plans, int32_t n_plans, int32_t flags, pg_batch **out);
 
 /* pg_batch_get_info - tree nodes, merged programs, and the total number of

@@ -247,15 +247,16 @@ class Plan:
 
 
 class Batch:
-    """Several plans merged into one prefix tree, counted in one launch."""
+    """Several plans counted in one launch (pg_compile_batch)."""
 
     EXPAND_ANTI = 1
+    SHARE_PREFIXES = 2
 
-    def __init__(self, plans, expand_anti_edges: bool = True):
+    def __init__(self, plans, expand_anti_edges: bool = True, share_prefixes: bool = False):
         self.plans = list(plans)
         h = _vp()
-        _check(_lib.pg_compile_batch(_plan_array(self.plans), len(self.plans),
-                                     self.EXPAND_ANTI if expand_anti_edges else 0, ctypes.byref(h)))
+        flags = (self.EXPAND_ANTI if expand_anti_edges else 0) | (self.SHARE_PREFIXES if share_prefixes else 0)
+        _check(_lib.pg_compile_batch(_plan_array(self.plans), len(self.plans), flags, ctypes.byref(h)))
         self._h = h
 
     @property

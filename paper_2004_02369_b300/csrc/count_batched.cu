@@ -1,24 +1,32 @@
-// Batched counting: many plans in one persistent launch over a shared
-// exploration tree.
+// Batched counting: many plans in one persistent launch.
 //
 // Every plan contributes one level program per matching order (Section 4.1);
-// every program starts at the task's start vertex (Section 5.1).  Programs of
-// all plans in a batch are merged into a prefix tree: two programs share a
-// node at depth l when their level specifications 1..l are identical (same
-// intersected / subtracted / bounding / excluded earlier levels and label),
-// so the candidate set of a shared prefix is computed once per start vertex
-// and its candidates are extended into every program below it.  A node where
-// one or more programs end is counted once by cardinality and adds
-// C(|S|, g) into each such plan's counter.  For the six induced 4-vertex
-// motifs the 22 programs share their first level (the start vertex's
-// out-neighbourhood) and most of their second.  Two counted patterns leave
-// the tree for kernels of their own: unlabeled k-cliques (the bitmap clique
-// kernel) and the unlabeled edge-induced 4-cycle (co-degree accumulation).
+// every program starts at the task's start vertex (Section 5.1).  The
+// programs of a counted pattern are merged into a prefix tree: two programs
+// share a node at depth l when their level specifications 1..l are
+// identical (same intersected / subtracted / bounding / excluded earlier
+// levels and label), so the candidate set of a shared prefix is computed
+// once per start vertex and its candidates are extended into every program
+// below it.  A node where one or more programs end is counted once by
+// cardinality and adds C(|S|, g) into each such plan's counter.  Two counted
+// patterns leave the tree for kernels of their own: unlabeled k-cliques (the
+// bitmap clique kernel) and the unlabeled edge-induced 4-cycle (co-degree
+// accumulation).
 //
-// GPU mapping: one warp per start vertex (device atomic queue, highest
-// degree first, Section 5.2); depth-first walk of the tree with an explicit
-// per-depth stack; per-depth candidate buffers in a per-warp scratch region;
-// per-warp 128-bit counters per plan in shared memory, flushed once per warp.
+// Task groups: by default each counted pattern is a group of its own and a
+// task is a (group, start vertex) pair, handed out group by group, so the
+// warps of an SM mostly run one pattern's set operations at a time (the
+// fused walk of several patterns' trees per start vertex measured slower
+// than the same trees one after another: more code in flight per SM, and
+// the instruction fetch stall is this kernel's largest).  With
+// PG_BATCH_SHARE_PREFIXES all patterns form one tree walked once per start
+// vertex, sharing identical prefixes across patterns.
+//
+// GPU mapping: one warp per task (device atomic queue, highest degree first
+// within a group, Section 5.2); depth-first walk of the tree with an
+// explicit per-depth stack; per-depth candidate buffers in a per-warp scratch
+// region; per-warp 128-bit counters per plan in shared memory, flushed once
+// per warp.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -36,6 +44,7 @@ struct PgTrieNode {
     int32_t first_child, n_children;
     int32_t first_term, n_terms;
     int32_t n_joint;
+    int32_t group; // roots: the task group that walks this tree
 };
 
 struct PgTrieTerm {
@@ -52,6 +61,7 @@ struct BatchArgs {
     const PgTrieNode *nodes;
     const PgTrieTerm *terms;
     int n_roots; // roots are nodes[0 .. n_roots)
+    int n_groups; // task t walks group t / n_tasks over start-vertex task t % n_tasks
     int n_slots;
     int *scratch;
     long long warp_stride;
@@ -114,10 +124,12 @@ __global__ void __launch_bounds__(W * 32, CAP == 1 ? 32 / W : CAP == 2 ? 20 / W 
             unsigned long long t = 0;
             if (lane == 0) t = atomicAdd(a.queue, (unsigned long long)a.chunk);
             task = (long long)__shfl_sync(PG_FULL, t, 0);
-            if (task >= a.n_tasks) break;
-            task_end = min(task + a.chunk, a.n_tasks);
+            if (task >= a.n_groups * a.n_tasks) break;
+            // a grab stays inside one group
+            task_end = min(task + a.chunk, (task / a.n_tasks + 1) * a.n_tasks);
         }
-        const long long tg = a.offset + task * a.stride;
+        const int grp = (int)(task / a.n_tasks);
+        const long long tg = a.offset + (task - grp * a.n_tasks) * a.stride;
         ++task;
         int v, part = 0, parts = 1;
         if (tg < a.n_split_tasks) {
@@ -135,7 +147,7 @@ __global__ void __launch_bounds__(W * 32, CAP == 1 ? 32 / W : CAP == 2 ? 20 / W 
         const int label = g.labeled ? __ldg(&g.vinfo[v].w) : 0;
         for (int r = 0; r < a.n_roots; ++r) {
             const PgTrieNode &R = a.nodes[r];
-            if (R.spec.label >= 0 && R.spec.label != label) continue;
+            if (R.group != grp || (R.spec.label >= 0 && R.spec.label != label)) continue;
             if (lane == 0 && part == 0)
                 for (int t = 0; t < R.n_terms; ++t) add_slot(acc, a.terms[R.first_term + t].slot, 1);
             if (R.n_children == 0) continue;
@@ -297,6 +309,8 @@ struct pg_batch {
     std::vector<PgTrieNode> nodes;
     std::vector<PgTrieTerm> terms;
     int n_roots = 0;
+    int n_groups = 1;           // task groups (one per counted pattern unless prefixes are shared)
+    bool share_prefixes = false;
     int n_slots = 0;
     int n_programs = 0;
     int n_levels_total = 0;     // sum over programs of their levels
@@ -432,6 +446,7 @@ int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out
         }
         bb->out_n.push_back((int)bb->term_slot.size() - bb->out_first.back());
     }
+    bb->share_prefixes = (flags & PG_BATCH_SHARE_PREFIXES) != 0;
     int rc = pg_batch_build_trie(bb);
     if (!rc && !(flags & PG_BATCH_HOST_ONLY)) rc = pg_batch_upload(bb);
     if (rc) { pg_batch_free(bb); return rc; }
@@ -467,7 +482,8 @@ int pg_batch_build_trie(pg_batch *b) {
         std::vector<PgTrieTerm> terms;
     };
     std::vector<TNode> t;
-    std::vector<int> roots;
+    std::vector<int> roots, root_group;
+    int n_groups = 0;
     for (int i = 0; i < PGP_MAXK; ++i) b->out_bounded[i] = true;
     b->n_slots = n_plans;
     b->clique_k.assign(n_plans, 0);
@@ -486,6 +502,11 @@ int pg_batch_build_trie(pg_batch *b) {
             b->c4_slot = p;
             continue;
         }
+        // programs of one pattern always share prefixes; of different
+        // patterns only with share_prefixes (else each pattern is a task
+        // group of its own, walked over all start vertices in turn)
+        const int grp = b->share_prefixes ? 0 : n_groups;
+        n_groups = b->share_prefixes ? 1 : n_groups + 1;
         for (const PgOrder &o : b->slot_plans[p].orders) {
             b->n_programs++;
             b->n_levels_total += o.n_levels;
@@ -494,12 +515,13 @@ int pg_batch_build_trie(pg_batch *b) {
             root_spec.group = 1;
             root_spec.label = o.lv[0].label;
             int cur = -1;
-            for (int r : roots)
-                if (same_spec(t[r].spec, root_spec)) cur = r;
+            for (size_t i = 0; i < roots.size(); ++i)
+                if (root_group[i] == grp && same_spec(t[roots[i]].spec, root_spec)) cur = roots[i];
             if (cur < 0) {
                 t.push_back({root_spec, 0, {}, {}});
                 cur = (int)t.size() - 1;
                 roots.push_back(cur);
+                root_group.push_back(grp);
             }
             for (int l = 1; l < o.n_levels; ++l) {
                 const PgLevel spec = normalized(o.lv[l]);
@@ -549,9 +571,11 @@ int pg_batch_build_trie(pg_batch *b) {
             if (pos[n.kids[k]] != d.first_child + (int)k) return pg_set_error(PG_EINVAL, "internal: trie layout");
         d.first_term = (int)b->terms.size();
         d.n_terms = (int)n.terms.size();
+        d.group = i < roots.size() ? root_group[i] : 0;
         for (auto &tm : n.terms) b->terms.push_back(tm);
     }
     b->n_roots = (int)roots.size();
+    b->n_groups = std::max(1, n_groups);
     return PG_OK;
 }
 
@@ -684,6 +708,7 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.nodes = b->d_nodes;
     a.terms = b->d_terms;
     a.n_roots = b->n_roots;
+    a.n_groups = b->n_groups;
     a.n_slots = b->n_slots;
     a.scratch = (int *)g->ex->scratch;
     a.warp_stride = batch_layout(g, b, a.lvl_off);
@@ -700,7 +725,7 @@ int pg_launch_batched(pg_graph *g, const pg_batch *b, unsigned long long *counts
     a.counts = b->d_slot_counts;
     a.ctl = ctl ? *ctl : PgRunCtl{};
     PG_CUDA(cudaMemsetAsync(b->d_slot_counts, 0, 2 * sizeof(unsigned long long) * (size_t)b->n_slots, s));
-    if (b->n_roots > 0) {
+    if (b->n_roots > 0 && a.n_tasks > 0) {
         PG_CUDA(cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), s));
         void *args[] = {&a};
         PG_CUDA(cudaLaunchKernel(batched_fn(g), dim3(batched_grid(g)), dim3(batched_warps(g) * 32), args, 0, s));

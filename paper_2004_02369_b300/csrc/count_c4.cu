@@ -26,17 +26,18 @@
 //    live in a per-warp open-addressing hash table in shared memory sized
 //    for T_w.  An anchor of degree above kLightDeg, or with more than kLightT
 //    increments, is appended to a deferred list instead;
-//  * dense pass (16-warp CTAs, no shared tables, so more resident warps to
-//    cover the atomics' latency): deferred anchors one per CTA; the counters
-//    are a dense n-entry array per CTA in global memory.  Each entry holds a
-//    12-bit anchor epoch and a 20-bit count; an increment from a newer epoch
-//    restarts the count (compare-and-swap), so no pass clears the counters
-//    between anchors (the array is cleared once when a CTA's epochs wrap).
-//    Graphs with a vertex of degree 2^20 or more use plain atomicAdd counters
-//    cleared by a second walk.
-//  Both walk the suffixes 32 neighbours a at a time: lanes binary-search
-//  their a's suffix start, a warp prefix sum flattens the 32 suffixes, and
-//  lanes read the flattened increments with coalesced loads.
+//  * tiled pass (16-warp CTAs, two per SM): deferred anchors one per CTA.
+//    The counters of x in (w, n) are kept in shared memory one x-range tile
+//    at a time (96 KB: 49,152 16-bit counters when the anchor has fewer than
+//    2^16 neighbours above it, else 24,576 32-bit ones); each tile takes,
+//    from every neighbour's suffix, the elements inside the tile (a per
+//    neighbour cursor in global memory, advanced by a galloping search), so
+//    every suffix element is read once and every increment is a shared-memory
+//    atomic; the tile is cleared before the next.  No counter lives in
+//    global memory.
+//  Both walk the suffixes 32 neighbours a at a time: lanes search their a's
+//  suffix start, a warp prefix sum flattens the 32 suffixes, and lanes read
+//  the flattened increments with coalesced loads.
 #include <mutex>
 
 #include "device_sets.cuh"
@@ -45,7 +46,9 @@ namespace {
 
 constexpr int kWarps = 4;
 constexpr int kBlock = kWarps * 32;   // light pass
-constexpr int kDenseBlock = 512;      // dense pass
+constexpr int kTileBlock = 512;       // tiled pass
+constexpr int kTileWords = 24576;     // 96 KB of counters per tiled CTA
+constexpr size_t kTileSmem = (size_t)kTileWords * sizeof(unsigned);
 constexpr int kLightDeg = 256;        // light anchors: degree <= kLightDeg
 constexpr int kHashCap = 1024;        // per-warp hash slots (power of two)
 constexpr int kLightT = kHashCap / 2; // light anchors: at most this many increments
@@ -54,8 +57,8 @@ constexpr int kEmpty = -1;
 struct C4Args {
     DevGraph g;
     int n;
-    int epochs;             // 1: epoch-tagged dense counters (all degrees below 2^20)
-    unsigned *dense;        // per-CTA counter arrays of n entries, all zero between anchors
+    unsigned *cursors;      // per tiled CTA: cur_stride suffix cursors (absolute adj indices)
+    long long cur_stride;
     int *deferred;          // anchors left to the CTAs
     unsigned long long *q;  // [0] warp cursor, [1] deferred count, [2] deferred cursor
     unsigned long long *count; // (low, high)
@@ -117,22 +120,31 @@ __device__ __forceinline__ void walk_chunk(const DevGraph &g, unsigned my_start,
     }
 }
 
-// Counter x of the current epoch ep (1..4095): raise it, return its count
-// before (0 when it held an older epoch).
-__device__ __forceinline__ unsigned epoch_inc(unsigned *c, unsigned ep) {
-    unsigned cur = *(volatile unsigned *)c;
-    for (;;) {
-        const bool mine = (cur >> 20) == ep;
-        const unsigned nv = mine ? cur + 1u : (ep << 20) | 1u;
-        const unsigned prev = atomicCAS(c, cur, nv);
-        if (prev == cur) return mine ? (cur & 0xFFFFFu) : 0u;
-        cur = prev; // another increment got there first: retry on its value
+// First index i in [p, end) with adj[i] >= v (end if none), galloping from
+// p: cheap when few elements precede v.
+__device__ __forceinline__ unsigned gallop_lb(const int *__restrict__ adj, unsigned p, unsigned end, int v) {
+    if (p >= end || __ldg(adj + p) >= v) return p;
+    unsigned lo = p, step = 1, hi = p + 1; // adj[lo] < v
+    while (hi < end && __ldg(adj + hi) < v) {
+        lo = hi;
+        step <<= 1;
+        hi = lo + step;
     }
+    if (hi > end) hi = end; // the answer lies in (lo, hi]
+    ++lo;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (__ldg(adj + mid) < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
-// Heavy anchor w by the whole CTA on the dense counters C (epoch ep when
-// a.epochs).  Returns this thread's share of the anchored count.
-__device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, int *s_next, int *s_p, unsigned ep) {
+// Heavy anchor w by the whole CTA, x-range tile by x-range tile, on the
+// shared counters T; cur: this CTA's cursors.  Returns this thread's share
+// of the anchored count; stops early (partial) when the run control says so
+// (*s_stop set).
+__device__ unsigned long long tiled_anchor(const C4Args &a, int w, unsigned *T, unsigned *cur, int *s_next,
+                                           int *s_p, int *s_stop) {
     const DevGraph &g = a.g;
     const int lane = threadIdx.x & 31;
     const int4 wi = __ldg(&g.vinfo[w]);
@@ -143,9 +155,19 @@ __device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, 
     }
     __syncthreads();
     const int p = *s_p, na = wi.y - p;
+    if (na < 2) return 0; // uniform across the CTA
+    const bool packed = na < 65536; // a counter never exceeds na
+    const int R = packed ? 2 * kTileWords : kTileWords;
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        const int4 ai = __ldg(&g.vinfo[__ldg(aw + p + i)]);
+        cur[i] = ((unsigned)ai.x << 2) + (unsigned)upper_bound_g(adj_of(g, ai), ai.y, w);
+    }
+    for (int i = threadIdx.x; i < kTileWords; i += blockDim.x) T[i] = 0u;
+    __syncthreads();
     unsigned long long cnt = 0;
-    const int passes = a.epochs ? 1 : 2;
-    for (int pass = 0; pass < passes; ++pass) {
+    for (long long t0 = (long long)w + 1; t0 < a.n; t0 += R) {
+        const int lo = (int)t0;
+        const int hi = (int)min((long long)a.n, t0 + R);
         for (;;) {
             int c = 0;
             if (lane == 0) c = atomicAdd(s_next, 32);
@@ -153,17 +175,31 @@ __device__ unsigned long long dense_anchor(const C4Args &a, int w, unsigned *C, 
             if (c >= na) break;
             unsigned st = 0;
             int ln = 0;
-            if (c + lane < na) suffix_of(g, __ldg(aw + p + c + lane), w, &st, &ln);
-            if (a.epochs)
-                walk_chunk(g, st, ln, lane, [&](int x) { cnt += epoch_inc(C + x, ep); });
-            else if (pass == 0)
-                walk_chunk(g, st, ln, lane, [&](int x) { cnt += atomicAdd(C + x, 1u); });
+            if (c + lane < na) {
+                const int4 ai = __ldg(&g.vinfo[__ldg(aw + p + c + lane)]);
+                st = cur[c + lane];
+                const unsigned e = gallop_lb(g.adj, st, ((unsigned)ai.x << 2) + (unsigned)ai.y, hi);
+                ln = (int)(e - st);
+                cur[c + lane] = e;
+            }
+            // every element lies in [lo, hi): the previous tile ended at lo
+            if (packed)
+                walk_chunk(g, st, ln, lane, [&](int x) {
+                    const unsigned i = (unsigned)(x - lo), sh = (i & 1u) << 4;
+                    cnt += (atomicAdd(T + (i >> 1), 1u << sh) >> sh) & 0xFFFFu;
+                });
             else
-                walk_chunk(g, st, ln, lane, [&](int x) { C[x] = 0u; });
+                walk_chunk(g, st, ln, lane, [&](int x) { cnt += atomicAdd(T + (x - lo), 1u); });
         }
         __syncthreads();
-        if (threadIdx.x == 0) *s_next = 0;
+        if (threadIdx.x == 0) {
+            *s_next = 0;
+            *s_stop = a.ctl.words && ctl_poll(a.ctl) ? 1 : 0;
+        }
+        if (hi < a.n)
+            for (int i = threadIdx.x; i < kTileWords; i += blockDim.x) T[i] = 0u;
         __syncthreads();
+        if (*s_stop) break;
     }
     return cnt;
 }
@@ -252,16 +288,16 @@ __global__ void __launch_bounds__(kBlock) k_c4_light(C4Args a) {
     if (lane == 0 && tot) atomic_add_u128(a.count, tot);
 }
 
-// Dense pass: one CTA per deferred anchor on its dense counter array.
-__global__ void __launch_bounds__(kDenseBlock) k_c4_dense(C4Args a) {
-    __shared__ int s_task, s_next, s_p;
+// Tiled pass: one CTA per deferred anchor, counters in shared memory.
+__global__ void __launch_bounds__(kTileBlock) k_c4_tiled(C4Args a) {
+    extern __shared__ __align__(16) unsigned tile[];
+    __shared__ int s_task, s_next, s_p, s_stop;
     const int lane = threadIdx.x & 31;
     const bool polled = a.ctl.words != nullptr;
     if (polled && threadIdx.x == 0) ctl_begin(a.ctl);
     unsigned long long cnt = 0;
-    unsigned *C = a.dense + (size_t)blockIdx.x * (size_t)a.n;
+    unsigned *cur = a.cursors + (size_t)blockIdx.x * (size_t)a.cur_stride;
     const unsigned long long n_def = *(volatile unsigned long long *)(a.q + 1);
-    unsigned ep = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             int w = -1;
@@ -270,18 +306,14 @@ __global__ void __launch_bounds__(kDenseBlock) k_c4_dense(C4Args a) {
                 if (t < n_def) w = a.deferred[t];
             }
             s_task = w;
+            s_stop = 0;
         }
         __syncthreads();
         const int w = s_task;
         __syncthreads();
         if (w < 0) break;
-        if (a.epochs && ++ep == 4096) {
-            // epochs wrap: clear this CTA's counters once
-            for (int i = threadIdx.x; i < a.n; i += blockDim.x) C[i] = 0u;
-            __syncthreads();
-            ep = 1;
-        }
-        cnt += dense_anchor(a, w, C, &s_next, &s_p, ep);
+        cnt += tiled_anchor(a, w, tile, cur, &s_next, &s_p, &s_stop);
+        if (s_stop) break;
     }
     const unsigned __int128 tot = warp_sum_u128(cnt);
     if (lane == 0 && tot) atomic_add_u128(a.count, tot);
@@ -295,9 +327,9 @@ constexpr size_t kLightSmem = (size_t)kWarps * sizeof(WarpSmem);
 constexpr int kMaxDevices = 64;
 std::once_flag g_once[kMaxDevices];
 cudaError_t g_err[kMaxDevices];
-int g_light_per_sm[kMaxDevices], g_dense_per_sm[kMaxDevices];
+int g_light_per_sm[kMaxDevices], g_tiled_per_sm[kMaxDevices];
 
-int c4_grids(const pg_graph *g, int *light, int *dense) {
+int c4_grids(const pg_graph *g, int *light, int *tiled) {
     const int dev = g->device;
     if (dev < 0 || dev >= kMaxDevices) return pg_set_error(PG_EINVAL, "device index out of range");
     std::call_once(g_once[dev], [dev] {
@@ -309,22 +341,25 @@ int c4_grids(const pg_graph *g, int *light, int *dense) {
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_light_per_sm[dev], k_c4_light, kBlock, kLightSmem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_dense_per_sm[dev], k_c4_dense, kDenseBlock, 0);
+            e = cudaFuncSetAttribute(k_c4_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tiled_per_sm[dev], k_c4_tiled, kTileBlock, kTileSmem);
         cudaSetDevice(prev);
         g_err[dev] = e;
     });
     if (g_err[dev] != cudaSuccess) return pg_cuda_error(g_err[dev], "4-cycle kernel set-up");
     *light = std::max(1, g_light_per_sm[dev]) * g->num_sms;
-    *dense = std::max(1, g_dense_per_sm[dev]) * g->num_sms;
+    *tiled = std::max(1, g_tiled_per_sm[dev]) * g->num_sms;
     return PG_OK;
 }
 
 }  // namespace
 
 size_t pg_c4_scratch_bytes(const pg_graph *g) {
-    int light = 0, dense = 0;
-    if (c4_grids(g, &light, &dense) != PG_OK) dense = 4 * g->num_sms;
-    return (size_t)dense * (size_t)g->n * sizeof(unsigned) + (size_t)(g->n + 1) * sizeof(int) + 256;
+    int light = 0, tiled = 0;
+    if (c4_grids(g, &light, &tiled) != PG_OK) tiled = 2 * g->num_sms;
+    const size_t cur = (size_t)tiled * (size_t)((g->max_deg + 31) & ~31ll) * sizeof(unsigned);
+    return cur + (size_t)(g->n + 1) * sizeof(int) + 256;
 }
 
 // Adds the number of edge-induced 4-cycles of g into count_dev (128-bit,
@@ -334,28 +369,26 @@ int pg_launch_c4(pg_graph *g, unsigned long long *count_dev, int queue_slot, cud
     if (g->n < 4) return PG_OK;
     if (queue_slot + 3 > PG_CTL_WORDS_SLOT) return pg_set_error(PG_EINVAL, "queue slot out of range");
     if (g->adj_entries >= (1ll << 32)) return pg_set_error(PG_EUNSUPPORTED, "4-cycle kernel: adjacency above 2^32 entries");
-    int light = 0, dense = 0;
-    int rc = c4_grids(g, &light, &dense);
+    int light = 0, tiled = 0;
+    int rc = c4_grids(g, &light, &tiled);
     if (rc) return rc;
-    const size_t dense_bytes = (size_t)dense * (size_t)g->n * sizeof(unsigned);
     if (pg_c4_scratch_bytes(g) > g->ex->scratch_bytes) return pg_set_error(PG_ENOMEM, "scratch smaller than the 4-cycle kernel needs");
     C4Args a;
     a.g = g->d;
     a.n = (int)g->n;
-    a.epochs = g->max_deg < (1ll << 20) ? 1 : 0;
-    a.dense = (unsigned *)g->ex->scratch;
-    a.deferred = (int *)((unsigned char *)g->ex->scratch + dense_bytes);
+    a.cur_stride = (g->max_deg + 31) & ~31ll;
+    a.cursors = (unsigned *)g->ex->scratch;
+    a.deferred = (int *)((unsigned char *)g->ex->scratch + (size_t)tiled * (size_t)a.cur_stride * sizeof(unsigned));
     a.q = g->ex->queues + queue_slot;
     a.count = count_dev;
     const PgTaskSel sel = pg_task_sel(g);
     a.stride = sel.stride;
     a.offset = sel.offset;
     a.ctl = ctl ? *ctl : PgRunCtl{};
-    PG_CUDA(cudaMemsetAsync(a.dense, 0, dense_bytes, s));
     PG_CUDA(cudaMemsetAsync(a.q, 0, 3 * sizeof(unsigned long long), s));
     k_c4_light<<<light, kBlock, kLightSmem, s>>>(a);
     PG_CUDA(cudaGetLastError());
-    k_c4_dense<<<dense, kDenseBlock, 0, s>>>(a);
+    k_c4_tiled<<<tiled, kTileBlock, kTileSmem, s>>>(a);
     PG_CUDA(cudaGetLastError());
     return PG_OK;
 }

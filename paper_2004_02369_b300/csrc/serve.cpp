@@ -18,6 +18,9 @@
 // oldest waiting query if it must run alone, else a batch of the waiting
 // short queries (which so overtake long ones), so a long query never holds
 // a batch of short ones and short queries are still fused into one launch.
+// With several streams the queries that run alone go one at a time on half
+// of the SMs (a smaller persistent grid), so short batches always find free
+// SMs instead of queueing behind a long launch that fills the GPU.
 //
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
@@ -79,6 +82,7 @@ struct Slot {
     bool dead = false;     // retired after a device error
     std::vector<uint64_t> cancelled; // cancelled queries of the launch in flight
     PgRunCtl ctl;          // run control of the launch in flight
+    bool long_class = false; // the launch in flight runs a query alone (long or unmeasured)
 };
 
 constexpr size_t kAreaBytes = 4u << 20;
@@ -330,6 +334,27 @@ void apply_cancels(pg_server *S) {
     // a ticket found nowhere already has its result: nothing to do
 }
 
+// Waiting queries whose time limit has passed fail now with PG_ETIMEOUT
+// (not when a stream would take them).
+void expire_waiting(pg_server *S) {
+    if (S->cfg.query_timeout_s <= 0) return;
+    std::vector<ServerQuery> gone;
+    const double now = S->now();
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        for (auto it = S->pending.begin(); it != S->pending.end();) {
+            if (S->cfg.query_timeout_s - (now - it->t_submit) <= 0) {
+                gone.push_back(*it);
+                it = S->pending.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+    for (auto &q : gone) emit(S, q, PG_ETIMEOUT, nullptr, now, now, 0);
+    S->outstanding -= (int64_t)gone.size();
+}
+
 // Whether query q must be launched by itself: isolated after a batch ran
 // out of time, an anti-vertex pattern, or a pattern not yet measured or
 // measured longer than the batch limit.
@@ -411,11 +436,14 @@ void worker_loop(pg_server *S) {
                     }
                 }
                 if (timed_out && s.qs.size() > 1) {
-                    // isolate: every query of the batch runs again by itself
+                    // isolate: every query of the batch runs again by itself,
+                    // first with a quarter of the time it has left (the slow
+                    // one then goes to the back of the queue)
                     std::lock_guard<std::mutex> lock(S->mu);
                     for (size_t i = s.qs.size(); i-- > 0;) {
                         ServerQuery q = s.qs[i];
                         q.alone = true;
+                        q.cap_s = 0.25 * (S->cfg.query_timeout_s - (t - q.t_submit));
                         S->pending.push_front(q);
                     }
                     pg_batch_free(s.batch);
@@ -436,16 +464,25 @@ void worker_loop(pg_server *S) {
             s.busy = false;
             progress = true;
         }
+        expire_waiting(S);
+        // With several streams, queries that run alone (long, unmeasured or
+        // isolated ones) run one at a time on half of the SMs, so that a
+        // persistent launch of a long query never holds every SM while short
+        // queries wait: their batches take the other half.
+        const bool multi = S->slots.size() > 1;
+        bool long_busy = false;
+        for (Slot &s : S->slots) long_busy |= s.busy && s.long_class;
         bool any_alive = false;
         for (Slot &s : S->slots) {
             any_alive |= !s.dead;
             if (s.busy || s.dead) continue;
             std::vector<ServerQuery> take;
+            bool is_long = false;
             {
                 std::lock_guard<std::mutex> lock(S->mu);
                 if (!S->pending.empty()) {
                     ServerQuery &f = S->pending.front();
-                    if (max_batch == 1 || goes_alone(S, f)) {
+                    if ((max_batch == 1 || goes_alone(S, f)) && !(multi && long_busy)) {
                         // the oldest query runs by itself: isolated, measuring
                         // its pattern, known long, or anti-vertex
                         if (!S->cfg.serial && S->cfg.query_timeout_s > 0 && !f.requeued && !f.alone &&
@@ -453,7 +490,8 @@ void worker_loop(pg_server *S) {
                             f.cap_s = 0.25 * S->cfg.query_timeout_s;
                         take.push_back(f);
                         S->pending.pop_front();
-                    } else {
+                        is_long = true;
+                    } else if (max_batch > 1) {
                         // a batch of the waiting short queries, oldest first
                         for (auto it = S->pending.begin(); it != S->pending.end() && (int)take.size() < max_batch;) {
                             if (goes_alone(S, *it)) {
@@ -467,7 +505,10 @@ void worker_loop(pg_server *S) {
                 }
             }
             if (take.empty()) break;
+            s.view.num_sms = is_long && multi ? std::max(1, S->g->num_sms / 2) : S->g->num_sms;
             launch_batch(S, s, take);
+            s.long_class = is_long && s.busy;
+            long_busy |= s.long_class;
             progress = true;
             if (S->cfg.serial) break;
         }

@@ -2,7 +2,8 @@
 every batch) against the oracle, bit-exact: the oracle's co-degree formula
 S(C4) = 1/2 sum over pairs of C(codeg, 2), its backtracking count on small
 graphs, and closed forms (K_n: 3 C(n, 4); K_{p,q}: C(p, 2) C(q, 2)).  Graphs
-with hubs above 512 neighbours exercise the deferred whole-CTA path."""
+with hubs above 256 neighbours exercise the deferred whole-CTA path (its
+x-range tiles of shared-memory counters, 16- and 32-bit)."""
 from math import comb
 
 import pytest
@@ -56,6 +57,18 @@ def test_c4_closed_forms(pg):
         assert pg.count(G, [plan]) == [comb(p_, 2) * comb(q_, 2)]
     star = sg.from_edges(2001, [(0, i) for i in range(1, 2001)])
     assert pg.count(pg.Graph.from_synth(star), [plan]) == [0]
+
+
+def test_c4_counter_widths_and_tiles(pg):
+    """K_{p,q} with the p side as anchors of q neighbours each: q = 65,535
+    keeps 16-bit counters at their largest value (the counter of the other
+    p vertex reaches q), q = 70,000 takes 32-bit counters; both span several
+    x-range tiles of the shared-memory pass."""
+    plan = pg.Plan.from_dict(C4)
+    for p_, q_ in ((2, 65535), (2, 70000), (3, 66000)):
+        edges = [(i, p_ + j) for i in range(p_) for j in range(q_)]
+        G = pg.Graph.from_synth(sg.from_edges(p_ + q_, edges))
+        assert pg.count(G, [plan]) == [comb(p_, 2) * comb(q_, 2)]
 
 
 def test_c4_in_mixed_batch_and_interpreter_agree(pg):
