@@ -967,7 +967,7 @@ def run_fsm(args):
 
 def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, labeled_only=("C5",),
                 query_timeout_s: float = 0.0, alone_only: bool = False, alone_budget_ms: float = 0.0,
-                types=None) -> dict:
+                types=None, alone_fractions=(0.5,)) -> dict:
     """Poisson streams of count queries over a resident R-MAT graph (the
     survey's mix, 10% labeled over 8 labels): continuous batching (4
     streams, up to 32 queries per launch) against the same kernels one query
@@ -1045,7 +1045,11 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
     for f in lambdas:
         arrivals = sg.poisson_arrivals(len(qs), f * capacity, seed=sg.SEED_BASE + int(100 * f))
         row = {"lambda_x_capacity": f, "rate_qps": f * capacity}
-        for mode, kw in (("serial", dict(serial=True)), ("batched", dict(n_streams=4, max_batch=32))):
+        modes = [("serial", dict(serial=True))]
+        for fr in alone_fractions:
+            modes.append(("batched" if fr == 0.5 else f"batched_alone_sm{fr:g}",
+                          dict(n_streams=4, max_batch=32, alone_sm_fraction=fr)))
+        for mode, kw in modes:
             srv = pg.Server(G, query_timeout_s=query_timeout_s, **kw)
             out, st = drive(srv, arrivals)
             srv.close()
@@ -1062,7 +1066,9 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
             "graph": {"n": g.n, "m": g.m, "max_degree": int(g.meta["max_degree"])},
             "queries": len(qs), "types": types, "labeled_fraction": 0.1, "labeled_only": list(labeled_only),
             "arrivals": "Poisson, rate = lambda x measured serial capacity",
-            "batched": "4 streams, up to 32 queries per launch", "serial_capacity_qps": capacity,
+            "batched": "4 streams, up to 32 queries per launch; a pattern's first query and patterns longer "
+                       "than 20 ms alone run alone, one at a time, on a share of the SMs (0.5 unless the mode "
+                       "name says otherwise)", "serial_capacity_qps": capacity,
             "alone_ms": alone_ms, "runs": runs, "mix_equals_alone": True,
             "query_timeout_s": query_timeout_s}
 
@@ -1089,7 +1095,7 @@ def run_serving(args):
     line = serving_run(pg, args.serve_scale, args.serve_n, args.serve_lambdas, args.serve_timeout,
                        labeled_only=tuple(args.serve_labeled_only), query_timeout_s=args.serve_query_timeout,
                        alone_only=args.serve_alone_only, alone_budget_ms=args.serve_alone_budget_ms,
-                       types=args.serve_types)
+                       types=args.serve_types, alone_fractions=tuple(args.serve_alone_fractions))
     line.update({"n_gpus": 1, "data": "synthetic"})
     print(json.dumps(line), flush=True)
     return 0
@@ -1121,6 +1127,8 @@ def main():
     ap.add_argument("--serve-alone-budget-ms", type=float, default=0.0,
                     help="device work budget of each alone measurement (0: none)")
     ap.add_argument("--serve-types", nargs="*", default=None, help="query types of the mix (default: all)")
+    ap.add_argument("--serve-alone-fractions", type=float, nargs="+", default=[0.5],
+                    help="SM shares of alone-running queries, one batched run each")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
     ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")
     ap.add_argument("--tuning-json", default=None,

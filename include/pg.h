@@ -718,6 +718,11 @@ typedef struct {
     double batch_limit_ms;  /* > 0: a pattern whose query took longer than
                                this alone is not batched again; 0: 20 ms;
                                < 0: no measuring, any query may be batched */
+    double alone_sm_fraction; /* with n_streams > 1, queries that run alone
+                               (long, unmeasured, isolated) go one at a time
+                               on this fraction of the SMs (a smaller
+                               persistent grid), leaving the rest to batches
+                               of short queries; (0, 1], 0: 0.5 */
 } pg_server_config;
 
 typedef struct {

@@ -609,7 +609,8 @@ def labeled_motif3(graph: Graph, stream=None) -> dict:
 class ServerConfig(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("memory_budget", ctypes.c_int64), ("serial", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("query_timeout_s", ctypes.c_double), ("batch_limit_ms", ctypes.c_double)]
+                ("query_timeout_s", ctypes.c_double), ("batch_limit_ms", ctypes.c_double),
+                ("alone_sm_fraction", ctypes.c_double)]
 
 
 class QueryResult(ctypes.Structure):
@@ -629,10 +630,11 @@ class Server:
     """Request loop over a resident graph (native worker thread, see pg.h)."""
 
     def __init__(self, graph: Graph, n_streams: int = 4, max_batch: int = 32, memory_budget: int = 0,
-                 serial: bool = False, query_timeout_s: float = 0.0, batch_limit_ms: float = 0.0):
+                 serial: bool = False, query_timeout_s: float = 0.0, batch_limit_ms: float = 0.0,
+                 alone_sm_fraction: float = 0.0):
         self.graph = graph  # keep the graph alive
         cfg = ServerConfig(n_streams, max_batch, memory_budget, 1 if serial else 0, 0, float(query_timeout_s),
-                           float(batch_limit_ms))
+                           float(batch_limit_ms), float(alone_sm_fraction))
         h = _vp()
         _check(_lib.pg_server_create(graph.handle, ctypes.byref(cfg), ctypes.byref(h)))
         self._h = h

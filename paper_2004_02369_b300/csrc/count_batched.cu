@@ -125,8 +125,7 @@ __global__ void __launch_bounds__(W * 32, CAP == 1 ? 32 / W : CAP == 2 ? 20 / W 
             if (lane == 0) t = atomicAdd(a.queue, (unsigned long long)a.chunk);
             task = (long long)__shfl_sync(PG_FULL, t, 0);
             if (task >= a.n_groups * a.n_tasks) break;
-            // a grab stays inside one group
-            task_end = min(task + a.chunk, (task / a.n_tasks + 1) * a.n_tasks);
+            task_end = min(task + a.chunk, a.n_groups * a.n_tasks); // may cross into the next group
         }
         const int grp = (int)(task / a.n_tasks);
         const long long tg = a.offset + (task - grp * a.n_tasks) * a.stride;

@@ -18,9 +18,10 @@
 // oldest waiting query if it must run alone, else a batch of the waiting
 // short queries (which so overtake long ones), so a long query never holds
 // a batch of short ones and short queries are still fused into one launch.
-// With several streams the queries that run alone go one at a time on half
-// of the SMs (a smaller persistent grid), so short batches always find free
-// SMs instead of queueing behind a long launch that fills the GPU.
+// With several streams the queries that run alone go one at a time on a
+// share of the SMs (a smaller persistent grid; half by default), so short
+// batches always find free SMs instead of queueing behind a long launch that
+// fills the GPU.
 //
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
@@ -108,6 +109,7 @@ struct pg_server {
     std::vector<uint64_t> cancelled;     // tickets to cancel (worker applies them)
     std::unordered_map<const pg_plan *, PatternCost> cost; // worker thread only
     double batch_limit_s = 0.02;         // < 0: batch everything
+    double alone_share = 0.5;            // share of the SMs for queries that run alone
     cudaStream_t ctl_stream = nullptr;   // raises stop words of running launches
     unsigned long long *h_one = nullptr; // pinned host word holding 1: the source of those
                                          // copies (host-to-device, done by a copy engine
@@ -466,9 +468,9 @@ void worker_loop(pg_server *S) {
         }
         expire_waiting(S);
         // With several streams, queries that run alone (long, unmeasured or
-        // isolated ones) run one at a time on half of the SMs, so that a
+        // isolated ones) run one at a time on a share of the SMs, so that a
         // persistent launch of a long query never holds every SM while short
-        // queries wait: their batches take the other half.
+        // queries wait: their batches take the rest.
         const bool multi = S->slots.size() > 1;
         bool long_busy = false;
         for (Slot &s : S->slots) long_busy |= s.busy && s.long_class;
@@ -505,7 +507,7 @@ void worker_loop(pg_server *S) {
                 }
             }
             if (take.empty()) break;
-            s.view.num_sms = is_long && multi ? std::max(1, S->g->num_sms / 2) : S->g->num_sms;
+            s.view.num_sms = is_long && multi ? std::max(1, (int)(S->g->num_sms * S->alone_share)) : S->g->num_sms;
             launch_batch(S, s, take);
             s.long_class = is_long && s.busy;
             long_busy |= s.long_class;
@@ -526,6 +528,8 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
     if (!g || !cfg || !out) return pg_set_error(PG_EINVAL, "NULL argument");
     if (!(cfg->query_timeout_s >= 0.0)) return pg_set_error(PG_EINVAL, "query_timeout_s must be >= 0");
     if (cfg->batch_limit_ms != cfg->batch_limit_ms) return pg_set_error(PG_EINVAL, "batch_limit_ms is NaN");
+    if (!(cfg->alone_sm_fraction >= 0.0) || cfg->alone_sm_fraction > 1.0)
+        return pg_set_error(PG_EINVAL, "alone_sm_fraction must lie in [0, 1]");
     *out = nullptr;
     pg_server *S = new (std::nothrow) pg_server();
     if (!S) return pg_set_error(PG_ENOMEM, "host allocation failed");
@@ -534,6 +538,7 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
     S->cfg = *cfg;
     if (cfg->batch_limit_ms > 0) S->batch_limit_s = cfg->batch_limit_ms * 1e-3;
     if (cfg->batch_limit_ms < 0) S->batch_limit_s = -1;
+    if (cfg->alone_sm_fraction > 0) S->alone_share = std::min(1.0, cfg->alone_sm_fraction);
     S->t0 = std::chrono::steady_clock::now();
     const int n_streams = cfg->serial ? 1 : std::max(1, std::min(cfg->n_streams, 16));
     int rc = PG_OK;

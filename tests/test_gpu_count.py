@@ -192,7 +192,11 @@ def test_batched_matches_generic_and_oracle(pg):
     plans = [pg.Plan.from_dict(p) for p in pats]
     batch = pg.Batch(plans)
     info = batch.info()
-    assert info["nodes"] < info["levels_total"]  # prefixes are shared
+    assert info["nodes"] < info["levels_total"]  # prefixes are shared within a pattern
+    shared = pg.Batch(plans, share_prefixes=True)
+    assert shared.info()["nodes"] < info["nodes"]  # and across patterns in one tree
+    out_s = torch.zeros(2 * len(plans), dtype=torch.int64, device="cuda")
+    pg.count_batch(G, shared, out_s)
     direct_info = pg.Batch(plans, expand_anti_edges=False).info()
     # unlabeled k-cliques are counted by the clique kernel, outside the tree
     is_clique = [p["k"] >= 3 and len(p["edges"]) == p["k"] * (p["k"] - 1) // 2 for p in pats]
@@ -202,6 +206,7 @@ def test_batched_matches_generic_and_oracle(pg):
     pg.count_batch(G, batch, out)
     torch.cuda.synchronize()
     got = pg.decode_counts(out)
+    assert pg.decode_counts(out_s) == got
     out2 = torch.zeros_like(out)
     pg.count_async(G, plans, out2, kernel=pg.KERNEL_GENERIC)
     torch.cuda.synchronize()

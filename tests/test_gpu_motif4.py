@@ -1,6 +1,7 @@
 """GPU parity of the fused batched launch for the six induced 4-vertex
 motifs (R-MAT scale 20, edge factor 16) against oracle-written counts, and
-of its two evaluation strategies against each other at a smaller scale."""
+of its evaluation strategies (anti-edges expanded or as set differences;
+one task group per pattern or one shared prefix tree) at a smaller scale."""
 import json
 import os
 
@@ -19,9 +20,9 @@ def pg(cuda_device):
     return pg
 
 
-def _batch_counts(pg, G, plans, expand):
+def _batch_counts(pg, G, plans, expand, share=False):
     import torch
-    b = pg.Batch(plans, expand_anti_edges=expand)
+    b = pg.Batch(plans, expand_anti_edges=expand, share_prefixes=share)
     out = torch.zeros(2 * len(plans), dtype=torch.int64, device="cuda")
     pg.count_batch(G, b, out)
     torch.cuda.synchronize()
@@ -36,6 +37,9 @@ def test_motif4_small_rmat_both_strategies(pg):
     want = [want[name] for name in sg.MOTIF4_SHAPES]
     assert _batch_counts(pg, G, plans, True) == want
     assert _batch_counts(pg, G, plans, False) == want
+    # one tree for all patterns instead of one task group per pattern
+    assert _batch_counts(pg, G, plans, True, share=True) == want
+    assert _batch_counts(pg, G, plans, False, share=True) == want
     # brute-force definition on the induced patterns themselves
     for p, w in zip(sg.motif4_patterns(), want):
         if p["name"] in ("induced_clique", "induced_diamond", "induced_cycle"):

@@ -34,10 +34,11 @@ def test_all_induced_5_motifs(pg, gi):
     plans = [pg.Plan.from_dict(p) for p in pats]
     assert pg.count(G, plans) == want
     for expand in (True, False):
-        b = pg.Batch(plans, expand_anti_edges=expand)
-        out = torch.zeros(2 * len(plans), dtype=torch.int64, device="cuda")
-        pg.count_batch(G, b, out)
-        assert pg.decode_counts(out) == want, expand
+        for share in (False, True):
+            b = pg.Batch(plans, expand_anti_edges=expand, share_prefixes=share)
+            out = torch.zeros(2 * len(plans), dtype=torch.int64, device="cuda")
+            pg.count_batch(G, b, out)
+            assert pg.decode_counts(out) == want, (expand, share)
     out = torch.zeros(2, dtype=torch.int64, device="cuda")
     for pl, w in zip(plans[::4], want[::4]):
         pg.count_async(G, [pl], out, kernel=pg.KERNEL_GENERIC)
