@@ -967,7 +967,7 @@ def run_fsm(args):
 
 def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, labeled_only=("C5",),
                 query_timeout_s: float = 0.0, alone_only: bool = False, alone_budget_ms: float = 0.0,
-                types=None, alone_fractions=(0.5,)) -> dict:
+                types=None, alone_fractions=(1.0,)) -> dict:
     """Poisson streams of count queries over a resident R-MAT graph (the
     survey's mix, 10% labeled over 8 labels): continuous batching (4
     streams, up to 32 queries per launch) against the same kernels one query
@@ -1047,7 +1047,7 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
         row = {"lambda_x_capacity": f, "rate_qps": f * capacity}
         modes = [("serial", dict(serial=True))]
         for fr in alone_fractions:
-            modes.append(("batched" if fr == 0.5 else f"batched_alone_sm{fr:g}",
+            modes.append(("batched" if fr == 1.0 else f"batched_alone_sm{fr:g}",
                           dict(n_streams=4, max_batch=32, alone_sm_fraction=fr)))
         for mode, kw in modes:
             srv = pg.Server(G, query_timeout_s=query_timeout_s, **kw)
@@ -1067,8 +1067,8 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
             "queries": len(qs), "types": types, "labeled_fraction": 0.1, "labeled_only": list(labeled_only),
             "arrivals": "Poisson, rate = lambda x measured serial capacity",
             "batched": "4 streams, up to 32 queries per launch; a pattern's first query and patterns longer "
-                       "than 20 ms alone run alone, one at a time, on a share of the SMs (0.5 unless the mode "
-                       "name says otherwise)", "serial_capacity_qps": capacity,
+                       "than 20 ms alone run alone (with the waiting queries of the same pattern), one launch at "
+                       "a time, on all SMs unless the mode name gives a share", "serial_capacity_qps": capacity,
             "alone_ms": alone_ms, "runs": runs, "mix_equals_alone": True,
             "query_timeout_s": query_timeout_s}
 
@@ -1127,7 +1127,7 @@ def main():
     ap.add_argument("--serve-alone-budget-ms", type=float, default=0.0,
                     help="device work budget of each alone measurement (0: none)")
     ap.add_argument("--serve-types", nargs="*", default=None, help="query types of the mix (default: all)")
-    ap.add_argument("--serve-alone-fractions", type=float, nargs="+", default=[0.5],
+    ap.add_argument("--serve-alone-fractions", type=float, nargs="+", default=[1.0],
                     help="SM shares of alone-running queries, one batched run each")
     ap.add_argument("--serve-lambdas", type=float, nargs="+", default=[0.5, 0.9, 1.5])
     ap.add_argument("--serve-timeout", type=float, default=600.0, help="seconds to wait for a run's results")

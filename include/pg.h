@@ -719,10 +719,11 @@ typedef struct {
                                this alone is not batched again; 0: 20 ms;
                                < 0: no measuring, any query may be batched */
     double alone_sm_fraction; /* with n_streams > 1, queries that run alone
-                               (long, unmeasured, isolated) go one at a time
-                               on this fraction of the SMs (a smaller
+                               (long, unmeasured, isolated; with the waiting
+                               queries of the same pattern) go one launch at
+                               a time on this fraction of the SMs (a smaller
                                persistent grid), leaving the rest to batches
-                               of short queries; (0, 1], 0: 0.5 */
+                               of short queries; (0, 1], 0: 1 (all SMs) */
 } pg_server_config;
 
 typedef struct {

@@ -18,23 +18,28 @@
 // oldest waiting query if it must run alone, else a batch of the waiting
 // short queries (which so overtake long ones), so a long query never holds
 // a batch of short ones and short queries are still fused into one launch.
-// With several streams the queries that run alone go one at a time on a
-// share of the SMs (a smaller persistent grid; half by default), so short
-// batches always find free SMs instead of queueing behind a long launch that
-// fills the GPU.
+// With several streams the queries that run alone go one at a time
+// (together with the waiting queries of the same pattern, which a batch
+// counts once), optionally on a share of the SMs (a smaller persistent grid),
+// so that short batches find free SMs instead of queueing behind a long
+// launch that fills the GPU.
 //
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
 // the kernels stop when it runs out, so one slow pattern cannot hold a
-// stream indefinitely.  A single query that runs out gets PG_ETIMEOUT.  A
-// batch gets half the least time left among its queries; if it runs out,
-// its queries (it is not known which one was slow) go back to the front of
-// the queue to be launched one by one with the time they have left, which
-// isolates the straggler.  The measuring run of a new pattern gets at most
-// a quarter of the limit; if it runs out, the query goes to the back of the
-// queue with the time it has left, so queries behind it are not held for
-// its whole limit.  A stream whose launch fails with a device error is retired and its queries
-// get PG_EDEVICE; when no stream is left, waiting queries fail the same way.
+// stream indefinitely.  A launch of one pattern (one query, or several
+// queries of the same pattern) gets the least time left among its queries;
+// when it runs out, the queries with more time left than the launch ran go
+// to the back of the queue and the others get PG_ETIMEOUT.  A batch of
+// several patterns gets half the least time left; if it runs out, its
+// queries (it is not known which one was slow) go back to the front of the
+// queue to be launched one by one, first with a quarter of the time they
+// have left, which isolates the straggler.  The measuring run of a new
+// pattern likewise gets at most a quarter of the limit, so queries behind it
+// are not held for its whole limit.  Waiting queries fail with PG_ETIMEOUT as
+// soon as their limit passes.  A stream whose launch fails with a device
+// error is retired and its queries get PG_EDEVICE; when no stream is left,
+// waiting queries fail the same way.
 //
 // Section 5.1 processing model (tasks = start vertices) applied to a stream
 // of patterns; the paper itself runs one mining program at a time.
@@ -64,7 +69,7 @@ struct ServerQuery {
 
 // Measured service time of a pattern (worker thread only).
 struct PatternCost {
-    double alone_s = -1; // last time of a one-query launch; < 0: not measured
+    double alone_s = -1; // last time of a launch of this pattern alone; < 0: not measured
     bool slow = false;   // longer than the batch limit alone, or ran out of time
 };
 
@@ -109,7 +114,7 @@ struct pg_server {
     std::vector<uint64_t> cancelled;     // tickets to cancel (worker applies them)
     std::unordered_map<const pg_plan *, PatternCost> cost; // worker thread only
     double batch_limit_s = 0.02;         // < 0: batch everything
-    double alone_share = 0.5;            // share of the SMs for queries that run alone
+    double alone_share = 1.0;            // share of the SMs for queries that run alone
     cudaStream_t ctl_stream = nullptr;   // raises stop words of running launches
     unsigned long long *h_one = nullptr; // pinned host word holding 1: the source of those
                                          // copies (host-to-device, done by a copy engine
@@ -171,7 +176,8 @@ void drop_expired(pg_server *S, std::vector<ServerQuery> &qs) {
 }
 
 // Work budget of a launch counting qs (ns), 0 without a limit: the smallest
-// remaining query time for a single query; half of it for a batch, so that
+// remaining query time when every query is of one pattern (at most the cap
+// of a measuring run); half of it for a batch of several patterns, so that
 // when a batch runs out every query still has at least half its time to run
 // alone.  False if some query has no time left (reported).
 bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
@@ -179,8 +185,12 @@ bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
     if (S->cfg.query_timeout_s <= 0) return true;
     const double now = S->now();
     double left = 1e300;
-    for (auto &q : qs) left = std::min(left, S->cfg.query_timeout_s - (now - q.t_submit));
-    if (qs.size() > 1) left *= 0.5;
+    bool one_pattern = true;
+    for (auto &q : qs) {
+        left = std::min(left, S->cfg.query_timeout_s - (now - q.t_submit));
+        one_pattern &= q.plan == qs[0].plan;
+    }
+    if (!one_pattern) left *= 0.5;
     else if (qs[0].cap_s > 0 && left > 0) left = std::min(left, qs[0].cap_s);
     if (left <= 0) {
         for (auto &q : qs) emit(S, q, PG_ETIMEOUT, nullptr, now, now, (int)qs.size());
@@ -413,21 +423,34 @@ void worker_loop(pg_server *S) {
                 continue;
             } else {
                 const bool timed_out = *(const unsigned long long *)(s.h_counts + 2 * PG_MAX_QUEUES) != 0;
-                if (s.qs.size() == 1) {
-                    // a one-query launch measures its pattern
+                bool one_pattern = true;
+                for (auto &q : s.qs) one_pattern &= q.plan == s.qs[0].plan;
+                if (one_pattern) {
+                    // a launch of one pattern measures it
+                    const double ran = t - s.t_start;
                     PatternCost &c = S->cost[s.qs[0].plan];
-                    c.alone_s = t - s.t_start;
-                    c.slow = timed_out || (S->batch_limit_s >= 0 && c.alone_s > S->batch_limit_s);
-                    ServerQuery q = s.qs[0];
-                    if (timed_out && q.cap_s > 0 && S->cfg.query_timeout_s - (t - q.t_submit) > 0) {
-                        // the measuring run ran out of its cap: to the back
-                        // of the queue with the time it has left
-                        q.cap_s = 0;
-                        q.requeued = true;
-                        q.alone = true;
+                    c.alone_s = ran;
+                    c.slow = timed_out || (S->batch_limit_s >= 0 && ran > S->batch_limit_s);
+                    if (timed_out) {
+                        // the pattern needs more than this launch had: its
+                        // queries with more time left than that go to the
+                        // back of the queue (uncapped), the others fail
+                        std::vector<ServerQuery> again;
+                        for (auto &q : s.qs) {
+                            if (S->cfg.query_timeout_s - (t - q.t_submit) > ran) {
+                                ServerQuery r = q;
+                                r.cap_s = 0;
+                                r.requeued = true;
+                                r.alone = false;
+                                again.push_back(r);
+                            } else {
+                                emit(S, q, PG_ETIMEOUT, nullptr, s.t_start, t, (int)s.qs.size());
+                                S->outstanding--;
+                            }
+                        }
                         {
                             std::lock_guard<std::mutex> lock(S->mu);
-                            S->pending.push_back(q);
+                            for (auto &r : again) S->pending.push_back(r);
                         }
                         pg_batch_free(s.batch);
                         s.batch = nullptr;
@@ -493,6 +516,17 @@ void worker_loop(pg_server *S) {
                         take.push_back(f);
                         S->pending.pop_front();
                         is_long = true;
+                        // waiting queries of the same pattern ride along: a
+                        // batch counts each distinct pattern once
+                        if (max_batch > 1 && !take[0].plan->h.anti_vertices && !take[0].alone)
+                            for (auto it = S->pending.begin(); it != S->pending.end() && (int)take.size() < max_batch;) {
+                                if (it->plan == take[0].plan && !it->alone) {
+                                    take.push_back(*it);
+                                    it = S->pending.erase(it);
+                                } else {
+                                    ++it;
+                                }
+                            }
                     } else if (max_batch > 1) {
                         // a batch of the waiting short queries, oldest first
                         for (auto it = S->pending.begin(); it != S->pending.end() && (int)take.size() < max_batch;) {
