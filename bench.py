@@ -696,6 +696,11 @@ def _cfg_motif4(pg, dev, args) -> dict:
     c4_out = torch.zeros(2, dtype=torch.int64, device=dev)
     pg.count_batch(G, c4, c4_out)
     c4_ms = _timed(lambda: pg.count_batch(G, c4, c4_out), stream, flush)
+    # the prefix-tree kernel's part of the step: the other edge-induced terms
+    tree = pg.Batch([pg.Plan(4, sg.MOTIF4_SHAPES[k]) for k in ("path", "star", "tailed_triangle", "diamond")])
+    tree_out = torch.zeros(8, dtype=torch.int64, device=dev)
+    pg.count_batch(G, tree, tree_out)
+    tree_ms = _timed(lambda: pg.count_batch(G, tree, tree_out), stream, flush)
     matches = sum(got)
     e2e = _e2e(pg, g, lambda G2: pg.count(G2, plans), reps=2)
     if e2e["result"] != got:
@@ -710,7 +715,13 @@ def _cfg_motif4(pg, dev, args) -> dict:
             "roofline": hbm_roofline("k_c4_tiled", 4 * inc, c4_ms,
                                      "4 B x adjacency elements the co-degree pass reads (neighbour suffixes "
                                      "above each anchor); timed: the 4-cycle term alone",
-                                     {"share_of_fused_step": c4_ms / fused_ms})}
+                                     {"share_of_fused_step": c4_ms / fused_ms,
+                                      "dominant_kernel": {
+                                          "kernel": "k_count_batched", "ms": tree_ms,
+                                          "share_of_fused_step": tree_ms / fused_ms,
+                                          "terms": "edge-induced path, star, tailed triangle, diamond",
+                                          "bound": "latency of the binary-search loads of its set operations "
+                                                   "(graph L2-resident; ncu in profiles/)"}})}
 
 
 def fsm_bytes(g) -> int:

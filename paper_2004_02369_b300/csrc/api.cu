@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "pg_internal.h"
@@ -11,11 +12,55 @@
 namespace {
 thread_local std::string g_last_error;
 
+// A temporary from the library pool, freed on its stream at scope exit.
 struct DevTmp {
     void *p = nullptr;
-    ~DevTmp() { if (p) cudaFree(p); }
+    cudaStream_t s = nullptr;
+    int alloc(size_t bytes, cudaStream_t st) {
+        s = st;
+        return pg_dalloc(&p, bytes, st);
+    }
+    ~DevTmp() { if (p) pg_dfree(p, s); }
 };
+
+constexpr int kMaxPoolDevices = 64;
+std::once_flag g_pool_once[kMaxPoolDevices];
+cudaMemPool_t g_pool[kMaxPoolDevices];
+cudaError_t g_pool_err[kMaxPoolDevices];
 }  // namespace
+
+int pg_dalloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    int dev = 0;
+    PG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxPoolDevices) return pg_set_error(PG_EINVAL, "device index out of range");
+    std::call_once(g_pool_once[dev], [dev] {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&g_pool[dev], &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = 8ull << 30; // freed memory the pool keeps mapped
+            e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        g_pool_err[dev] = e;
+    });
+    if (g_pool_err[dev] != cudaSuccess) return pg_cuda_error(g_pool_err[dev], "library memory pool");
+    const cudaError_t e = cudaMallocFromPoolAsync(p, bytes ? bytes : 16, g_pool[dev], s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return pg_cuda_error(e, "pool allocation");
+    }
+    return PG_OK;
+}
+
+void pg_dfree(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
 
 int pg_set_error(int code, const std::string &msg) {
     g_last_error = msg;
@@ -58,12 +103,12 @@ extern "C" int pg_load_graph(const int64_t *offsets, int64_t n, const int32_t *a
         const int32_t *d_lab = labels;
         if (!inputs_on_device) {
             if (offsets[0] != 0 || offsets[n] != nnz) { rc = pg_set_error(PG_EINVAL, "offsets[0] must be 0 and offsets[n] == nnz"); break; }
-            if ((e = cudaMalloc(&toff.p, (n + 1) * sizeof(int64_t))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
-            if ((e = cudaMalloc(&tadj.p, (nnz > 0 ? nnz : 1) * sizeof(int32_t))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+            if ((rc = toff.alloc((n + 1) * sizeof(int64_t), s)) != PG_OK) break;
+            if ((rc = tadj.alloc((nnz > 0 ? nnz : 1) * sizeof(int32_t), s)) != PG_OK) break;
             if ((e = cudaMemcpyAsync(toff.p, offsets, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMemcpyAsync"); break; }
             if (nnz > 0 && (e = cudaMemcpyAsync(tadj.p, adj, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMemcpyAsync"); break; }
             if (labels) {
-                if ((e = cudaMalloc(&tlab.p, (n > 0 ? n : 1) * sizeof(int32_t))) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMalloc"); break; }
+                if ((rc = tlab.alloc((n > 0 ? n : 1) * sizeof(int32_t), s)) != PG_OK) break;
                 if (n > 0 && (e = cudaMemcpyAsync(tlab.p, labels, n * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess) { rc = pg_cuda_error(e, "cudaMemcpyAsync"); break; }
             }
             d_off = (const int64_t *)toff.p;
@@ -112,16 +157,22 @@ extern "C" int pg_graph_rank(const pg_graph *g, int32_t *rank_out) {
 
 extern "C" void pg_free_graph(pg_graph *g) {
     if (!g) return;
-    if (g->vinfo) cudaFree(g->vinfo);
-    if (g->adj) cudaFree(g->adj);
-    if (g->rank) cudaFree(g->rank);
-    if (g->orig) cudaFree(g->orig);
-    if (g->hubbits) cudaFree(g->hubbits);
+    int prev = 0;
+    const bool switched = cudaGetDevice(&prev) == cudaSuccess && prev != g->device &&
+                          cudaSetDevice(g->device) == cudaSuccess;
+    // launches on any stream may still read the graph
+    cudaDeviceSynchronize();
+    pg_dfree(g->vinfo, nullptr);
+    pg_dfree(g->adj, nullptr);
+    pg_dfree(g->rank, nullptr);
+    pg_dfree(g->orig, nullptr);
+    pg_dfree(g->hubbits, nullptr);
     pg_exec_release(&g->exec0);
-    if (g->heavy) cudaFree(g->heavy);
-    if (g->split_prefix) cudaFree(g->split_prefix);
+    pg_dfree(g->heavy, nullptr);
+    pg_dfree(g->split_prefix, nullptr);
     if (g->batch_cache) pg_batch_free(g->batch_cache);
     delete g;
+    if (switched) cudaSetDevice(prev);
 }
 
 int pg_exec_init(pg_exec *x) {
@@ -131,7 +182,10 @@ int pg_exec_init(pg_exec *x) {
 }
 
 void pg_exec_release(pg_exec *x) {
-    if (x->scratch) cudaFree(x->scratch);
+    if (x->scratch) {
+        cudaDeviceSynchronize(); // launches on any stream may still use the arena
+        pg_dfree(x->scratch, nullptr);
+    }
     if (x->queues) cudaFree(x->queues);
     if (x->tmp_counts) cudaFree(x->tmp_counts);
     x->scratch = nullptr;
@@ -144,12 +198,11 @@ int pg_ensure_scratch(pg_graph *g, size_t bytes, cudaStream_t s) {
     if (g->ex->scratch) {
         // earlier launches on any stream may still read the old arena
         PG_CUDA(cudaDeviceSynchronize());
-        cudaFree(g->ex->scratch);
+        pg_dfree(g->ex->scratch, s);
         g->ex->scratch = nullptr;
         g->ex->scratch_bytes = 0;
     }
-    (void)s;
-    PG_CUDA(cudaMalloc(&g->ex->scratch, bytes));
+    PG_TRY(pg_dalloc(&g->ex->scratch, bytes, s));
     g->ex->scratch_bytes = bytes;
     return PG_OK;
 }
@@ -502,7 +555,7 @@ extern "C" int pg_count(pg_graph *g, pg_plan *const *plans, int32_t n_plans, uin
     if (n_plans == 0) return PG_OK;
     cudaStream_t s = (cudaStream_t)stream;
     DevTmp c;
-    PG_CUDA(cudaMalloc(&c.p, 2 * sizeof(uint64_t) * n_plans));
+    PG_TRY(c.alloc(2 * sizeof(uint64_t) * n_plans, s));
     PgRunCtl ctl;
     int rc = pg_run_ctl(g, 0, s, &ctl);
     if (rc) return rc;

@@ -156,9 +156,16 @@ inline unsigned grid_for(int64_t n, int block) {
     return (unsigned)g;
 }
 
+// Load temporaries: stream-ordered from the library pool, freed on the same
+// stream when they go out of scope.
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    cudaStream_t s = nullptr;
+    int alloc(size_t bytes, cudaStream_t st) {
+        s = st;
+        return pg_dalloc(&p, bytes, st);
+    }
+    ~DevBuf() { if (p) pg_dfree(p, s); }
 };
 
 }  // namespace
@@ -167,7 +174,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
                    const int32_t *d_labels, cudaStream_t s) {
     const int64_t n = g->n;
     DevBuf err_b, vkeys, vkeys2, tmp, udeg, pdeg, ustart, pstart, ekeys, ekeys2, maxes_b;
-    PG_CUDA(cudaMalloc(&err_b.p, sizeof(unsigned)));
+    PG_TRY(err_b.alloc(sizeof(unsigned), s));
     unsigned *err = (unsigned *)err_b.p;
     PG_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
     k_check_offsets<<<grid_for(n + 1, kBlock), kBlock, 0, s>>>(d_off, n, nnz, err);
@@ -188,16 +195,16 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     if (herr & 16) return pg_set_error(PG_EINVAL, "negative vertex label");
 
     const int64_t nn = n > 0 ? n : 1;
-    PG_CUDA(cudaMalloc(&vkeys.p, nn * sizeof(unsigned long long)));
-    PG_CUDA(cudaMalloc(&vkeys2.p, nn * sizeof(unsigned long long)));
-    PG_CUDA(cudaMalloc(&udeg.p, nn * sizeof(int64_t)));
-    PG_CUDA(cudaMalloc(&pdeg.p, nn * sizeof(int64_t)));
-    PG_CUDA(cudaMalloc(&ustart.p, nn * sizeof(int64_t)));
-    PG_CUDA(cudaMalloc(&pstart.p, nn * sizeof(int64_t)));
-    PG_CUDA(cudaMalloc(&g->rank, nn * sizeof(int)));
-    PG_CUDA(cudaMalloc(&g->orig, nn * sizeof(int)));
-    PG_CUDA(cudaMalloc(&g->vinfo, nn * sizeof(int4)));
-    PG_CUDA(cudaMalloc(&maxes_b.p, 3 * sizeof(int)));
+    PG_TRY(vkeys.alloc(nn * sizeof(unsigned long long), s));
+    PG_TRY(vkeys2.alloc(nn * sizeof(unsigned long long), s));
+    PG_TRY(udeg.alloc(nn * sizeof(int64_t), s));
+    PG_TRY(pdeg.alloc(nn * sizeof(int64_t), s));
+    PG_TRY(ustart.alloc(nn * sizeof(int64_t), s));
+    PG_TRY(pstart.alloc(nn * sizeof(int64_t), s));
+    PG_TRY(pg_dalloc((void **)&g->rank, nn * sizeof(int), s));
+    PG_TRY(pg_dalloc((void **)&g->orig, nn * sizeof(int), s));
+    PG_TRY(pg_dalloc((void **)&g->vinfo, nn * sizeof(int4), s));
+    PG_TRY(maxes_b.alloc(3 * sizeof(int), s));
     int *maxes = (int *)maxes_b.p;
     PG_CUDA(cudaMemsetAsync(maxes, 0, 3 * sizeof(int), s));
 
@@ -215,7 +222,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     cub::DeviceRadixSort::SortKeys(nullptr, need, (unsigned long long *)nullptr,
                                    (unsigned long long *)nullptr, (int64_t)nnz, 0, 32 + bits_n, s);
     tmp_bytes = std::max(tmp_bytes, need);
-    PG_CUDA(cudaMalloc(&tmp.p, tmp_bytes + 16));
+    PG_TRY(tmp.alloc(tmp_bytes + 16, s));
 
     need = tmp_bytes;
     PG_CUDA(cub::DeviceRadixSort::SortKeys(tmp.p, need, (unsigned long long *)vkeys.p,
@@ -239,11 +246,11 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     }
     g->adj_entries = last_start + last_pdeg;
     if (g->adj_entries / 4 > 0xffffffffll) return pg_set_error(PG_EINVAL, "graph too large for 32-bit list starts");
-    PG_CUDA(cudaMalloc(&g->adj, (g->adj_entries > 0 ? g->adj_entries : 4) * sizeof(int)));
+    PG_TRY(pg_dalloc((void **)&g->adj, (g->adj_entries > 0 ? g->adj_entries : 4) * sizeof(int), s));
 
     // rewrite adjacency in ranks, sort by (rank_u, rank_w)
-    PG_CUDA(cudaMalloc(&ekeys.p, ne * sizeof(unsigned long long)));
-    PG_CUDA(cudaMalloc(&ekeys2.p, ne * sizeof(unsigned long long)));
+    PG_TRY(ekeys.alloc(ne * sizeof(unsigned long long), s));
+    PG_TRY(ekeys2.alloc(ne * sizeof(unsigned long long), s));
     if (nnz > 0) {
         k_edge_keys<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, n, g->rank,
                                                                 (unsigned long long *)ekeys.p);
@@ -286,7 +293,7 @@ int64_t pg_graph_bytes(const pg_graph *g) {
 int pg_graph_build_split(pg_graph *g, int grain, cudaStream_t s) {
     if (g->split_prefix) {
         PG_CUDA(cudaDeviceSynchronize());
-        cudaFree(g->split_prefix);
+        pg_dfree(g->split_prefix, s);
         g->split_prefix = nullptr;
     }
     g->n_split = 0;
@@ -316,7 +323,7 @@ int pg_graph_build_split(pg_graph *g, int grain, cudaStream_t s) {
     std::vector<long long> prefix(h + 1, 0);
     for (int64_t r = 0; r < h; ++r)
         prefix[r + 1] = prefix[r] + std::min<long long>(1024, ((long long)head[r].y + grain - 1) / grain);
-    PG_CUDA(cudaMalloc(&g->split_prefix, (h + 1) * sizeof(long long)));
+    PG_TRY(pg_dalloc((void **)&g->split_prefix, (h + 1) * sizeof(long long), s));
     PG_CUDA(cudaMemcpyAsync(g->split_prefix, prefix.data(), (h + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
     PG_CUDA(cudaStreamSynchronize(s));
     g->n_split = (int)h;
@@ -330,7 +337,7 @@ int pg_graph_build_hubs(pg_graph *g, int min_degree, int max_hubs, cudaStream_t 
     const int64_t n = g->n;
     if (g->hubbits) {
         PG_CUDA(cudaDeviceSynchronize()); // launches may still read the old rows
-        cudaFree(g->hubbits);
+        pg_dfree(g->hubbits, s);
         g->hubbits = nullptr;
     }
     g->n_hubs = 0;
@@ -344,7 +351,7 @@ int pg_graph_build_hubs(pg_graph *g, int min_degree, int max_hubs, cudaStream_t 
         const int stride = g->hub_stride;
         while (h > 0 && (int64_t)h * stride * 4 > (2ll << 30)) --h; // at most 2 GiB
         if (h > 0) {
-            PG_CUDA(cudaMalloc(&g->hubbits, (size_t)h * stride * sizeof(unsigned)));
+            PG_TRY(pg_dalloc((void **)&g->hubbits, (size_t)h * stride * sizeof(unsigned), s));
             PG_CUDA(cudaMemsetAsync(g->hubbits, 0, (size_t)h * stride * sizeof(unsigned), s));
             k_hub_bits<<<grid_for((int64_t)h * 32, kBlock), kBlock, 0, s>>>(g->vinfo, g->adj, h, stride, g->hubbits);
             PG_CUDA(cudaGetLastError());
@@ -364,21 +371,21 @@ int pg_graph_build_heavy(pg_graph *g, int heavy_min, cudaStream_t s) {
     const int64_t n = g->n;
     if (g->heavy) {
         PG_CUDA(cudaDeviceSynchronize());
-        cudaFree(g->heavy);
+        pg_dfree(g->heavy, s);
         g->heavy = nullptr;
     }
     g->n_heavy = 0;
     const int64_t nn = n > 0 ? n : 1;
-    PG_CUDA(cudaMalloc(&g->heavy, nn * sizeof(int)));
+    PG_TRY(pg_dalloc((void **)&g->heavy, nn * sizeof(int), s));
     if (n == 0) return PG_OK;
     DevBuf k1, k2, cnt, tmp;
-    PG_CUDA(cudaMalloc(&k1.p, nn * sizeof(unsigned long long)));
-    PG_CUDA(cudaMalloc(&k2.p, nn * sizeof(unsigned long long)));
-    PG_CUDA(cudaMalloc(&cnt.p, sizeof(unsigned)));
+    PG_TRY(k1.alloc(nn * sizeof(unsigned long long), s));
+    PG_TRY(k2.alloc(nn * sizeof(unsigned long long), s));
+    PG_TRY(cnt.alloc(sizeof(unsigned), s));
     size_t tmp_bytes = 0;
     PG_CUDA(cub::DeviceRadixSort::SortKeys(nullptr, tmp_bytes, (unsigned long long *)k1.p,
                                            (unsigned long long *)k2.p, (int64_t)n, 0, 64, s));
-    PG_CUDA(cudaMalloc(&tmp.p, tmp_bytes + 16));
+    PG_TRY(tmp.alloc(tmp_bytes + 16, s));
     PG_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), s));
     k_heavy_keys<<<grid_for(n, kBlock), kBlock, 0, s>>>(g->vinfo, n, heavy_min, (unsigned long long *)k1.p,
                                                         (unsigned *)cnt.p);

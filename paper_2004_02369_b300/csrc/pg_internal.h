@@ -170,6 +170,23 @@ int pg_cuda_error(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return pg_cuda_error(_e, #call);        \
     } while (0)
 
+#define PG_TRY(call)                                                   \
+    do {                                                               \
+        const int _rc = (call);                                        \
+        if (_rc != PG_OK) return _rc;                                  \
+    } while (0)
+
+// Device memory of graphs, their load temporaries and execution arenas
+// comes from a library memory pool per device (stream-ordered; freed memory
+// stays with the pool up to 8 GiB, so repeated graph loads and arena growth
+// reuse mapped memory).  pg_dalloc: *p on the current device, usable on
+// stream s (and on other streams after s is synchronised).  pg_dfree:
+// stream-ordered free on s; callers that may still have work on other
+// streams synchronise first.  Memory from pg_dalloc is freed only by
+// pg_dfree.
+int pg_dalloc(void **p, size_t bytes, cudaStream_t s);
+void pg_dfree(void *p, cudaStream_t s);
+
 // graph.cu
 int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int64_t nnz,
                    const int32_t *d_labels, cudaStream_t s);

@@ -595,7 +595,8 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
     S->slots.resize(n_streams);
     for (Slot &s : S->slots) {
         if ((rc = pg_exec_init(&s.ex)) != PG_OK) break;
-        if ((e = cudaMalloc(&s.ex.scratch, per_stream)) != cudaSuccess) { rc = pg_cuda_error(e, "server scratch"); break; }
+        if ((rc = pg_dalloc(&s.ex.scratch, per_stream, nullptr)) != PG_OK) break;
+        if ((e = cudaStreamSynchronize(nullptr)) != cudaSuccess) { rc = pg_cuda_error(e, "server scratch"); break; }
         s.ex.scratch_bytes = per_stream;
         s.view = *g;
         s.view.ex = &s.ex;
