@@ -18,14 +18,20 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Per-vertex validation: ids in range, no loop, strictly ascending, and the
-// reverse edge present.  err bit 1: range, 2: loop, 4: order, 8: asymmetric,
-// 16: negative label.
+// Per-vertex validation: ids in range, no loop, strictly ascending, and
+// every edge present in both directions.  Symmetry is checked with half the
+// searches: every upward entry (u, x), x > u, must find u in adj(x), and
+// the upward and downward entries must be equally many (lists hold no
+// duplicates, so the reverses of the upward entries are distinct downward
+// entries, and equal counts leave no other downward entry).  err bit 1:
+// range, 2: loop, 4: order, 8: asymmetric, 16: negative label;
+// updown[0] / [1]: upward / downward entries.
 __global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t *labels, int64_t n,
-                           unsigned *err) {
+                           unsigned *err, unsigned long long *updown) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    unsigned long long up = 0, down = 0;
     for (int64_t u = warp; u < n; u += nwarps) {
         const int64_t b = off[u], e = off[u + 1];
         unsigned bad = 0;
@@ -35,6 +41,11 @@ __global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t
             if (x < 0 || x >= n) { bad |= 1; continue; }
             if (x == u) bad |= 2;
             if (i > b && adj[i - 1] >= x) bad |= 4;
+            if (x < u) {
+                ++down;
+                continue;
+            }
+            ++up;
             // reverse edge u in adj(x)
             int64_t lo = off[x], hi = off[x + 1];
             while (lo < hi) {
@@ -44,6 +55,14 @@ __global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t
             if (lo >= off[x + 1] || adj[lo] != u) bad |= 8;
         }
         if (bad) atomicOr(err, bad);
+    }
+    for (int o = 16; o; o >>= 1) {
+        up += __shfl_down_sync(0xffffffffu, up, o);
+        down += __shfl_down_sync(0xffffffffu, down, o);
+    }
+    if (lane == 0 && (up || down)) {
+        atomicAdd(updown, up);
+        atomicAdd(updown + 1, down);
     }
 }
 
@@ -174,19 +193,23 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
                    const int32_t *d_labels, cudaStream_t s) {
     const int64_t n = g->n;
     DevBuf err_b, vkeys, vkeys2, tmp, udeg, pdeg, ustart, pstart, ekeys, ekeys2, maxes_b;
-    PG_TRY(err_b.alloc(sizeof(unsigned), s));
+    PG_TRY(err_b.alloc(4 * sizeof(unsigned long long), s));
     unsigned *err = (unsigned *)err_b.p;
-    PG_CUDA(cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+    unsigned long long *updown = (unsigned long long *)err_b.p + 2;
+    PG_CUDA(cudaMemsetAsync(err_b.p, 0, 4 * sizeof(unsigned long long), s));
     k_check_offsets<<<grid_for(n + 1, kBlock), kBlock, 0, s>>>(d_off, n, nnz, err);
     unsigned herr = 0;
     PG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
     if (herr) return pg_set_error(PG_EINVAL, "offsets must start at 0, end at nnz and be non-decreasing");
     if (n > 0) {
-        k_validate<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, d_labels, n, err);
+        k_validate<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, d_labels, n, err, updown);
         PG_CUDA(cudaGetLastError());
-        PG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        unsigned long long h[4] = {0, 0, 0, 0}; // err word (low half of h[0]), unused, up, down
+        PG_CUDA(cudaMemcpyAsync(h, err_b.p, sizeof(h), cudaMemcpyDeviceToHost, s));
         PG_CUDA(cudaStreamSynchronize(s));
+        herr = (unsigned)(h[0] & 0xffffffffull);
+        if (h[2] != h[3]) herr |= 8;
     }
     if (herr & 1) return pg_set_error(PG_EINVAL, "adjacency entry out of range");
     if (herr & 2) return pg_set_error(PG_EINVAL, "self loop in data graph");

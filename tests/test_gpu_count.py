@@ -171,6 +171,20 @@ def test_invalid_csr_rejected(pg):
     with pytest.raises(pg.PgError) as e:
         pg.Graph(off, adj)
     assert e.value.code == pg.PG_EINVAL
+    off = np.array([0, 0, 1], dtype=np.int64)
+    adj = np.array([0], dtype=np.int32)  # 1->0 without 0->1 (a downward entry alone)
+    with pytest.raises(pg.PgError) as e:
+        pg.Graph(off, adj)
+    assert e.value.code == pg.PG_EINVAL
+    # a triangle with one direction of one edge missing, and one with a
+    # reversed extra entry: the symmetric part is fine, one entry is not
+    for off, adj in ((np.array([0, 2, 4, 5]), np.array([1, 2, 0, 2, 1])),
+                     (np.array([0, 1, 3, 5]), np.array([1, 0, 2, 0, 1]))):
+        with pytest.raises(pg.PgError) as e:
+            pg.Graph(off.astype(np.int64), adj.astype(np.int32))
+        assert e.value.code == pg.PG_EINVAL
+    ok = pg.Graph(np.array([0, 2, 4, 6], dtype=np.int64), np.array([1, 2, 0, 2, 0, 1], dtype=np.int32))
+    assert pg.count(ok, [pg.Plan(3, sg.clique_edges(3))]) == [1]
     off = np.array([0, 2, 3, 4], dtype=np.int64)
     adj = np.array([2, 1, 0, 0], dtype=np.int32)  # unsorted list of 0
     with pytest.raises(pg.PgError):
