@@ -1078,8 +1078,8 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
             "queries": len(qs), "types": types, "labeled_fraction": 0.1, "labeled_only": list(labeled_only),
             "arrivals": "Poisson, rate = lambda x measured serial capacity",
             "batched": "4 streams, up to 32 queries per launch; a pattern's first query and patterns longer "
-                       "than 20 ms alone run alone (with the waiting queries of the same pattern), one launch at "
-                       "a time, on all SMs unless the mode name gives a share", "serial_capacity_qps": capacity,
+                       "than 20 ms alone run alone (with the waiting queries of the same pattern) on at most 3 "
+                       "streams, on all SMs unless the mode name gives a share", "serial_capacity_qps": capacity,
             "alone_ms": alone_ms, "runs": runs, "mix_equals_alone": True,
             "query_timeout_s": query_timeout_s}
 

@@ -681,9 +681,10 @@ int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int
  * while others run are admitted as soon as a stream frees up.  Plans are
  * compiled once per distinct pattern and kept, with the pattern's measured
  * service time: the first query of a pattern runs alone, and a pattern that
- * took longer than batch_limit_ms alone keeps running alone, so batches
- * gather the short queries (which overtake long ones waiting in the queue)
- * and a long query never holds a batch of short ones.  An anti-vertex query
+ * took longer than batch_limit_ms alone keeps running alone (with the
+ * waiting queries of the same pattern), on at most n_streams - 1 streams,
+ * so batches gather the short queries (which overtake long ones waiting in
+ * the queue) and a long query never holds a batch of short ones.  An anti-vertex query
  * is launched alone on the plan interpreter (PG_KERNEL_GENERIC), since
  * batches do not take anti-vertex plans.  The paper runs one mining
  * program at a time (Section 5.1); this loop applies its processing model to
@@ -718,12 +719,13 @@ typedef struct {
     double batch_limit_ms;  /* > 0: a pattern whose query took longer than
                                this alone is not batched again; 0: 20 ms;
                                < 0: no measuring, any query may be batched */
-    double alone_sm_fraction; /* with n_streams > 1, queries that run alone
-                               (long, unmeasured, isolated; with the waiting
-                               queries of the same pattern) go one launch at
-                               a time on this fraction of the SMs (a smaller
-                               persistent grid), leaving the rest to batches
-                               of short queries; (0, 1], 0: 1 (all SMs) */
+    double alone_sm_fraction; /* with n_streams > 1, launches of queries
+                               that run alone (long, unmeasured, isolated;
+                               with the waiting queries of the same pattern)
+                               hold at most n_streams - 1 streams and use this
+                               fraction of the SMs (a smaller persistent
+                               grid), leaving the rest to batches of short
+                               queries; (0, 1], 0: 1 (all SMs) */
 } pg_server_config;
 
 typedef struct {

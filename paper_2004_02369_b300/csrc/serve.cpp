@@ -18,11 +18,10 @@
 // oldest waiting query if it must run alone, else a batch of the waiting
 // short queries (which so overtake long ones), so a long query never holds
 // a batch of short ones and short queries are still fused into one launch.
-// With several streams the queries that run alone go one at a time
-// (together with the waiting queries of the same pattern, which a batch
-// counts once), optionally on a share of the SMs (a smaller persistent grid),
-// so that short batches find free SMs instead of queueing behind a long
-// launch that fills the GPU.
+// With several streams the launches of queries that run alone (together
+// with the waiting queries of the same pattern, which a batch counts once)
+// hold at most all streams but one, optionally on a share of the SMs (a
+// smaller persistent grid), so that short batches always find a stream.
 //
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
@@ -371,7 +370,7 @@ void expire_waiting(pg_server *S) {
 // out of time, an anti-vertex pattern, or a pattern not yet measured or
 // measured longer than the batch limit.
 bool goes_alone(pg_server *S, const ServerQuery &q) {
-    if (q.alone || q.plan->h.anti_vertices) return true;
+    if (q.alone || q.requeued || q.plan->h.anti_vertices) return true;
     if (S->batch_limit_s < 0) return false;
     auto it = S->cost.find(q.plan);
     return it == S->cost.end() || it->second.slow;
@@ -491,12 +490,13 @@ void worker_loop(pg_server *S) {
         }
         expire_waiting(S);
         // With several streams, queries that run alone (long, unmeasured or
-        // isolated ones) run one at a time on a share of the SMs, so that a
-        // persistent launch of a long query never holds every SM while short
-        // queries wait: their batches take the rest.
+        // isolated ones) hold at most all streams but one (optionally on a
+        // share of the SMs), so that short batches always find a stream.
         const bool multi = S->slots.size() > 1;
-        bool long_busy = false;
-        for (Slot &s : S->slots) long_busy |= s.busy && s.long_class;
+        // launches that run alone may hold all streams but one
+        const int long_max = std::max(1, (int)S->slots.size() - 1);
+        int long_running = 0;
+        for (Slot &s : S->slots) long_running += s.busy && s.long_class ? 1 : 0;
         bool any_alive = false;
         for (Slot &s : S->slots) {
             any_alive |= !s.dead;
@@ -507,7 +507,7 @@ void worker_loop(pg_server *S) {
                 std::lock_guard<std::mutex> lock(S->mu);
                 if (!S->pending.empty()) {
                     ServerQuery &f = S->pending.front();
-                    if ((max_batch == 1 || goes_alone(S, f)) && !(multi && long_busy)) {
+                    if ((max_batch == 1 || goes_alone(S, f)) && !(multi && long_running >= long_max)) {
                         // the oldest query runs by itself: isolated, measuring
                         // its pattern, known long, or anti-vertex
                         if (!S->cfg.serial && S->cfg.query_timeout_s > 0 && !f.requeued && !f.alone &&
@@ -518,7 +518,7 @@ void worker_loop(pg_server *S) {
                         is_long = true;
                         // waiting queries of the same pattern ride along: a
                         // batch counts each distinct pattern once
-                        if (max_batch > 1 && !take[0].plan->h.anti_vertices && !take[0].alone)
+                        if (max_batch > 1 && !take[0].plan->h.anti_vertices && !take[0].alone && take[0].cap_s <= 0)
                             for (auto it = S->pending.begin(); it != S->pending.end() && (int)take.size() < max_batch;) {
                                 if (it->plan == take[0].plan && !it->alone) {
                                     take.push_back(*it);
@@ -544,7 +544,7 @@ void worker_loop(pg_server *S) {
             s.view.num_sms = is_long && multi ? std::max(1, (int)(S->g->num_sms * S->alone_share)) : S->g->num_sms;
             launch_batch(S, s, take);
             s.long_class = is_long && s.busy;
-            long_busy |= s.long_class;
+            long_running += s.long_class ? 1 : 0;
             progress = true;
             if (S->cfg.serial) break;
         }
