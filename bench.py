@@ -263,6 +263,7 @@ def hbm_roofline(kernel: str, alg_bytes: int, ms: float, per_launch_note: str, e
     rec = ncu_record(kernel)
     out = {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
            "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+           "frac_of_nominal_7700": achieved / 7700.0,
            "algorithmic_bytes_per_launch": int(alg_bytes), "algorithmic_bytes": per_launch_note,
            "traffic": rec["dram_bytes_per_launch"] if rec and "dram_bytes_per_launch" in rec else None}
     if rec:

@@ -66,6 +66,17 @@ __global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t
     }
 }
 
+// First rank whose degree is at most d (degrees fall with rank): binary
+// search by one thread.
+__global__ void k_first_at_most(const int4 *vinfo, int64_t n, int d, long long *out) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (vinfo[mid].y > d) lo = mid + 1; else hi = mid;
+    }
+    *out = (long long)lo;
+}
+
 __global__ void k_check_offsets(const int64_t *off, int64_t n, int64_t nnz, unsigned *err) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0 && (off[0] != 0 || off[n] != nnz)) atomicOr(err, 32u);
@@ -323,22 +334,14 @@ int pg_graph_build_split(pg_graph *g, int grain, cudaStream_t s) {
     g->n_split_tasks = 0;
     g->split_grain_built = grain;
     if (grain <= 0 || g->n == 0) return PG_OK;
-    auto degree = [&](int64_t r, int *d) -> int {
-        int4 vi;
-        PG_CUDA(cudaMemcpyAsync(&vi, g->vinfo + r, sizeof(int4), cudaMemcpyDeviceToHost, s));
-        PG_CUDA(cudaStreamSynchronize(s));
-        *d = vi.y;
-        return PG_OK;
-    };
-    int64_t lo = 0, hi = g->n; // first rank with degree <= grain
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) / 2;
-        int d = 0;
-        int rc = degree(mid, &d);
-        if (rc) return rc;
-        if (d > grain) lo = mid + 1; else hi = mid;
-    }
-    const int64_t h = lo;
+    // first rank with degree <= grain (one device search, one copy)
+    DevBuf first_b;
+    PG_TRY(first_b.alloc(sizeof(long long), s));
+    k_first_at_most<<<1, 1, 0, s>>>(g->vinfo, g->n, grain, (long long *)first_b.p);
+    PG_CUDA(cudaGetLastError());
+    long long h = 0;
+    PG_CUDA(cudaMemcpyAsync(&h, first_b.p, sizeof(long long), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaStreamSynchronize(s));
     if (h == 0) return PG_OK;
     std::vector<int4> head(h);
     PG_CUDA(cudaMemcpyAsync(head.data(), g->vinfo, h * sizeof(int4), cudaMemcpyDeviceToHost, s));

@@ -88,6 +88,10 @@ struct Slot {
     std::vector<uint64_t> cancelled; // cancelled queries of the launch in flight
     PgRunCtl ctl;          // run control of the launch in flight
     bool long_class = false; // the launch in flight runs a query alone (long or unmeasured)
+    double deadline = 0;   // host time the launch in flight must end by (0: none)
+    bool deadline_raised = false;
+    cudaEvent_t raised = nullptr; // after the last stop-word copy on the control stream
+    bool raise_pending = false;   // the next launch on this slot must wait for it
 };
 
 constexpr size_t kAreaBytes = 4u << 20;
@@ -181,6 +185,14 @@ void drop_expired(pg_server *S, std::vector<ServerQuery> &qs) {
 // alone.  False if some query has no time left (reported).
 bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
     s.view.budget_ns = 0;
+    s.deadline = 0;
+    s.deadline_raised = false;
+    if (s.raise_pending) {
+        // a stop word raised for the previous launch lands before this
+        // launch resets it
+        cudaStreamWaitEvent(s.stream, s.raised, 0);
+        s.raise_pending = false;
+    }
     if (S->cfg.query_timeout_s <= 0) return true;
     const double now = S->now();
     double left = 1e300;
@@ -197,6 +209,7 @@ bool set_budget(pg_server *S, Slot &s, std::vector<ServerQuery> &qs) {
         return false;
     }
     s.view.budget_ns = (unsigned long long)(left * 1e9) + 1;
+    s.deadline = now + left;
     return true;
 }
 
@@ -312,6 +325,30 @@ void fail_pending(pg_server *S, int status) {
     S->outstanding -= (int64_t)qs.size();
 }
 
+// Raises the stop word of slot s's launch in flight (and its timed-out word
+// first, for a deadline) by host-to-device copies on the control stream:
+// a copy engine delivers them while the running kernel holds every SM.
+void raise_stop(pg_server *S, Slot &s, bool timed_out) {
+    if (timed_out)
+        cudaMemcpyAsync(s.ctl.words + 1, S->h_one, sizeof(unsigned long long), cudaMemcpyHostToDevice, S->ctl_stream);
+    cudaMemcpyAsync(s.ctl.words, S->h_one, sizeof(unsigned long long), cudaMemcpyHostToDevice, S->ctl_stream);
+    cudaEventRecord(s.raised, S->ctl_stream);
+    s.raise_pending = true;
+}
+
+// Launches past their deadline on the host clock get their stop and
+// timed-out words raised: the device budget counts from the kernel's own
+// start, which may come late when other launches hold the SMs.
+void enforce_deadlines(pg_server *S) {
+    if (S->cfg.query_timeout_s <= 0) return;
+    const double now = S->now();
+    for (Slot &s : S->slots)
+        if (s.busy && s.ctl.words && s.deadline > 0 && !s.deadline_raised && now > s.deadline) {
+            raise_stop(S, s, true);
+            s.deadline_raised = true;
+        }
+}
+
 // Cancellations: waiting queries leave the queue with PG_ECANCELED; a
 // running launch that holds a cancelled query gets its stop word raised.
 void apply_cancels(pg_server *S) {
@@ -337,9 +374,7 @@ void apply_cancels(pg_server *S) {
             bool mine = false;
             for (auto &q : s.qs) mine |= q.ticket == t;
             if (!mine) continue;
-            if (s.cancelled.empty())
-                cudaMemcpyAsync(s.ctl.words, S->h_one, sizeof(unsigned long long), cudaMemcpyHostToDevice,
-                                S->ctl_stream);
+            if (s.cancelled.empty()) raise_stop(S, s, false);
             s.cancelled.push_back(t);
         }
     // a ticket found nowhere already has its result: nothing to do
@@ -382,6 +417,7 @@ void worker_loop(pg_server *S) {
     while (!S->stop.load()) {
         bool progress = false;
         apply_cancels(S);
+        enforce_deadlines(S);
         for (Slot &s : S->slots) {
             if (!s.busy) continue;
             const cudaError_t e = cudaEventQuery(s.done);
@@ -606,6 +642,7 @@ extern "C" int pg_server_create(pg_graph *g, const pg_server_config *cfg, pg_ser
         s.view.budget_ns = 0;
         if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s.raised, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaMalloc(&s.d_area, kAreaBytes)) != cudaSuccess ||
             (e = cudaMallocHost(&s.h_area, kAreaBytes)) != cudaSuccess ||
             (e = cudaMalloc(&s.d_counts, 2 * sizeof(uint64_t) * PG_MAX_QUEUES)) != cudaSuccess ||
@@ -694,6 +731,7 @@ extern "C" void pg_server_free(pg_server *S) {
         if (s.stream) cudaStreamSynchronize(s.stream);
         if (s.batch) pg_batch_free(s.batch);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.raised) cudaEventDestroy(s.raised);
         if (s.stream) cudaStreamDestroy(s.stream);
         if (s.d_area) cudaFree(s.d_area);
         if (s.h_area) cudaFreeHost(s.h_area);
