@@ -558,12 +558,16 @@ MOTIF4_SHAPE_NAMES = {1: "path", 2: "star", 3: "cycle", 4: "tailed_triangle", 5:
 def labeled_motif4(graph: Graph, stream=None) -> dict:
     """pg_labeled_motif4: {(shape name, (l0, l1, l2, l3)): vertex-induced count}
     for every labeled connected 4-vertex pattern present."""
-    n = _i64()
-    rc = _lib.pg_labeled_motif4(graph.handle, None, 0, ctypes.byref(n), _stream_ptr(stream))
-    if rc not in (PG_OK, PG_ETRUNC):
+    cap = 1 << 16  # a second call only when more labeled patterns are present
+    while True:
+        arr = (LabeledCount4 * cap)()
+        n = _i64()
+        rc = _lib.pg_labeled_motif4(graph.handle, arr, cap, ctypes.byref(n), _stream_ptr(stream))
+        if rc == PG_ETRUNC:
+            cap = int(n.value) + 1
+            continue
         _check(rc)
-    arr = (LabeledCount4 * max(1, n.value))()
-    _check(_lib.pg_labeled_motif4(graph.handle, arr, n.value, ctypes.byref(n), _stream_ptr(stream)))
+        break
     return {(MOTIF4_SHAPE_NAMES[r.shape], tuple(int(x) for x in r.labels)): _u128(r.count_lo, r.count_hi)
             for r in arr[:n.value]}
 
@@ -593,7 +597,7 @@ class LabeledCount(ctypes.Structure):
 def labeled_motif3(graph: Graph, stream=None) -> dict:
     """Vertex-induced labeled 3-motif counts with label discovery:
     {("triangle", (a, b, c)): n, ("wedge", (centre, x, y)): n}, nonzero only."""
-    cap = 4096
+    cap = 1 << 16  # a second call only when more labeled patterns are present
     while True:
         arr = (LabeledCount * cap)()
         n = _i64()

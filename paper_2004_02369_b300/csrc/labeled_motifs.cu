@@ -152,9 +152,15 @@ __global__ void k_lm_emit(int L, const unsigned long long *wn, const unsigned lo
     if ((long long)slot < capacity) out[slot] = r;
 }
 
+// Temporaries from the library pool, freed on their stream.
 struct DevBuf {
     void *p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    cudaStream_t s = nullptr;
+    int alloc(size_t bytes, cudaStream_t st) {
+        s = st;
+        return pg_dalloc(&p, bytes, st);
+    }
+    ~DevBuf() { if (p) pg_dfree(p, s); }
 };
 
 }  // namespace
@@ -167,7 +173,7 @@ int pg_labeled_motif3_run(pg_graph *g, pg_labeled_count *out, int64_t capacity, 
     const int P = L * (L + 1) / 2, Q = L * (L + 1) * (L + 2) / 6;
     const size_t wn_words = 2 * (size_t)L * P, tri_words = 2 * (size_t)Q;
     DevBuf tabs, recs;
-    PG_CUDA(cudaMalloc(&tabs.p, (wn_words + tri_words + 1) * sizeof(unsigned long long)));
+    PG_TRY(tabs.alloc((wn_words + tri_words + 1) * sizeof(unsigned long long), s));
     unsigned long long *wn = (unsigned long long *)tabs.p, *tri = wn + wn_words, *cnt = tri + tri_words;
     PG_CUDA(cudaMemsetAsync(tabs.p, 0, (wn_words + tri_words + 1) * sizeof(unsigned long long), s));
     const size_t smem_w = (size_t)L * P * sizeof(unsigned long long) + (size_t)kWarps * L * sizeof(int);
@@ -185,7 +191,7 @@ int pg_labeled_motif3_run(pg_graph *g, pg_labeled_count *out, int64_t capacity, 
     }
     const long long total = (long long)L * P + Q;
     const long long cap = std::max<long long>(capacity, 0);
-    PG_CUDA(cudaMalloc(&recs.p, std::max<long long>(cap, 1) * sizeof(pg_labeled_count)));
+    PG_TRY(recs.alloc(std::max<long long>(cap, 1) * sizeof(pg_labeled_count), s));
     k_lm_emit<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(L, wn, tri, (pg_labeled_count *)recs.p, cap, cnt);
     PG_CUDA(cudaGetLastError());
     unsigned long long n = 0;

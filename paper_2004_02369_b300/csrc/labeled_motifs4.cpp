@@ -80,12 +80,12 @@ int pg_labeled_motif4_run(pg_graph *g, pg_labeled_count4 *out, int64_t capacity,
     if (!g->labeled) return pg_set_error(PG_EINVAL, "labeled motifs need a labeled graph");
     const int L = std::max(1, (int)g->n_labels);
     if (L > 32) return pg_set_error(PG_EUNSUPPORTED, "labeled motifs support labels 0..31");
-    // 1. discovery: the labeled 3-motifs present
+    // 1. discovery: the labeled 3-motifs present (at most every labeled
+    // wedge and triangle: L * L(L+1)/2 + L(L+1)(L+2)/6 of them)
     int64_t n3 = 0;
-    int rc = pg_labeled_motif3_run(g, nullptr, 0, &n3, s);
-    if (rc != PG_OK && rc != PG_ETRUNC) return rc;
-    std::vector<pg_labeled_count> m3((size_t)std::max<int64_t>(n3, 1));
-    if ((rc = pg_labeled_motif3_run(g, m3.data(), n3, &n3, s)) != PG_OK) return rc;
+    std::vector<pg_labeled_count> m3((size_t)L * L * (L + 1) / 2 + (size_t)L * (L + 1) * (L + 2) / 6);
+    int rc = pg_labeled_motif3_run(g, m3.data(), (int64_t)m3.size(), &n3, s);
+    if (rc != PG_OK) return rc;
     std::set<std::array<int, 3>> tri, wedge; // sorted triples; (centre, x <= y)
     for (int64_t i = 0; i < n3; ++i) {
         const pg_labeled_count &r = m3[i];
