@@ -981,9 +981,10 @@ def serving_run(pg, scale: int, n_queries: int, lambdas, timeout_s: float, label
                 query_timeout_s: float = 0.0, alone_only: bool = False, alone_budget_ms: float = 0.0,
                 types=None, alone_fractions=(1.0,)) -> dict:
     """Poisson streams of count queries over a resident R-MAT graph (the
-    survey's mix, 10% labeled over 8 labels): continuous batching (4
-    streams, up to 32 queries per launch) against the same kernels one query
-    at a time; every result of the mix equals the query's count alone."""
+    serving mix of cliques, stars, paths, cycles and tailed triangles, 10%
+    labeled over 8 labels): continuous batching (4 streams, up to 32 queries
+    per launch) against the same kernels one query at a time; every result
+    of the mix equals the query's count alone."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     g = sg.workload_graph(5, scale_down=22 - scale)
