@@ -682,7 +682,9 @@ int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int
  * compiled once per distinct pattern and kept, with the pattern's measured
  * service time: the first query of a pattern runs alone, and a pattern that
  * took longer than batch_limit_ms alone keeps running alone (with the
- * waiting queries of the same pattern), on at most n_streams - 1 streams,
+ * waiting queries of the same pattern), on at most n_streams - 1 streams
+ * (one under a query time limit: a persistent launch keeps its SMs until it
+ * ends, so a second long launch would start only past its deadlines),
  * so batches gather the short queries (which overtake long ones waiting in
  * the queue) and a long query never holds a batch of short ones.  An anti-vertex query
  * is launched alone on the plan interpreter (PG_KERNEL_GENERIC), since
@@ -722,7 +724,8 @@ typedef struct {
     double alone_sm_fraction; /* with n_streams > 1, launches of queries
                                that run alone (long, unmeasured, isolated;
                                with the waiting queries of the same pattern)
-                               hold at most n_streams - 1 streams and use this
+                               hold at most n_streams - 1 streams (1 with a
+                               query time limit) and use this
                                fraction of the SMs (a smaller persistent
                                grid), leaving the rest to batches of short
                                queries; (0, 1], 0: 1 (all SMs) */

@@ -20,8 +20,9 @@
 // a batch of short ones and short queries are still fused into one launch.
 // With several streams the launches of queries that run alone (together
 // with the waiting queries of the same pattern, which a batch counts once)
-// hold at most all streams but one, optionally on a share of the SMs (a
-// smaller persistent grid), so that short batches always find a stream.
+// hold at most all streams but one (one, under a query time limit),
+// optionally on a share of the SMs (a smaller persistent grid), so that
+// short batches always find a stream.
 //
 // A query time limit (query_timeout_s) becomes the device work budget of
 // the launch that counts it (the smallest remaining time over the batch):
@@ -529,8 +530,11 @@ void worker_loop(pg_server *S) {
         // isolated ones) hold at most all streams but one (optionally on a
         // share of the SMs), so that short batches always find a stream.
         const bool multi = S->slots.size() > 1;
-        // launches that run alone may hold all streams but one
-        const int long_max = std::max(1, (int)S->slots.size() - 1);
+        // launches that run alone may hold all streams but one; with a time
+        // limit only one at a time: a persistent launch keeps the SMs it
+        // starts on until it ends, so a second one would wait for them (and
+        // could not see its stop word) past its queries' deadlines
+        const int long_max = S->cfg.query_timeout_s > 0 ? 1 : std::max(1, (int)S->slots.size() - 1);
         int long_running = 0;
         for (Slot &s : S->slots) long_running += s.busy && s.long_class ? 1 : 0;
         bool any_alive = false;
