@@ -675,7 +675,7 @@ int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int
  * requirement fits that stream's preallocated share of memory_budget (a
  * batch that does not fit is split; a query that does not fit alone fails
  * with PG_ENOMEM in its result), counts each batch in one launch (the batch
- * kernel over the shared prefix tree, cliques by the clique kernel), and
+ * kernel, one task group per pattern; cliques by the clique kernel), and
  * publishes per-query results with submit / start / completion times.
  * Batches on different streams overlap on the device, and queries arriving
  * while others run are admitted as soon as a stream frees up.  Plans are
@@ -686,9 +686,9 @@ int pg_labeled_motif4(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int
  * (one under a query time limit: a persistent launch keeps its SMs until it
  * ends, so a second long launch would start only past its deadlines),
  * so batches gather the short queries (which overtake long ones waiting in
- * the queue) and a long query never holds a batch of short ones.  An anti-vertex query
- * is launched alone on the plan interpreter (PG_KERNEL_GENERIC), since
- * batches do not take anti-vertex plans.  The paper runs one mining
+ * the queue) and a long query never holds a batch of short ones.  An
+ * anti-vertex query is launched alone on the plan interpreter
+ * (PG_KERNEL_GENERIC), since batches do not take anti-vertex plans.  The paper runs one mining
  * program at a time (Section 5.1); this loop applies its processing model to
  * a stream of patterns.
  *   n_streams      concurrent batches (1..16); memory_budget: device bytes
@@ -706,18 +706,22 @@ typedef struct {
     int32_t serial;
     int32_t pad;
     double query_timeout_s; /* > 0: a query not done this long after its
-                               submission fails with PG_ETIMEOUT (enforced as
-                               the device work budget of its launch, see
-                               pg_set_time_budget: a single query gets its
-                               time left, a batch half the least time left
-                               among its queries; when a batch runs out, its
-                               queries are launched again one by one with
-                               their own time left, so only the slow one
-                               fails).  The first (measuring) run of a
-                               pattern gets at most a quarter of the limit;
-                               if that runs out, the query goes to the back
-                               of the queue with the time it has left.
-                               0: no limit */
+                               submission fails with PG_ETIMEOUT.  Enforced
+                               as the device work budget of its launch (see
+                               pg_set_time_budget) and on the host clock (a
+                               launch past its deadline gets its stop word
+                               raised): a launch of one pattern gets the
+                               least time left among its queries, a batch of
+                               several patterns half of it.  When a batch
+                               runs out its queries are launched again one
+                               by one, so only the slow one fails; when a
+                               one-pattern launch runs out, its queries with
+                               more time left than it ran go to the back of
+                               the queue.  The first (measuring) run of a
+                               pattern, and the first rerun after a batch
+                               ran out, get at most a quarter of the time
+                               left.  Waiting queries fail as soon as their
+                               limit passes.  0: no limit */
     double batch_limit_ms;  /* > 0: a pattern whose query took longer than
                                this alone is not batched again; 0: 20 ms;
                                < 0: no measuring, any query may be batched */
