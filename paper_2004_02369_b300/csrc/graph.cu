@@ -18,20 +18,15 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// Per-vertex validation: ids in range, no loop, strictly ascending, and
-// every edge present in both directions.  Symmetry is checked with half the
-// searches: every upward entry (u, x), x > u, must find u in adj(x), and
-// the upward and downward entries must be equally many (lists hold no
-// duplicates, so the reverses of the upward entries are distinct downward
-// entries, and equal counts leave no other downward entry).  err bit 1:
-// range, 2: loop, 4: order, 8: asymmetric, 16: negative label;
-// updown[0] / [1]: upward / downward entries.
+// Per-vertex validation before the build: ids in range, no loop, strictly
+// ascending lists, labels >= 0.  err bit 1: range, 2: loop, 4: order,
+// 16: negative label.  Symmetry is checked by k_symmetric on the ranked
+// lists.
 __global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t *labels, int64_t n,
-                           unsigned *err, unsigned long long *updown) {
+                           unsigned *err) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
-    unsigned long long up = 0, down = 0;
     for (int64_t u = warp; u < n; u += nwarps) {
         const int64_t b = off[u], e = off[u + 1];
         unsigned bad = 0;
@@ -41,29 +36,42 @@ __global__ void k_validate(const int64_t *off, const int32_t *adj, const int32_t
             if (x < 0 || x >= n) { bad |= 1; continue; }
             if (x == u) bad |= 2;
             if (i > b && adj[i - 1] >= x) bad |= 4;
-            if (x < u) {
-                ++down;
-                continue;
-            }
-            ++up;
-            // reverse edge u in adj(x)
-            int64_t lo = off[x], hi = off[x + 1];
-            while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                if (adj[mid] < u) lo = mid + 1; else hi = mid;
-            }
-            if (lo >= off[x + 1] || adj[lo] != u) bad |= 8;
         }
         if (bad) atomicOr(err, bad);
     }
-    for (int o = 16; o; o >>= 1) {
-        up += __shfl_down_sync(0xffffffffu, up, o);
-        down += __shfl_down_sync(0xffffffffu, down, o);
+}
+
+// Symmetry on the ranked lists: every entry s of adj(r) ranked above r
+// (an upward entry) must have r in adj(s), where r lies in the out-prefix of
+// s (its neighbours ranked below it: at most max out-degree entries, a
+// short search); and upward entries must be half of all entries.  Lists
+// hold no duplicates, so the reverses of the upward entries are distinct
+// downward entries, and equal counts leave no other downward entry: every
+// edge is present in both directions.  err bit 8: asymmetric; *up: upward
+// entries.
+__global__ void k_symmetric(const int4 *vinfo, const int *adj, int64_t n, unsigned *err, unsigned long long *up) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (gridDim.x * (int64_t)blockDim.x) >> 5;
+    bool bad = false;
+    unsigned long long cnt = 0;
+    for (int64_t r = warp; r < n; r += nwarps) {
+        const int4 vr = vinfo[r];
+        if (lane == 0) cnt += (unsigned long long)(vr.y - vr.z);
+        const int *ar = adj + ((size_t)(unsigned)vr.x << 2);
+        for (int i = vr.z + lane; i < vr.y; i += 32) {
+            const int4 vs = vinfo[ar[i]];
+            const int *as = adj + ((size_t)(unsigned)vs.x << 2);
+            int lo = 0, hi = vs.z;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (as[mid] < (int)r) lo = mid + 1; else hi = mid;
+            }
+            bad |= lo >= vs.z || as[lo] != (int)r;
+        }
     }
-    if (lane == 0 && (up || down)) {
-        atomicAdd(updown, up);
-        atomicAdd(updown + 1, down);
-    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, 8u);
+    if (lane == 0 && cnt) atomicAdd(up, cnt);
 }
 
 // First rank whose degree is at most d (degrees fall with rank): binary
@@ -206,7 +214,7 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     DevBuf err_b, vkeys, vkeys2, tmp, udeg, pdeg, ustart, pstart, ekeys, ekeys2, maxes_b;
     PG_TRY(err_b.alloc(4 * sizeof(unsigned long long), s));
     unsigned *err = (unsigned *)err_b.p;
-    unsigned long long *updown = (unsigned long long *)err_b.p + 2;
+    unsigned long long *up = (unsigned long long *)err_b.p + 2;
     PG_CUDA(cudaMemsetAsync(err_b.p, 0, 4 * sizeof(unsigned long long), s));
     k_check_offsets<<<grid_for(n + 1, kBlock), kBlock, 0, s>>>(d_off, n, nnz, err);
     unsigned herr = 0;
@@ -214,18 +222,14 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
     PG_CUDA(cudaStreamSynchronize(s));
     if (herr) return pg_set_error(PG_EINVAL, "offsets must start at 0, end at nnz and be non-decreasing");
     if (n > 0) {
-        k_validate<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, d_labels, n, err, updown);
+        k_validate<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(d_off, d_adj, d_labels, n, err);
         PG_CUDA(cudaGetLastError());
-        unsigned long long h[4] = {0, 0, 0, 0}; // err word (low half of h[0]), unused, up, down
-        PG_CUDA(cudaMemcpyAsync(h, err_b.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        PG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         PG_CUDA(cudaStreamSynchronize(s));
-        herr = (unsigned)(h[0] & 0xffffffffull);
-        if (h[2] != h[3]) herr |= 8;
     }
     if (herr & 1) return pg_set_error(PG_EINVAL, "adjacency entry out of range");
     if (herr & 2) return pg_set_error(PG_EINVAL, "self loop in data graph");
     if (herr & 4) return pg_set_error(PG_EINVAL, "adjacency list not strictly ascending (unsorted or duplicate)");
-    if (herr & 8) return pg_set_error(PG_EINVAL, "asymmetric edge: graph must be undirected");
     if (herr & 16) return pg_set_error(PG_EINVAL, "negative vertex label");
 
     const int64_t nn = n > 0 ? n : 1;
@@ -294,13 +298,21 @@ int pg_graph_build(pg_graph *g, const int64_t *d_off, const int32_t *d_adj, int6
         k_scatter<<<grid_for(nnz, kBlock), kBlock, 0, s>>>((unsigned long long *)ekeys2.p, nnz,
                                                            (int64_t *)ustart.p, (int64_t *)pstart.p, g->adj);
     }
-    if (n > 0)
+    if (n > 0) {
         k_finish<<<grid_for(n, kBlock), kBlock, 0, s>>>(g->adj, (int64_t *)pstart.p, (int64_t *)udeg.p,
                                                         (int64_t *)pdeg.p, sorted, d_labels, n, g->vinfo, maxes);
+        PG_CUDA(cudaGetLastError());
+        k_symmetric<<<grid_for(n * 32, kBlock), kBlock, 0, s>>>(g->vinfo, g->adj, n, err, up);
+    }
     PG_CUDA(cudaGetLastError());
     int hm[3] = {0, 0, 0};
+    unsigned long long hup = 0;
     PG_CUDA(cudaMemcpyAsync(hm, maxes, sizeof(hm), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    PG_CUDA(cudaMemcpyAsync(&hup, up, sizeof(hup), cudaMemcpyDeviceToHost, s));
     PG_CUDA(cudaStreamSynchronize(s));
+    if ((herr & 8) || 2 * hup != (unsigned long long)nnz)
+        return pg_set_error(PG_EINVAL, "asymmetric edge: graph must be undirected");
     g->max_deg = hm[0];
     g->max_out = hm[1];
     g->n_labels = d_labels ? hm[2] + 1 : 0;
