@@ -150,7 +150,7 @@ typedef struct {
 #define PG_KERNEL_GENERIC 1       /* plan interpreter, any pattern */
 #define PG_KERNEL_CLIQUE_PLAIN 2  /* plan interpreter, one warp per task, one launch per pattern */
 #define PG_KERNEL_CLIQUE 3        /* k-clique, persistent, bitmap sub-graph */
-#define PG_KERNEL_BATCHED 4       /* all plans in one launch over their shared prefix tree */
+#define PG_KERNEL_BATCHED 4       /* all plans in one launch (pg_compile_batch) */
 #define PG_KERNEL_CLIQUE_NONPERSISTENT 5 /* k-clique bitmap kernel without persistence: one warp per
                                             start vertex (one CTA per heavy one), one launch pair
                                             per pattern -- the plain form of PG_KERNEL_CLIQUE */

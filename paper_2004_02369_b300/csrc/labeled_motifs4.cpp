@@ -9,7 +9,7 @@
 // each of its connected induced triples, with its labels, occurs.  The
 // surviving labeled patterns are canonicalised under the shape's
 // automorphisms and counted exactly as vertex-induced labeled plans, several
-// per fused launch (the batch kernel over a shared prefix tree, anti-edges
+// per fused launch (the batch kernel, one task group per pattern, anti-edges
 // expanded into edge-induced terms).  Only nonzero counts are reported.
 #include <algorithm>
 #include <array>

@@ -240,7 +240,7 @@ int pg_labeled_motif3_run(pg_graph *g, pg_labeled_count *out, int64_t capacity, 
 // labeled_motifs4.cpp
 int pg_labeled_motif4_run(pg_graph *g, pg_labeled_count4 *out, int64_t capacity, int64_t *n_out, cudaStream_t s);
 
-// count_batched.cu: many plans, one launch over a shared prefix tree
+// count_batched.cu: many plans in one launch (prefix trees, task groups)
 int pg_batch_build(pg_plan *const *plans, int n_plans, int flags, pg_batch **out);
 int pg_batch_build_trie(pg_batch *b);
 #define PG_BATCH_HOST_ONLY 0x100 // internal flag: build the tree only, stage later

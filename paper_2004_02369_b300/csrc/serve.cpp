@@ -5,8 +5,9 @@
 // queries into batches whenever one of the server's streams is free and the
 // batch's scratch requirement fits that stream's preallocated arena (device
 // memory admission), counts each batch in one launch of the batched kernel
-// (shared prefix tree, cliques through the clique kernel), and publishes the
-// results with their submit / start / completion times.  Batches on different
+// (one task group per pattern, cliques through the clique kernel), and
+// publishes the results with their submit / start / completion times.
+// Batches on different
 // streams run concurrently on the device (continuous batching: queries that
 // arrive while others are on the GPU are admitted as soon as a stream frees
 // up).  With serial = 1 the same kernels run one query per launch, one
