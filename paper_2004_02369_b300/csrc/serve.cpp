@@ -7,11 +7,11 @@
 // memory admission), counts each batch in one launch of the batched kernel
 // (one task group per pattern, cliques through the clique kernel), and
 // publishes the results with their submit / start / completion times.
-// Batches on different
-// streams run concurrently on the device (continuous batching: queries that
-// arrive while others are on the GPU are admitted as soon as a stream frees
-// up).  With serial = 1 the same kernels run one query per launch, one
-// launch at a time -- the one-query-at-a-time baseline.
+// Batches on different streams run concurrently on the device (continuous
+// batching: queries that arrive while others are on the GPU are admitted as
+// soon as a stream frees up).  With serial = 1 the same kernels run one
+// query per launch, one launch at a time -- the one-query-at-a-time
+// baseline.
 //
 // Admission by measured cost: the first query of a pattern runs alone and
 // its service time is kept with the cached plan; patterns that took longer
