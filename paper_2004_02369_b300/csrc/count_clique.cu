@@ -313,6 +313,22 @@ __device__ void walk(const Tile &t, Walker &wk, const unsigned *C, int limit, in
 //   5-cliques:  sum_a sum_{b in B_a} popc(B_a & B_b)
 //   6-cliques:  sum_a sum_{b in B_a} sum_{q in B_a & B_b} popc(B_a & B_b & B_q)
 // Returns false (nothing counted) when R_i has more than 32 bits.
+// Position of the set bit of x with k set bits below it (0 <= k < popc(x)):
+// a binary search on the bit counts of halves, quarters, ... (five fixed
+// steps, the same for every lane).
+__device__ __forceinline__ int nth_set_bit(unsigned x, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int width = 16; width > 0; width >>= 1) {
+        const int low = __popc(x & ((1u << width) - 1u));
+        const bool up = k >= low;
+        k -= up ? low : 0;
+        x = up ? x >> width : x;
+        pos += up ? width : 0;
+    }
+    return pos;
+}
+
 __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, unsigned *bsh, int lane,
                                                unsigned long long *cnt) {
     const unsigned *Ri = t.rows + (size_t)i * t.ws;
@@ -326,11 +342,7 @@ __device__ __forceinline__ bool compressed_row(const Tile &t, int i, int kmax, u
     for (int w = 0; w < nw; ++w) {
         const unsigned x = Ri[w];
         const int pc = __popc(x);
-        if (lane >= prefix && lane < prefix + pc) {
-            unsigned y = x;
-            for (int k = lane - prefix; k > 0; --k) y &= y - 1; // drop the lower set bits
-            pa = w * 32 + __ffs(y) - 1;
-        }
+        if (lane >= prefix && lane < prefix + pc) pa = w * 32 + nth_set_bit(x, lane - prefix);
         prefix += pc;
     }
     unsigned B = 0;
